@@ -1,0 +1,346 @@
+/*
+ * psolve_oracle.c -- plain, serial FP64 CPU oracle for the preconditioned
+ * Bi-CGSTAB Poisson solver of arxiv 2503.08935.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product (CUDA) path includes,
+ * links or calls this file; only the tests, the smoke check and the timed
+ * CPU-baseline leg of the benchmark load it.  It shares no code, header,
+ * table or constant with the CUDA library.
+ *
+ * Every routine is the textbook definition written out with plain loops in
+ * the order the paper states it:
+ *   - 7-point operator          : Eq. 3 (second-order difference) and Eq. 6
+ *                                 (Kronecker sum of 1-D Dirichlet matrices D,
+ *                                 Eq. 4); neighbours outside the grid are 0.
+ *   - Block restriction         : Eq. 12-14 (R_s A R_s^T, non-overlapping
+ *                                 equal blocks; cross-block neighbours are 0).
+ *   - Eigenvalue bounds         : Eq. 8-11 with the Dirichlet spectrum Eq. 9.
+ *   - Chebyshev iteration       : Eq. 15 (theta, delta, sigma) and Algorithm 2.
+ *   - Preconditioned Bi-CGSTAB  : Algorithm 1 (right-preconditioned form with
+ *                                 the half-step exit), stopping on the
+ *                                 relative residual ||r||_2/||b||_2.
+ *   - Dot products              : Ogita-Rump-Oishi "Dot2" (SIAM J. Sci.
+ *                                 Comput. 26(6), 2005), summed in index order,
+ *                                 so the oracle's dots are close to correctly
+ *                                 rounded and independent of any GPU
+ *                                 reduction tree.
+ *
+ * Layout: a grid vector is n[0]*n[1]*n[2] doubles, x fastest:
+ *   idx(i,j,k) = i + n[0]*(j + n[1]*k).
+ *
+ * Build with -O2 -ffp-contract=off and without -ffast-math: Dot2's
+ * error-free transformations need IEEE rounding of every operation.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "psolve_oracle.h"
+
+/* ------------------------------------------------------------------------ */
+/* Dot2 (Ogita, Rump, Oishi 2005): error-free TwoProduct via fma, Knuth's     */
+/* TwoSum, and a running compensation term.                                   */
+/* ------------------------------------------------------------------------ */
+static void two_sum(double a, double b, double *s, double *e)
+{
+    double x = a + b;
+    double z = x - a;
+    *e = (a - (x - z)) + (b - z);
+    *s = x;
+}
+
+static void two_prod(double a, double b, double *p, double *e)
+{
+    double x = a * b;
+    *e = fma(a, b, -x);
+    *p = x;
+}
+
+double oracle_dot(int64_t N, const double *a, const double *b)
+{
+    if (N <= 0) return 0.0;
+    double p, s, h, r, q;
+    two_prod(a[0], b[0], &p, &s);
+    for (int64_t i = 1; i < N; ++i) {
+        two_prod(a[i], b[i], &h, &r);
+        two_sum(p, h, &p, &q);
+        s = s + (q + r);
+    }
+    return p + s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 7-point operator, Eq. 3 / Eq. 6.                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Value of u at integer coordinates c (one of which may be out of range), or
+ * 0 if c lies outside the grid (zero Dirichlet ghost, Eq. 4) or, when
+ * bs != NULL, outside the block of size bs that contains `home`. */
+static double nb_value(const int64_t n[3], const int64_t *bs, const double *u,
+                       const int64_t home[3], const int64_t c[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        if (c[d] < 0 || c[d] >= n[d]) return 0.0;
+        if (bs && (c[d] / bs[d]) != (home[d] / bs[d])) return 0.0;
+    }
+    return u[c[0] + n[0] * (c[1] + n[1] * c[2])];
+}
+
+int oracle_apply_A(const int64_t n[3], const double h[3], const int32_t blocks[3],
+                   const double *u, double *out)
+{
+    int64_t bs_store[3];
+    const int64_t *bs = NULL;
+    for (int d = 0; d < 3; ++d)
+        if (n[d] < 1 || !(h[d] > 0.0)) return ORACLE_E_ARG;
+    if (blocks) {
+        for (int d = 0; d < 3; ++d) {
+            if (blocks[d] < 1 || n[d] % blocks[d] != 0) return ORACLE_E_ARG;
+            bs_store[d] = n[d] / blocks[d];
+        }
+        bs = bs_store;
+    }
+    for (int64_t k = 0; k < n[2]; ++k)
+        for (int64_t j = 0; j < n[1]; ++j)
+            for (int64_t i = 0; i < n[0]; ++i) {
+                const int64_t home[3] = {i, j, k};
+                const double uc = u[i + n[0] * (j + n[1] * k)];
+                double acc = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    int64_t lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                    lo[d] -= 1;
+                    hi[d] += 1;
+                    const double ul = nb_value(n, bs, u, home, lo);
+                    const double uh = nb_value(n, bs, u, home, hi);
+                    /* (-u_{d-1} + 2 u_d - u_{d+1}) / h_d^2 , Eq. 3 */
+                    acc += (-ul + 2.0 * uc - uh) / (h[d] * h[d]);
+                }
+                out[i + n[0] * (j + n[1] * k)] = acc;
+            }
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eigenvalue bounds, Eq. 8-11 with Eq. 9.                                    */
+/* ------------------------------------------------------------------------ */
+static double mu_dirichlet(int64_t i, int64_t n)
+{
+    const double pi = 3.14159265358979323846;
+    const double s = sin((double)i * pi / (2.0 * (double)(n + 1)));
+    return 4.0 * s * s; /* Eq. 9 */
+}
+
+int oracle_eig_bounds(const int64_t n[3], const double h[3], double *lmin, double *lmax)
+{
+    double lo = 0.0, hi = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] < 1 || !(h[d] > 0.0)) return ORACLE_E_ARG;
+        /* Eq. 10 / 11: sum over axes of the extreme 1-D eigenvalues. */
+        lo += mu_dirichlet(1, n[d]) / (h[d] * h[d]);
+        hi += mu_dirichlet(n[d], n[d]) / (h[d] * h[d]);
+    }
+    *lmin = lo;
+    *lmax = hi;
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Chebyshev iteration, Eq. 15 and Algorithm 2.                               */
+/* The operator is the full grid operator (blocks == NULL) or its block-      */
+/* diagonal restriction (Eq. 14).  [a, b] is the eigenvalue interval.         */
+/* ------------------------------------------------------------------------ */
+int oracle_cheb(const int64_t n[3], const double h[3], const int32_t blocks[3],
+                double a, double b, int32_t degree, const double *rhs, double *x)
+{
+    if (degree < 0 || !(b > a) || !(a > 0.0)) return ORACLE_E_ARG;
+    const int64_t N = n[0] * n[1] * n[2];
+    const double theta = 0.5 * (b + a);
+    const double delta = 0.5 * (b - a);
+    const double sigma = theta / delta;
+    double rho_old = 1.0 / sigma;
+    double rho_cur = 1.0 / (2.0 * sigma - rho_old);
+
+    double *z = (double *)malloc(sizeof(double) * (size_t)N);
+    double *y = (double *)malloc(sizeof(double) * (size_t)N);
+    double *w = (double *)malloc(sizeof(double) * (size_t)N);
+    double *Av = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!z || !y || !w || !Av) {
+        free(z); free(y); free(w); free(Av);
+        return ORACLE_E_OOM;
+    }
+    int st = ORACLE_OK;
+    for (int64_t q = 0; q < N; ++q) z[q] = rhs[q] / theta;
+    if (degree == 0) {
+        memcpy(x, z, sizeof(double) * (size_t)N);
+        goto done;
+    }
+    st = oracle_apply_A(n, h, blocks, rhs, Av);
+    if (st) goto done;
+    for (int64_t q = 0; q < N; ++q)
+        y[q] = 2.0 * rho_cur / delta * (2.0 * rhs[q] - Av[q] / theta);
+    for (int32_t it = 2; it <= degree; ++it) {
+        rho_old = rho_cur;
+        rho_cur = 1.0 / (2.0 * sigma - rho_old);
+        st = oracle_apply_A(n, h, blocks, y, Av);
+        if (st) goto done;
+        for (int64_t q = 0; q < N; ++q)
+            w[q] = rho_cur * (2.0 * sigma * y[q] + 2.0 / delta * (rhs[q] - Av[q]) - rho_old * z[q]);
+        double *tmp = z; /* z <- y, y <- w */
+        z = y;
+        y = w;
+        w = tmp;
+    }
+    memcpy(x, y, sizeof(double) * (size_t)N);
+done:
+    free(z); free(y); free(w); free(Av);
+    return st;
+}
+
+/* Interval [a, b] handed to the Chebyshev iteration for a preconditioner.
+ * G(CI): closed-form bounds of the whole grid.  BJ(CI): bounds of one block
+ * (all blocks are equal, so they share them).  GNoComm(CI): bounds of the
+ * whole grid with the block-restricted operator.  Each bound is multiplied by
+ * its scale (the eigenvalue rescaling of the experimental set-up). */
+int oracle_cheb_interval(const int64_t n[3], const double h[3], int32_t precond,
+                         const int32_t blocks[3], double lmin_scale, double lmax_scale,
+                         double *a, double *b)
+{
+    int64_t m[3] = {n[0], n[1], n[2]};
+    if (precond == ORACLE_PC_BJ_CHEB) {
+        for (int d = 0; d < 3; ++d) {
+            if (!blocks || blocks[d] < 1 || n[d] % blocks[d]) return ORACLE_E_ARG;
+            m[d] = n[d] / blocks[d];
+        }
+    }
+    double lo, hi;
+    int st = oracle_eig_bounds(m, h, &lo, &hi);
+    if (st) return st;
+    *a = lmin_scale * lo;
+    *b = lmax_scale * hi;
+    if (!(*b > *a) || !(*a > 0.0)) return ORACLE_E_ARG;
+    return ORACLE_OK;
+}
+
+int oracle_precond_apply(const int64_t n[3], const double h[3], const oracle_pc *pc,
+                         const double *in, double *out)
+{
+    const int64_t N = n[0] * n[1] * n[2];
+    if (pc->type == ORACLE_PC_NONE) {
+        memcpy(out, in, sizeof(double) * (size_t)N);
+        return ORACLE_OK;
+    }
+    double a, b;
+    int st = oracle_cheb_interval(n, h, pc->type, pc->blocks, pc->lmin_scale, pc->lmax_scale, &a, &b);
+    if (st) return st;
+    const int32_t *blk = (pc->type == ORACLE_PC_CHEB) ? NULL : pc->blocks;
+    return oracle_cheb(n, h, blk, a, b, pc->degree, in, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioned Bi-CGSTAB, Algorithm 1.                                     */
+/* ------------------------------------------------------------------------ */
+static int finite(double v) { return isfinite(v); }
+
+int oracle_bicgstab(const int64_t n[3], const double h[3], const double *bvec,
+                    double *x, int32_t use_x0, double rtol, int32_t maxit,
+                    const oracle_pc *pc, int32_t half_step_check,
+                    oracle_result *res, double *hist_s, double *hist_r)
+{
+    memset(res, 0, sizeof(*res));
+    for (int d = 0; d < 3; ++d)
+        if (n[d] < 1 || !(h[d] > 0.0)) return res->status = ORACLE_E_ARG;
+    if (maxit < 0 || !(rtol >= 0.0) || !pc || pc->degree < 0) return res->status = ORACLE_E_ARG;
+    const int64_t N = n[0] * n[1] * n[2];
+    const size_t bytes = sizeof(double) * (size_t)N;
+
+    double *r = malloc(bytes), *rt = malloc(bytes), *p = malloc(bytes);
+    double *ph = malloc(bytes), *w = malloc(bytes), *s = malloc(bytes);
+    double *rh = malloc(bytes), *t = malloc(bytes);
+    int st = ORACLE_OK;
+    if (!r || !rt || !p || !ph || !w || !s || !rh || !t) { st = ORACLE_E_OOM; goto out; }
+
+    const double nb = sqrt(oracle_dot(N, bvec, bvec));
+    if (!finite(nb)) { st = ORACLE_NONFINITE; goto out; }
+    if (nb == 0.0) { /* b = 0: the solution is x = 0 */
+        memset(x, 0, bytes);
+        st = ORACLE_OK;
+        goto out;
+    }
+    /* r0 = b - A x0 */
+    if (use_x0) {
+        st = oracle_apply_A(n, h, NULL, x, t);
+        if (st) goto out;
+        for (int64_t q = 0; q < N; ++q) r[q] = bvec[q] - t[q];
+    } else {
+        memset(x, 0, bytes);
+        memcpy(r, bvec, bytes);
+    }
+    memcpy(rt, r, bytes); /* r~ = r0 */
+    memcpy(p, r, bytes);  /* p0 = r0 */
+    double rho = oracle_dot(N, rt, r);
+    double rnorm = sqrt(oracle_dot(N, r, r));
+    res->rel_res_recursive = rnorm / nb;
+    if (rnorm / nb <= rtol) { st = ORACLE_OK; goto out; }
+
+    st = ORACLE_NOT_CONVERGED;
+    for (int32_t i = 1; i <= maxit; ++i) {
+        res->iterations = i;
+        int e = oracle_precond_apply(n, h, pc, p, ph); /* M p^ = p */
+        if (e) { st = e; break; }
+        e = oracle_apply_A(n, h, NULL, ph, w); /* w = A p^ */
+        if (e) { st = e; break; }
+        const double sig1 = oracle_dot(N, rt, w);
+        if (!finite(sig1)) { st = ORACLE_NONFINITE; break; }
+        if (sig1 == 0.0) { st = ORACLE_BREAKDOWN; break; }
+        const double alpha = rho / sig1;
+        for (int64_t q = 0; q < N; ++q) s[q] = r[q] - alpha * w[q];
+        const double snorm = sqrt(oracle_dot(N, s, s));
+        if (hist_s) hist_s[i - 1] = snorm / nb;
+        if (!finite(snorm)) { st = ORACLE_NONFINITE; break; }
+        if (half_step_check && snorm / nb <= rtol) {
+            for (int64_t q = 0; q < N; ++q) x[q] = x[q] + alpha * ph[q];
+            res->half_step_exit = 1;
+            res->rel_res_recursive = snorm / nb;
+            st = ORACLE_OK;
+            break;
+        }
+        e = oracle_precond_apply(n, h, pc, s, rh); /* M r^ = s */
+        if (e) { st = e; break; }
+        e = oracle_apply_A(n, h, NULL, rh, t); /* t = A r^ */
+        if (e) { st = e; break; }
+        const double tt = oracle_dot(N, t, t);
+        const double ts = oracle_dot(N, t, s);
+        if (!finite(tt) || !finite(ts)) { st = ORACLE_NONFINITE; break; }
+        if (tt == 0.0) { st = ORACLE_BREAKDOWN; break; }
+        const double omega = ts / tt;
+        if (omega == 0.0) { st = ORACLE_BREAKDOWN; break; }
+        for (int64_t q = 0; q < N; ++q) {
+            x[q] = x[q] + alpha * ph[q] + omega * rh[q];
+            r[q] = s[q] - omega * t[q];
+        }
+        rnorm = sqrt(oracle_dot(N, r, r));
+        res->rel_res_recursive = rnorm / nb;
+        if (hist_r) hist_r[i - 1] = rnorm / nb;
+        if (!finite(rnorm)) { st = ORACLE_NONFINITE; break; }
+        if (rnorm / nb <= rtol) { st = ORACLE_OK; break; }
+        const double rho_new = oracle_dot(N, rt, r);
+        if (rho_new == 0.0) { st = ORACLE_BREAKDOWN; break; }
+        const double beta = (rho_new / rho) * (alpha / omega);
+        rho = rho_new;
+        for (int64_t q = 0; q < N; ++q) p[q] = r[q] + beta * (p[q] - omega * w[q]);
+    }
+
+out:
+    if (st != ORACLE_E_ARG && st != ORACLE_E_OOM && N > 0 && r && t) {
+        /* true residual ||b - A x|| / ||b|| of the returned x */
+        if (oracle_apply_A(n, h, NULL, x, t) == ORACLE_OK) {
+            for (int64_t q = 0; q < N; ++q) r[q] = bvec[q] - t[q];
+            const double nbb = sqrt(oracle_dot(N, bvec, bvec));
+            res->rel_res_true = nbb > 0.0 ? sqrt(oracle_dot(N, r, r)) / nbb : 0.0;
+        }
+    }
+    res->status = st;
+    free(r); free(rt); free(p); free(ph); free(w); free(s); free(rh); free(t);
+    return st;
+}

@@ -1,0 +1,89 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle runs.
+
+This module holds no arithmetic of the solver: it only produces right-hand
+sides, grid spacings and workload mixes.  Both the CUDA path and the CPU oracle
+are fed the identical arrays it returns.
+
+Random values use splitmix64 (Steele, Lea, Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) as a counter-based generator:
+value i of a stream with seed s is mix(s + (i + 1) * 0x9E3779B97F4A7C15), and a
+uniform double in [0, 1) is (value >> 11) * 2**-53.
+
+Arrays are numpy float64 with shape (nz, ny, nx), x fastest.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """uint64 values ``offset .. offset+count-1`` of the counter-based stream ``seed``."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        z = np.uint64(seed) + idx * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, count: int, lo: float = -1.0, hi: float = 1.0, offset: int = 0) -> np.ndarray:
+    """i.i.d. uniform[lo, hi) doubles from the splitmix64 stream ``seed``."""
+    u = (splitmix64(seed, count, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return lo + (hi - lo) * u
+
+
+def default_h(shape_zyx) -> tuple:
+    """Unit-cube spacing h_d = 1/(n_d + 1), returned as (hx, hy, hz)."""
+    nz, ny, nx = shape_zyx
+    return (1.0 / (nx + 1), 1.0 / (ny + 1), 1.0 / (nz + 1))
+
+
+def rhs_uniform(shape_zyx, seed: int = 1) -> np.ndarray:
+    """b ~ U[-1, 1) per point, linear index order (x fastest)."""
+    n = int(np.prod(shape_zyx))
+    return uniform(seed, n).reshape(shape_zyx)
+
+
+def rhs_manufactured(shape_zyx, h=None) -> np.ndarray:
+    """f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) at interior points x_i = (i+1) h."""
+    nz, ny, nx = shape_zyx
+    hx, hy, hz = default_h(shape_zyx) if h is None else h
+    sx = np.sin(math.pi * hx * np.arange(1, nx + 1))
+    sy = np.sin(math.pi * hy * np.arange(1, ny + 1))
+    sz = np.sin(math.pi * hz * np.arange(1, nz + 1))
+    return 3.0 * math.pi ** 2 * sz[:, None, None] * sy[None, :, None] * sx[None, None, :]
+
+
+def rhs_manufactured_noisy(shape_zyx, seed: int = 1, noise: float = 1e-3, h=None) -> np.ndarray:
+    """Manufactured sine plus ``noise`` * U[-1, 1) (seeded)."""
+    return rhs_manufactured(shape_zyx, h) + noise * rhs_uniform(shape_zyx, seed)
+
+
+def batch_shapes(count: int = 64, seed: int = 2, sides=(32, 48, 64, 96, 128)) -> list:
+    """``count`` grid shapes (nz, ny, nx), each side drawn independently from ``sides``."""
+    v = splitmix64(seed, 3 * count)
+    k = (v % np.uint64(len(sides))).astype(np.int64)
+    out = []
+    for g in range(count):
+        nx, ny, nz = (sides[k[3 * g]], sides[k[3 * g + 1]], sides[k[3 * g + 2]])
+        out.append((nz, ny, nx))
+    return out
+
+
+def serving_stream(count: int = 2000, seed: int = 3, lo: int = 16, hi: int = 256):
+    """Per-request grid shapes with each side log-uniform on [lo, hi] (rounded),
+    plus unit-rate exponential inter-arrival gaps (scale them by 1/lambda)."""
+    u = uniform(seed, 3 * count, 0.0, 1.0)
+    sides = np.rint(np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))).astype(np.int64)
+    sides = np.clip(sides, lo, hi)
+    shapes = [(int(sides[3 * i + 2]), int(sides[3 * i + 1]), int(sides[3 * i])) for i in range(count)]
+    g = uniform(seed + 1000, count, 0.0, 1.0)
+    gaps = -np.log1p(-g)  # Exp(1)
+    return shapes, gaps

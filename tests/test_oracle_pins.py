@@ -1,0 +1,384 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+Nothing here re-types the oracle's own formulas.  Each check compares the
+oracle against an independent object:
+
+* the dense Kronecker-sum matrix P of Eq. 6 built from the 1-D matrix D of
+  Eq. 4 with numpy (and its block-diagonal restriction, Eq. 12-14);
+* the golden matrix D and the Dirichlet eigenvalues of Eq. 4 / Eq. 9 for n = 5
+  written out in closed form (tests/golden/);
+* LAPACK's symmetric eigen-solver and dense LU solve on P;
+* the Chebyshev residual polynomial T_{d+1}((theta-lambda)/delta)/T_{d+1}(sigma)
+  evaluated through the cos / cosh closed form of T_m;
+* Krylov finite termination, the minimal-residual property of omega, and the
+  exact discrete solution for the manufactured right-hand side;
+* exact rational arithmetic (fractions) for the compensated dot product.
+
+A plausible slip in the oracle (a wrong h_d on an axis, a dropped neighbour, a
+sign, an off-by-one in a Chebyshev coefficient, a wrong beta or omega, a missing
+x-update term) fails at least one of them.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_08935_b300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ---------------------------------------------------------------- helpers --
+def D1(n):
+    """Eq. 4, built independently of the oracle."""
+    return 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+
+
+def dense_P(shape, h, blocks=None):
+    """Eq. 6: P = I_z x I_y x D_x/hx^2 + I_z x D_y/hy^2 x I_x + D_z/hz^2 x I_y x I_x.
+    With ``blocks`` (x, y, z counts): keep only entries inside one block (R_s A R_s^T)."""
+    nz, ny, nx = shape
+    hx, hy, hz = h
+    M = (np.kron(np.eye(nz), np.kron(np.eye(ny), D1(nx) / hx ** 2))
+         + np.kron(np.eye(nz), np.kron(D1(ny) / hy ** 2, np.eye(nx)))
+         + np.kron(D1(nz) / hz ** 2, np.kron(np.eye(ny), np.eye(nx))))
+    if blocks is not None:
+        bx, by, bz = blocks
+        k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        lab = (((k // (nz // bz)) * by + (j // (ny // by))) * bx + (i // (nx // bx))).ravel()
+        M = M * (lab[:, None] == lab[None, :])
+    return M
+
+
+def cheb_T(m, x):
+    """Chebyshev polynomial of the first kind via its trigonometric closed form."""
+    if abs(x) <= 1.0:
+        return math.cos(m * math.acos(x))
+    if x > 1.0:
+        return math.cosh(m * math.acosh(x))
+    return (-1) ** m * math.cosh(m * math.acosh(-x))
+
+
+def cheb_q(lam, a, b, d):
+    """Degree-d Chebyshev iterate from x0 = 0 acting on an eigenvector of eigenvalue lam:
+    x = (1 - T_{d+1}((theta - lam)/delta) / T_{d+1}(sigma)) / lam."""
+    th, de = 0.5 * (b + a), 0.5 * (b - a)
+    return (1.0 - cheb_T(d + 1, (th - lam) / de) / cheb_T(d + 1, th / de)) / lam
+
+
+def sine_mode(shape, kx, ky, kz):
+    nz, ny, nx = shape
+    sx = np.sin(kx * math.pi * np.arange(1, nx + 1) / (nx + 1))
+    sy = np.sin(ky * math.pi * np.arange(1, ny + 1) / (ny + 1))
+    sz = np.sin(kz * math.pi * np.arange(1, nz + 1) / (nz + 1))
+    return sz[:, None, None] * sy[None, :, None] * sx[None, None, :]
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+def read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append([float(eval(t, {"sqrt": math.sqrt})) for t in line.split()])
+    return np.array(rows)
+
+
+# ------------------------------------------------------------------- dots --
+def _exact_dot(a, b):
+    return sum((Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b)), Fraction(0))
+
+
+@pytest.mark.parametrize("cond", ["plain", "cancelling"])
+def test_dot2_near_correctly_rounded(cond):
+    rng = np.random.default_rng(7)
+    n = 400
+    a = rng.standard_normal(n)
+    b = rng.standard_normal(n)
+    if cond == "cancelling":
+        # Each pair (a_i 2^e_i, b_i) and (a_i 2^e_i, -b_i (1 + 2^-20)) nearly cancels, but the two
+        # products round differently, so the sum is ~2^-20 of the products' magnitude and a
+        # dot product that drops the products' rounding errors misses the bound by ~2^20.
+        e = np.ldexp(1.0, rng.integers(-30, 30, n))
+        a = np.concatenate([a * e, a * e])
+        b = np.concatenate([b, -b * (1.0 + 2.0 ** -20)])
+    got = O.dot(a, b)
+    exact = _exact_dot(a, b)
+    eps = 2.0 ** -53
+    n = a.size
+    gam = n * eps / (1 - n * eps)
+    bound = eps * abs(float(exact)) + gam * gam * float(sum(abs(x * y) for x, y in zip(a, b)))
+    assert abs(Fraction(got) - exact) <= Fraction(bound) * 2
+
+
+def test_dot_empty_and_single():
+    assert O.dot(np.zeros(0), np.zeros(0)) == 0.0
+    assert O.dot(np.array([3.0]), np.array([-2.5])) == -7.5
+
+
+# ---------------------------------------------------------------- stencil --
+def test_D_matrix_golden_eq4():
+    """Columns of A on a 5x1x1 grid with h = 1 equal D_5 (Eq. 4, golden) plus the
+    1x1 Dirichlet matrices [2] of the y and z axes on the diagonal."""
+    Dg = read_golden("dirichlet_D_n5.txt")
+    assert Dg.shape == (5, 5)
+    cols = []
+    for q in range(5):
+        e = np.zeros((1, 1, 5))
+        e[0, 0, q] = 1.0
+        cols.append(O.apply_A(e, (1.0, 1.0, 1.0)).ravel())
+    A = np.array(cols).T
+    assert np.array_equal(A, Dg + 4.0 * np.eye(5))
+
+
+@pytest.mark.parametrize("shape,h", [((5, 4, 3), (0.3, 0.7, 1.1)), ((4, 4, 4), (0.5, 0.25, 0.125)),
+                                     ((2, 7, 1), (1.0, 0.2, 0.9)), ((1, 1, 1), (0.5, 0.5, 0.5))])
+def test_stencil_equals_dense_kronecker(shape, h):
+    u = np.random.default_rng(11).standard_normal(shape)
+    ref = dense_P(shape, h) @ u.ravel()
+    got = O.apply_A(u, h).ravel()
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("shape,blocks", [((4, 6, 4), (2, 3, 2)), ((6, 4, 8), (4, 2, 3)),
+                                          ((3, 3, 3), (1, 1, 1)), ((4, 4, 4), (4, 4, 4))])
+def test_block_stencil_equals_block_diagonal(shape, blocks):
+    h = (0.2, 0.3, 0.25)
+    u = np.random.default_rng(12).standard_normal(shape)
+    ref = dense_P(shape, h, blocks) @ u.ravel()
+    got = O.apply_A(u, h, blocks).ravel()
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_block_sizes_must_divide():
+    with pytest.raises(ValueError):
+        O.apply_A(np.zeros((4, 4, 5)), (1, 1, 1), (2, 2, 2))
+
+
+# ------------------------------------------------------------ eigenvalues --
+def test_dirichlet_eigs_golden_eq9():
+    """Eq. 9 for n = 5 in closed form: {2 - sqrt3, 1, 2, 3, 2 + sqrt3} (golden)."""
+    ev = read_golden("dirichlet_eigs_n5.txt").ravel()
+    lam = np.linalg.eigvalsh(D1(5))
+    assert np.allclose(np.sort(lam), ev, rtol=0, atol=1e-14)
+    lo, hi = O.eig_bounds((5, 1, 1), (1.0, 1.0, 1.0))
+    assert abs(lo - (ev[0] + 4.0)) <= 1e-14 and abs(hi - (ev[-1] + 4.0)) <= 1e-14
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 4), (3, 7, 2), (1, 1, 9)])
+def test_sine_modes_are_eigenvectors(shape):
+    h = (0.31, 0.17, 0.23)
+    nz, ny, nx = shape
+    for kx, ky, kz in [(1, 1, 1), (nx, ny, nz), (max(1, nx // 2), 1, nz)]:
+        v = sine_mode(shape, kx, ky, kz)
+        lam = sum(4.0 / hd ** 2 * math.sin(k * math.pi / (2 * (n + 1))) ** 2
+                  for k, n, hd in [(kx, nx, h[0]), (ky, ny, h[1]), (kz, nz, h[2])])
+        Av = O.apply_A(v, h)
+        assert rel(Av, lam * v) <= 1e-13
+
+
+@pytest.mark.parametrize("shape,h", [((3, 5, 4), (0.4, 0.2, 0.3)), ((6, 6, 6), None)])
+def test_eig_bounds_match_dense_spectrum(shape, h):
+    h = I.default_h(shape) if h is None else h
+    lam = np.linalg.eigvalsh(dense_P(shape, h))
+    nz, ny, nx = shape
+    lo, hi = O.eig_bounds((nx, ny, nz), h)
+    assert abs(lo - lam[0]) <= 1e-12 * lam[-1]
+    assert abs(hi - lam[-1]) <= 1e-12 * lam[-1]
+
+
+# -------------------------------------------------------------- Chebyshev --
+@pytest.mark.parametrize("scales", [(1.0, 1.0), (3.0, 0.9), (0.5, 1.2)])
+@pytest.mark.parametrize("d", [0, 1, 2, 3, 5, 8, 12])
+def test_cheb_matches_spectral_closed_form(d, scales):
+    shape = (6, 5, 4)
+    h = I.default_h(shape)
+    P = dense_P(shape, h)
+    lam, V = np.linalg.eigh(P)
+    a0, b0 = O.eig_bounds((4, 5, 6), h)
+    a, b = a0 * scales[0], b0 * scales[1]
+    rhs = np.random.default_rng(3).standard_normal(shape)
+    q = np.array([cheb_q(l, a, b, d) for l in lam])
+    ref = V @ (q * (V.T @ rhs.ravel()))
+    got = O.cheb(rhs, h, a, b, d).ravel()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("precond", [O.PC_BJ_CHEB, O.PC_GNOCOMM_CHEB])
+def test_block_cheb_matches_block_spectrum(precond):
+    shape, blocks = (4, 6, 8), (2, 3, 2)
+    h = (0.11, 0.13, 0.17)
+    Pb = dense_P(shape, h, blocks)
+    lam, V = np.linalg.eigh(Pb)
+    a, b = O.cheb_interval(shape, h, precond, blocks)
+    if precond == O.PC_BJ_CHEB:  # interval of one block (all blocks equal)
+        assert abs(a - lam[0]) <= 1e-12 * lam[-1] and abs(b - lam[-1]) <= 1e-12 * lam[-1]
+    else:  # GNoComm: whole-grid interval, strictly wider than any block's spectrum
+        g0, g1 = np.linalg.eigvalsh(dense_P(shape, h))[[0, -1]]
+        assert abs(a - g0) <= 1e-12 * g1 and abs(b - g1) <= 1e-12 * g1
+    rhs = np.random.default_rng(4).standard_normal(shape)
+    for d in (0, 1, 4):
+        q = np.array([cheb_q(l, a, b, d) for l in lam])
+        ref = V @ (q * (V.T @ rhs.ravel()))
+        got = O.precond_apply(rhs, h, precond, d, blocks).ravel()
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_cheb_degree0_is_b_over_theta_and_linear():
+    shape = (5, 6, 7)
+    h = I.default_h(shape)
+    a, b = O.eig_bounds((7, 6, 5), h)
+    u = I.rhs_uniform(shape, seed=5)
+    v = I.rhs_uniform(shape, seed=6)
+    assert np.array_equal(O.cheb(u, h, a, b, 0), u / (0.5 * (a + b)))
+    lhs = O.cheb(2.5 * u + v, h, a, b, 6)
+    rhs = 2.5 * O.cheb(u, h, a, b, 6) + O.cheb(v, h, a, b, 6)
+    assert rel(lhs, rhs) <= 1e-13
+
+
+def test_cheb_error_decay_exact_bounds():
+    """With exact bounds, ||CI_d(b) - A^{-1} b||_A <= 2 ((sqrt k - 1)/(sqrt k + 1))^{d+1} ||A^{-1} b||_A."""
+    shape = (8, 8, 8)
+    h = I.default_h(shape)
+    P = dense_P(shape, h)
+    a, b = O.eig_bounds((8, 8, 8), h)
+    rhs = I.rhs_uniform(shape, seed=9)
+    xs = np.linalg.solve(P, rhs.ravel())
+    kap = b / a
+    c = (math.sqrt(kap) - 1) / (math.sqrt(kap) + 1)
+
+    def anorm(e):
+        return math.sqrt(e @ P @ e)
+
+    for d in (1, 4, 8, 16):
+        e = O.cheb(rhs, h, a, b, d).ravel() - xs
+        assert anorm(e) <= 2 * c ** (d + 1) * anorm(xs) * (1 + 1e-9)
+
+
+# -------------------------------------------------------------- Bi-CGSTAB --
+PCS = [(O.PC_NONE, 0, (1, 1, 1)), (O.PC_CHEB, 3, (1, 1, 1)), (O.PC_BJ_CHEB, 2, (2, 1, 2)),
+       (O.PC_GNOCOMM_CHEB, 2, (2, 1, 2)), (O.PC_CHEB, 0, (1, 1, 1))]
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (6, 6, 6), (6, 5, 4)])
+@pytest.mark.parametrize("pc", PCS)
+@pytest.mark.parametrize("with_x0", [False, True])
+def test_bicgstab_matches_dense_solve(shape, pc, with_x0):
+    h = I.default_h(shape)
+    P = dense_P(shape, h)
+    b = I.rhs_uniform(shape, seed=21)
+    x0 = I.rhs_uniform(shape, seed=22) if with_x0 else None
+    x, res = O.bicgstab(b, h, rtol=1e-13, maxit=1000, precond=pc[0], degree=pc[1], blocks=pc[2], x0=x0)
+    assert res.status == O.OK
+    xs = np.linalg.solve(P, b.ravel())
+    kappa = np.linalg.cond(P)
+    assert rel(x, xs) <= 10 * kappa * 1e-13
+    assert res.rel_res_true <= 1e-12
+
+
+def test_finite_termination_on_m_modes():
+    """b in the span of m eigenvectors with distinct eigenvalues: the Krylov space has
+    dimension m, BiCG ends at step m, so Bi-CGSTAB's half-step residual s_m vanishes."""
+    shape = (7, 6, 5)
+    h = I.default_h(shape)
+    modes = [(1, 1, 1), (2, 3, 1), (5, 6, 7), (3, 2, 4)]
+    for m in range(1, len(modes) + 1):
+        b = sum((0.7 + q) * sine_mode(shape, *modes[q]) for q in range(m))
+        for pc in (O.PC_NONE, O.PC_CHEB):
+            x, res = O.bicgstab(b, h, rtol=1e-11, maxit=50, precond=pc, degree=2 if pc else 0)
+            assert res.status == O.OK and res.iterations <= m, (m, pc, res)
+            assert res.rel_res_true <= 1e-10
+
+
+@pytest.mark.parametrize("pc", PCS[:4])
+def test_omega_minimises_residual(pc):
+    """omega = t.s / t.t minimises ||s - omega t||, so ||r_i|| <= ||s_i|| each iteration."""
+    shape = (10, 9, 8)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=31)
+    x, res = O.bicgstab(b, h, rtol=0.0, maxit=6, precond=pc[0], degree=pc[1], blocks=pc[2])
+    assert res.iterations == 6
+    hs, hr = res.hist_s, res.hist_r
+    assert np.all(np.isfinite(hr)) and np.all(hr <= hs * (1 + 1e-13))
+
+
+@pytest.mark.parametrize("pc", PCS[:4])
+def test_true_and_recursive_residual_agree(pc):
+    shape = (16, 16, 16)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=41)
+    rtol = 1e-10
+    x, res = O.bicgstab(b, h, rtol=rtol, maxit=2000, precond=pc[0], degree=pc[1] + 2, blocks=pc[2])
+    assert res.status == O.OK
+    assert res.rel_res_recursive <= rtol
+    assert abs(res.rel_res_true - res.rel_res_recursive) <= 0.1 * rtol
+
+
+@pytest.mark.parametrize("n", [15, 32])
+def test_manufactured_exact_discrete_solution_and_half_step(n):
+    """f = 3 pi^2 prod sin(pi x_d) is the (1,1,1) sine mode, so A^{-1} f = f / lambda_111
+    exactly, and the first half-step already converges (s = f - alpha A f = 0)."""
+    shape = (n, n, n)
+    h = I.default_h(shape)
+    f = I.rhs_manufactured(shape)
+    x, res = O.bicgstab(f, h, rtol=1e-10, maxit=2000)
+    lam111 = 3 * 4.0 / h[0] ** 2 * math.sin(math.pi * h[0] / 2) ** 2
+    assert res.status == O.OK and res.iterations == 1 and res.half_step_exit
+    assert rel(x, f / lam111) <= 1e-12
+
+
+def test_manufactured_second_order_convergence():
+    """Discretisation error against the continuous solution sin sin sin: O(h^2), ratio ~4."""
+    errs = []
+    for n in (15, 31, 63):
+        shape = (n, n, n)
+        h = I.default_h(shape)
+        f = I.rhs_manufactured(shape)
+        x, res = O.bicgstab(f, h, rtol=1e-12, maxit=100)
+        exact = f / (3 * math.pi ** 2)
+        errs.append(np.max(np.abs(x - exact)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.8 < r1 < 4.2 and 3.9 < r2 < 4.1
+
+
+# --------------------------------------------------------- special cases --
+def test_zero_rhs_gives_zero():
+    b = np.zeros((3, 4, 5))
+    x, res = O.bicgstab(b, (1, 1, 1), rtol=1e-10, maxit=10, x0=np.ones_like(b))
+    assert res.status == O.OK and res.iterations == 0 and not np.any(x)
+
+
+def test_nonfinite_rhs_is_reported():
+    b = I.rhs_uniform((4, 4, 4))
+    b[1, 2, 3] = np.nan
+    x, res = O.bicgstab(b, I.default_h(b.shape), rtol=1e-10, maxit=10)
+    assert res.status == O.NONFINITE
+
+
+def test_maxit_exhaustion():
+    shape = (12, 12, 12)
+    b = I.rhs_uniform(shape)
+    x, res = O.bicgstab(b, I.default_h(shape), rtol=1e-14, maxit=2)
+    assert res.status == O.NOT_CONVERGED and res.iterations == 2
+
+
+def test_exact_initial_guess_returns_immediately():
+    shape = (5, 5, 5)
+    h = I.default_h(shape)
+    xs = I.rhs_uniform(shape, seed=8)
+    b = O.apply_A(xs, h)
+    x, res = O.bicgstab(b, h, rtol=1e-10, maxit=10, x0=xs)
+    assert res.status == O.OK and res.iterations == 0 and np.array_equal(x, xs)
+
+
+def test_rescaled_interval_inverted_is_rejected():
+    """lambda_min x 100 exceeds lambda_max on a tiny grid: the interval is empty."""
+    with pytest.raises(ValueError):
+        O.cheb_interval((4, 4, 4), I.default_h((4, 4, 4)), O.PC_CHEB, (1, 1, 1), 100.0, 1 - 1e-4)
