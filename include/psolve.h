@@ -1,0 +1,255 @@
+/*
+ * psolve.h -- C ABI of libpsolve, a single-GPU (B300, sm_103a) solver for the
+ * 3-D Poisson equation -Laplace(phi) = f (Eq. 1) discretised with the
+ * second-order 7-point finite-difference operator (Eq. 3, Eq. 6) and zero
+ * Dirichlet boundaries (the 1-D matrix D of Eq. 4), by preconditioned
+ * Bi-CGSTAB (Algorithm 1) with Chebyshev-iteration preconditioners (Eq. 15,
+ * Algorithm 2) on the whole grid, G(CI), or per block, BJ(CI) and
+ * GNoComm(CI) (Eq. 12-14 and the preconditioner summary, Table 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid vectors are contiguous arrays of n = nx*ny*nz doubles, x fastest:
+ *     index(i, j, k) = i + nx * (j + ny * k),  0 <= i < nx, ...
+ * (a torch tensor of shape [nz, ny, nx], float64, contiguous).  Unless an
+ * entry point says "host", every vector pointer is a DEVICE pointer on the
+ * current CUDA device, 8-byte aligned, owned by the caller, and must stay
+ * valid until the call returns (or, for psolve_submit, until psolve_poll
+ * reports a status other than PSOLVE_PENDING).
+ *
+ * Grid spacing h[3] = (hx, hy, hz) > 0; the interior points are
+ * x_i = (i + 1) hx etc. (the unit cube has h_d = 1/(n_d + 1)).
+ *
+ * All work is ordered on the CUDA stream passed at creation (a cudaStream_t
+ * cast to uintptr_t; 0 = the legacy default stream).  Solves are
+ * synchronous: they return after the result is known.  A context is not
+ * thread-safe: use one context per host thread.
+ *
+ * Every call returns a psolve_status and never aborts the process; on error
+ * psolve_last_error() gives a message for the calling thread.  There is no
+ * CPU fallback: without a usable CUDA device the calls return
+ * PSOLVE_E_CUDA.
+ */
+#ifndef PSOLVE_H
+#define PSOLVE_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PSOLVE_API __attribute__((visibility("default")))
+#else
+#define PSOLVE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PSOLVE_OK = 0,            /* converged (or nothing to do)                 */
+    PSOLVE_E_ARG = 1,         /* invalid argument; nothing was launched       */
+    PSOLVE_E_OOM = 2,         /* device or pinned allocation failed           */
+    PSOLVE_E_CUDA = 3,        /* a CUDA runtime call failed                   */
+    PSOLVE_NOT_CONVERGED = 4, /* maxit reached; x holds the last iterate      */
+    PSOLVE_BREAKDOWN = 5,     /* r~.w, t.t, omega or rho became exactly zero  */
+    PSOLVE_NONFINITE = 6,     /* NaN/Inf met in a reduction                   */
+    PSOLVE_TIMEOUT = 7,       /* a bounded wait gave up                       */
+    PSOLVE_PENDING = 8,       /* psolve_poll: request not finished yet        */
+    PSOLVE_REJECTED = 9       /* psolve_submit: exceeds the memory budget     */
+} psolve_status;
+
+/* Preconditioner M of Algorithm 1 (Table 1). */
+typedef enum {
+    PSOLVE_PC_NONE = 0,         /* M = I: plain Bi-CGSTAB                         */
+    PSOLVE_PC_CHEB = 1,         /* G(CI): Chebyshev iteration on the whole grid   */
+    PSOLVE_PC_BJ_CHEB = 2,      /* BJ(CI): Chebyshev per block (Eq. 14), bounds
+                                   of one block                                   */
+    PSOLVE_PC_GNOCOMM_CHEB = 3  /* GNoComm(CI): per block, bounds of the whole
+                                   grid                                           */
+} psolve_precond;
+
+/* Storage precision of the Chebyshev preconditioner's vectors.  The outer
+ * Bi-CGSTAB vectors, its dot products and alpha/omega/beta stay FP64. */
+typedef enum {
+    PSOLVE_FP64 = 0,  /* everything FP64                                    */
+    PSOLVE_FP32 = 1,  /* Chebyshev vectors FP32, FP32 arithmetic             */
+    PSOLVE_BF16 = 2   /* Chebyshev vectors stored BF16, FP32 arithmetic      */
+} psolve_prec;
+
+typedef struct {
+    /* Chebyshev interval [a, b] = [lmin_scale * lambda_min, lmax_scale *
+     * lambda_max], lambda from the closed form (Eq. 9-11).  1, 1 = exact
+     * bounds.  The experimental set-up's rescaling for G(CI)/GNoComm(CI) is
+     * lmin_scale = 100, lmax_scale = 1 - 1e-4. */
+    double lmin_scale;
+    double lmax_scale;
+    /* Number of equal blocks along x, y, z for BJ(CI) / GNoComm(CI); each
+     * must divide the grid size on its axis. */
+    int32_t blocks[3];
+    int32_t cheb_prec;       /* psolve_prec                                  */
+    int32_t half_step_check; /* 1: exit after the alpha half-step when
+                                ||s||/||b|| <= rtol (Algorithm 1); 0: never */
+    int32_t use_x0;          /* 1: x_dev holds the initial guess x0; 0: x0 = 0 */
+    int32_t poll_every;      /* outer iterations per host status check; 0 = auto */
+    int32_t use_graph;       /* 1: replay captured CUDA graphs; 0: plain launches */
+    int32_t timing;          /* 1: time each kernel class with CUDA events
+                                (plain launches); see psolve_result           */
+    int32_t true_residual;   /* 1: recompute ||b - A x||/||b|| at exit        */
+    int32_t rr_every;        /* mixed precision: replace r by b - A x every
+                                rr_every iterations (0 = never)              */
+    int32_t reserved[5];
+} psolve_opts;
+
+/* Fill *o with the defaults: scales 1, 1; blocks 1,1,1; FP64; half-step check
+ * on; x0 = 0; poll auto; graphs on; timing off; true residual on; rr off. */
+PSOLVE_API void psolve_opts_default(psolve_opts *o);
+
+/* Kernel classes reported by timing mode (psolve_result.kclass_*). */
+enum {
+    PSOLVE_K_INIT = 0,        /* r0 and norms                                  */
+    PSOLVE_K_CI_FIRST = 1,    /* direction / half-step update fused with CI
+                                 sweep 1                                       */
+    PSOLVE_K_CI_SWEEP3 = 2,   /* CI sweep k = 2 (reads 2 vectors, writes 1)     */
+    PSOLVE_K_CI_SWEEP4 = 3,   /* CI sweeps k >= 3 (reads 3 vectors, writes 1)   */
+    PSOLVE_K_STENCIL_DOT = 4, /* w = A p^, r~.w                                */
+    PSOLVE_K_STENCIL_2DOT = 5,/* t = A r^, t.s, t.t                            */
+    PSOLVE_K_UPDATE = 6,      /* x, r update with r~.r, r.r                    */
+    PSOLVE_K_OTHER = 7,       /* true residual, unpreconditioned updates, ...  */
+    PSOLVE_K_NCLASS = 8
+};
+
+typedef struct {
+    int32_t status;            /* psolve_status of the solve                   */
+    int32_t iterations;        /* outer index i at exit (0 if r0 passes)       */
+    int32_t half_step_exit;    /* 1 if the exit was the ||s|| half-step test   */
+    int32_t pad_;
+    double rel_res_recursive;  /* ||r||/||b|| of the recursive residual        */
+    double rel_res_true;       /* ||b - A x||/||b|| at exit (if enabled)       */
+    double seconds;            /* wall time of the call                        */
+    double model_bytes;        /* algorithmic HBM bytes of the work done       */
+    int64_t kernel_launches;   /* kernels launched by this call (incl. no-ops) */
+    /* timing mode only: per kernel class, summed CUDA-event milliseconds,
+     * number of launches that did work, and algorithmic bytes they moved. */
+    double kclass_ms[PSOLVE_K_NCLASS];
+    int64_t kclass_launches[PSOLVE_K_NCLASS];
+    double kclass_bytes[PSOLVE_K_NCLASS];
+} psolve_result;
+
+typedef struct psolve_ctx psolve_ctx;
+
+/* Create a solver for one grid.
+ *   grid[3] = (nx, ny, nz) interior points, each >= 1, product < 2^31.
+ *   h[3]    = (hx, hy, hz) > 0.
+ *   bc[6]   = boundary type of the faces x-, x+, y-, y+, z-, z+; only 0 (zero
+ *             Dirichlet, Eq. 4) is implemented; NULL means all Dirichlet.
+ *   opts    = NULL for psolve_opts_default().
+ *   stream  = cudaStream_t (as uintptr_t) that orders all work.
+ * Allocates the device workspace (at most 12 grid vectors) once; returns
+ * PSOLVE_E_ARG for bad sizes, blocks < 1 or a Neumann face, PSOLVE_E_OOM if
+ * it does not fit.  *out is set only on success. */
+PSOLVE_API psolve_status psolve_create(const int64_t grid[3], const double h[3], const int32_t bc[6],
+                            const psolve_opts *opts, uintptr_t stream, psolve_ctx **out);
+
+/* Solve A x = b (Algorithm 1) to ||r||/||b|| <= rtol or maxit iterations.
+ *   rhs_dev : b (device, read only).
+ *   x_dev   : out: x.  In: x0 if opts.use_x0, else ignored (x0 = 0).
+ *   rtol >= 0 (0 runs exactly maxit iterations unless a residual is 0).
+ *   maxit >= 0.
+ *   precond : psolve_precond; degree = Chebyshev iterations d of Algorithm 2
+ *             (0 <= d <= 64; = number of A applications; 0 gives b/theta).
+ * Returns the solve's status (also in res->status; res may be NULL).
+ * PSOLVE_E_ARG: bad rtol/maxit/precond/degree, blocks not dividing the grid
+ * for BJ/GNoComm, or an empty Chebyshev interval (scaled lambda_min >=
+ * scaled lambda_max). */
+PSOLVE_API psolve_status psolve_solve(psolve_ctx *ctx, const double *rhs_dev, double *x_dev, double rtol,
+                           int32_t maxit, int32_t precond, int32_t degree, psolve_result *res);
+
+/* The same solve from HOST memory: copies rhs_host (n doubles) to the device,
+ * solves, and copies x back to x_host (n doubles; read as x0 when
+ * opts.use_x0).  Host buffers may be pageable or pinned (pinned is faster).
+ * The copies are ordered on the context's stream; the device copies of b and
+ * x are owned by the context. */
+PSOLVE_API psolve_status psolve_solve_host(psolve_ctx *ctx, const double *rhs_host, double *x_host,
+                                double rtol, int32_t maxit, int32_t precond, int32_t degree,
+                                psolve_result *res);
+
+PSOLVE_API void psolve_destroy(psolve_ctx *ctx);
+
+/* ---- building blocks of the hot path, exposed for parity testing ------- */
+
+/* out = A u (Eq. 6).  block_restricted != 0 applies R_s A R_s^T per block
+ * (Eq. 14) with the context's opts.blocks.  u and out must not overlap. */
+PSOLVE_API psolve_status psolve_apply_A(psolve_ctx *ctx, const double *u_dev, double *out_dev,
+                             int32_t block_restricted);
+
+/* out = M^{-1} v for the Chebyshev preconditioner (precond, degree) exactly
+ * as psolve_solve applies it, at the context's opts.cheb_prec (the result is
+ * widened to double).  precond must not be PSOLVE_PC_NONE.  v and out must
+ * not overlap. */
+PSOLVE_API psolve_status psolve_precond_apply(psolve_ctx *ctx, const double *v_dev, double *out_dev,
+                                   int32_t precond, int32_t degree);
+
+/* *result_host = a . b with the solver's deterministic device reduction. */
+PSOLVE_API psolve_status psolve_dot(psolve_ctx *ctx, const double *a_dev, const double *b_dev,
+                         double *result_host);
+
+/* Closed-form Chebyshev interval [a, b] that psolve_solve hands to the
+ * preconditioner (Eq. 9-11 with the context's scales and blocks). */
+PSOLVE_API psolve_status psolve_cheb_interval(psolve_ctx *ctx, int32_t precond, double *a, double *b);
+
+/* ---- many independent grids at once ----------------------------------- */
+
+/* Solve `count` independent problems of (possibly) different sizes together:
+ * every kernel launch processes the units of all unfinished problems, and
+ * the iteration loop is replayed from one CUDA graph.  Problem q has grid
+ * grids[3q..3q+2] = (nx, ny, nz), spacing h[3q..3q+2], right-hand side
+ * rhs_dev[q] and solution x_dev[q] (device, caller-owned, same conventions as
+ * psolve_solve).  All problems share rtol, maxit, precond, degree and opts.
+ * results[q] receives problem q's result.  Each problem's iterates are
+ * bitwise the same as when it is solved alone with the same opts. */
+PSOLVE_API psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const double *h,
+                                 const double *const *rhs_dev, double *const *x_dev, double rtol,
+                                 int32_t maxit, int32_t precond, int32_t degree,
+                                 const psolve_opts *opts, uintptr_t stream,
+                                 psolve_result *results);
+
+/* ---- continuous-batching server ---------------------------------------- */
+
+typedef struct psolve_server psolve_server;
+
+/* A server owns a device memory pool of hbm_budget_bytes, a request queue
+ * and a host thread that advances all admitted problems together, one outer
+ * iteration per round, admitting queued requests at round boundaries as
+ * slots (max_slots) and memory free up.  precond/degree/cheb_prec are
+ * shared by all requests.  The server's kernels run on `stream`. */
+PSOLVE_API psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, int32_t precond,
+                                   int32_t degree, int32_t cheb_prec, uintptr_t stream,
+                                   psolve_server **out);
+
+/* Queue one solve.  grid/h as in psolve_create; rhs_dev/x_dev device
+ * pointers that stay valid until psolve_poll returns non-PENDING.  opts may
+ * be NULL (scales, blocks and half-step check are taken from it; x0 = 0).
+ * *ticket identifies the request.  PSOLVE_REJECTED if the request alone
+ * exceeds the memory budget. */
+PSOLVE_API psolve_status psolve_submit(psolve_server *srv, const int64_t grid[3], const double h[3],
+                            const double *rhs_dev, double *x_dev, double rtol, int32_t maxit,
+                            const psolve_opts *opts, uint64_t *ticket);
+
+/* PSOLVE_PENDING while the request runs; otherwise its final status, with
+ * *res filled (res may be NULL) and the ticket released. */
+PSOLVE_API psolve_status psolve_poll(psolve_server *srv, uint64_t ticket, psolve_result *res);
+
+/* Stops the host thread after the running round and frees everything;
+ * requests still queued or running end with PSOLVE_TIMEOUT. */
+PSOLVE_API void psolve_server_destroy(psolve_server *srv);
+
+/* Message describing the last error on the calling thread ("" if none). */
+PSOLVE_API const char *psolve_last_error(void);
+
+/* Library version string. */
+PSOLVE_API const char *psolve_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSOLVE_H */

@@ -1,0 +1,856 @@
+// psolve_api.cu -- the C ABI of libpsolve: single-grid contexts, the
+// building-block entry points and the batched solve.
+//
+// Solve loop.  The host launches the initial-residual kernel, then replays a
+// captured CUDA graph of K outer iterations (or launches them directly) and
+// after each replay copies the problems' scalar blocks to pinned memory.  Two
+// replays are kept in flight, so the GPU never waits for the host; kernels of
+// a problem whose `stop` flag is set return at once, so iterations issued
+// past convergence cost only their launch.  alpha, omega, beta and every
+// convergence decision are made on the device (Algorithm 1's scalars never
+// round-trip through the host inside the loop).
+#include <algorithm>
+#include <chrono>
+
+#include "psolve_engine.cuh"
+
+using namespace psolve;
+
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct GraphEntry {
+    Plan plan;
+    int k = 0;
+    cudaGraphExec_t exec = nullptr;
+    int64_t nodes = 0;
+};
+
+// State of one solve loop over a launch list of `nsc` problems whose scalar
+// blocks lie contiguously at d_sc.
+struct Runner {
+    cudaStream_t stream = 0, cap = 0;
+    const Desc *d_desc = nullptr;
+    const int32_t *d_list = nullptr;
+    int grid = 1;
+    Plan plan;
+    int K = 1;
+    bool use_graph = true;
+    bool timing = false;
+    double npts = 0;
+    std::vector<GraphEntry> *graphs = nullptr;
+    std::vector<cudaEvent_t> *events = nullptr;
+    size_t event_next = 0;
+    std::vector<LaunchRec> recs;
+    Scal *d_sc = nullptr;
+    int nsc = 1;
+    Scal *h_sc[2] = {nullptr, nullptr};
+    cudaEvent_t poll_ev[2] = {nullptr, nullptr};
+    int64_t launches = 0;
+    int iter_issued = 0;
+    int last_slot = 0;
+
+    Launcher launcher()
+    {
+        Launcher L;
+        L.stream = stream;
+        L.grid = grid;
+        L.d_desc = d_desc;
+        L.d_list = d_list;
+        L.timing = timing;
+        L.npts = npts;
+        L.recs = timing ? &recs : nullptr;
+        L.event_pool = events;
+        L.event_next = &event_next;
+        return L;
+    }
+};
+
+psolve_status get_graph(Runner &R, int k, GraphEntry **out)
+{
+    for (GraphEntry &g : *R.graphs)
+        if (g.plan == R.plan && g.k == k) {
+            *out = &g;
+            return PSOLVE_OK;
+        }
+    Launcher C;
+    C.stream = R.cap;
+    C.grid = R.grid;
+    C.d_desc = R.d_desc;
+    C.d_list = R.d_list;
+    C.iter = 2;
+    PS_CK(cudaStreamBeginCapture(R.cap, cudaStreamCaptureModeThreadLocal));
+    for (int j = 0; j < k; ++j) enqueue_iteration(C, R.plan);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(R.cap, &g);
+    if (C.err != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        set_error("graph capture failed: %s", cudaGetErrorString(C.err != cudaSuccess ? C.err : e));
+        return PSOLVE_E_CUDA;
+    }
+    GraphEntry ent;
+    ent.plan = R.plan;
+    ent.k = k;
+    ent.nodes = C.launches;
+    e = cudaGraphInstantiate(&ent.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        set_error("cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        return PSOLVE_E_CUDA;
+    }
+    R.graphs->push_back(ent);
+    *out = &R.graphs->back();
+    return PSOLVE_OK;
+}
+
+psolve_status issue(Runner &R, int slot, int k)
+{
+    if (R.use_graph && !R.timing) {
+        GraphEntry *g = nullptr;
+        psolve_status st = get_graph(R, k, &g);
+        if (st != PSOLVE_OK) return st;
+        PS_CK(cudaGraphLaunch(g->exec, R.stream));
+        R.launches += g->nodes;
+        R.iter_issued += k;
+    } else {
+        Launcher L = R.launcher();
+        for (int j = 0; j < k; ++j) {
+            L.iter = ++R.iter_issued;
+            enqueue_iteration(L, R.plan);
+        }
+        R.launches += L.launches;
+        PS_CK(L.err);
+    }
+    PS_CK(cudaMemcpyAsync(R.h_sc[slot], R.d_sc, sizeof(Scal) * R.nsc, cudaMemcpyDeviceToHost, R.stream));
+    PS_CK(cudaEventRecord(R.poll_ev[slot], R.stream));
+    return PSOLVE_OK;
+}
+
+bool all_stopped(const Scal *s, int n)
+{
+    for (int q = 0; q < n; ++q)
+        if (!s[q].stop) return false;
+    return true;
+}
+
+// Runs iterations until every problem has stopped.  maxit bounds the loop
+// (the device stops each problem at its own maxit).  On return h_sc[last_slot]
+// holds the final scalar blocks.
+psolve_status run_loop(Runner &R, int maxit)
+{
+    psolve_status st = issue(R, 0, 1);
+    if (st != PSOLVE_OK) return st;
+    st = issue(R, 1, 1);
+    if (st != PSOLVE_OK) return st;
+    const long long bound = (long long)maxit + 2LL * R.K + 4;
+    int slot = 0;
+    for (;;) {
+        PS_CK(cudaEventSynchronize(R.poll_ev[slot]));
+        if (all_stopped(R.h_sc[slot], R.nsc)) break;
+        if (R.iter_issued > bound) {
+            set_error("device did not stop after %d issued iterations (maxit %d)", R.iter_issued, maxit);
+            return PSOLVE_TIMEOUT;
+        }
+        st = issue(R, slot, R.K);
+        if (st != PSOLVE_OK) return st;
+        slot ^= 1;
+    }
+    R.last_slot = slot;
+    PS_CK(cudaStreamSynchronize(R.stream));
+    return PSOLVE_OK;
+}
+
+int auto_poll(double bytes_per_iter, int kernels_per_iter)
+{
+    // estimated iteration time: bytes at ~5 TB/s plus ~2 us per launch
+    const double us = bytes_per_iter / 5e6 + 2.0 * kernels_per_iter;
+    int k = (int)(600.0 / us);
+    return std::max(1, std::min(8, k));
+}
+
+void fill_timing(const std::vector<LaunchRec> &recs, int final_iter, int half_exit, psolve_result *res)
+{
+    for (const LaunchRec &r : recs) {
+        if (!r.ev0 || !launch_did_work(r, final_iter, half_exit)) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.ev0, r.ev1) != cudaSuccess) continue;
+        res->kclass_ms[r.cls] += ms;
+        res->kclass_launches[r.cls] += 1;
+        res->kclass_bytes[r.cls] += (r.iter == final_iter && half_exit && r.is_update) ? r.bytes_half : r.bytes;
+    }
+}
+
+bool valid_h(const double h[3])
+{
+    for (int d = 0; d < 3; ++d)
+        if (!(h[d] > 0.0) || !std::isfinite(h[d])) return false;
+    return true;
+}
+
+psolve_status check_grid(const int64_t g[3])
+{
+    long long n = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (g[d] < 1 || g[d] > (1LL << 30)) {
+            set_error("grid size %lld on axis %d out of range", (long long)g[d], d);
+            return PSOLVE_E_ARG;
+        }
+        n *= g[d];
+        if (n >= (1LL << 31)) {
+            set_error("grid has 2^31 points or more");
+            return PSOLVE_E_ARG;
+        }
+    }
+    return PSOLVE_OK;
+}
+
+psolve_status check_solve_args(double rtol, int maxit, int precond, int degree)
+{
+    if (!(rtol >= 0.0) || !std::isfinite(rtol)) {
+        set_error("rtol must be finite and >= 0");
+        return PSOLVE_E_ARG;
+    }
+    if (maxit < 0) {
+        set_error("maxit must be >= 0");
+        return PSOLVE_E_ARG;
+    }
+    if (precond < PSOLVE_PC_NONE || precond > PSOLVE_PC_GNOCOMM_CHEB) {
+        set_error("unknown preconditioner %d", precond);
+        return PSOLVE_E_ARG;
+    }
+    if (degree < 0 || degree > MAX_DEGREE) {
+        set_error("Chebyshev degree %d outside [0, %d]", degree, MAX_DEGREE);
+        return PSOLVE_E_ARG;
+    }
+    return PSOLVE_OK;
+}
+
+psolve_status check_blocks(const Problem &P, int precond)
+{
+    if (precond != PSOLVE_PC_BJ_CHEB && precond != PSOLVE_PC_GNOCOMM_CHEB) return PSOLVE_OK;
+    for (int d = 0; d < 3; ++d)
+        if (P.n[d] % P.blocks[d] != 0) {
+            set_error("blocks[%d] = %d does not divide the grid size %lld", d, P.blocks[d], (long long)P.n[d]);
+            return PSOLVE_E_ARG;
+        }
+    return PSOLVE_OK;
+}
+
+void fill_result(const Scal &s, const Problem &P, const Plan &plan, bool use_x0, bool true_res, double t0,
+                 int64_t launches, psolve_result *res)
+{
+    psolve_result r;
+    std::memset(&r, 0, sizeof r);
+    r.status = s.status;
+    r.iterations = s.iter;
+    r.half_step_exit = s.half_exit;
+    r.rel_res_recursive = s.nb2 > 0 ? std::sqrt(s.rr / s.nb2) : 0.0;
+    r.rel_res_true = !true_res ? -1.0 : (s.nb2 > 0 ? std::sqrt(s.true_rr / s.nb2) : 0.0);
+    r.seconds = now_s() - t0;
+    r.kernel_launches = launches;
+    // algorithmic bytes of the work done (dry run of the same launch sequence)
+    std::vector<LaunchRec> recs;
+    Launcher D;
+    D.dry = true;
+    D.npts = (double)P.npts();
+    D.recs = &recs;
+    D.iter = 0;
+    enqueue_init(D, use_x0);
+    for (int it = 1; it <= s.iter; ++it) {
+        D.iter = it;
+        enqueue_iteration(D, plan);
+    }
+    if (true_res) {
+        D.iter = -1;
+        enqueue_true_residual(D);
+    }
+    r.model_bytes = model_bytes_for(recs, s.iter, s.half_exit);
+    if (res) {
+        // keep timing fields the caller's run filled
+        for (int c = 0; c < PSOLVE_K_NCLASS; ++c) {
+            r.kclass_ms[c] = res->kclass_ms[c];
+            r.kclass_launches[c] = res->kclass_launches[c];
+            r.kclass_bytes[c] = res->kclass_bytes[c];
+        }
+        *res = r;
+    }
+}
+
+} // namespace
+
+// ====================================================================== ctx
+struct psolve_ctx {
+    DevInfo di;
+    cudaStream_t stream = 0;
+    cudaStream_t cap = 0;
+    psolve_opts opts;
+    Problem P;
+    Desc *d_desc = nullptr;
+    int32_t *d_list = nullptr;
+    Desc *h_desc = nullptr;
+    Scal *h_sc = nullptr; // 3 pinned slots: 2 for polling, 1 for set-up
+    cudaEvent_t poll_ev[2] = {nullptr, nullptr};
+    std::vector<GraphEntry> graphs;
+    std::vector<cudaEvent_t> events;
+    int grid = 1;
+    double *d_hb = nullptr, *d_hx = nullptr; // device copies for psolve_solve_host
+};
+
+extern "C" {
+
+void psolve_opts_default(psolve_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->lmin_scale = 1.0;
+    o->lmax_scale = 1.0;
+    o->blocks[0] = o->blocks[1] = o->blocks[2] = 1;
+    o->cheb_prec = PSOLVE_FP64;
+    o->half_step_check = 1;
+    o->use_x0 = 0;
+    o->poll_every = 0;
+    o->use_graph = 1;
+    o->timing = 0;
+    o->true_residual = 1;
+    o->rr_every = 0;
+}
+
+const char *psolve_last_error(void) { return last_error(); }
+
+const char *psolve_version(void) { return "psolve 0.1 (sm_103a, 7-point FD Poisson, Bi-CGSTAB + Chebyshev)"; }
+
+void psolve_destroy(psolve_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->di.dev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (GraphEntry &g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->poll_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->P.mem) cudaFree(c->P.mem);
+    if (c->d_desc) cudaFree(c->d_desc);
+    if (c->d_list) cudaFree(c->d_list);
+    if (c->d_hb) cudaFree(c->d_hb);
+    if (c->d_hx) cudaFree(c->d_hx);
+    if (c->h_desc) cudaFreeHost(c->h_desc);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+psolve_status psolve_create(const int64_t grid[3], const double h[3], const int32_t bc[6],
+                            const psolve_opts *opts, uintptr_t stream, psolve_ctx **out)
+{
+    clear_error();
+    if (!grid || !h || !out) {
+        set_error("null argument");
+        return PSOLVE_E_ARG;
+    }
+    psolve_status st = check_grid(grid);
+    if (st != PSOLVE_OK) return st;
+    if (!valid_h(h)) {
+        set_error("grid spacing must be finite and > 0");
+        return PSOLVE_E_ARG;
+    }
+    if (bc)
+        for (int f = 0; f < 6; ++f)
+            if (bc[f] != 0) {
+                set_error("face %d: only zero Dirichlet boundaries (0) are implemented", f);
+                return PSOLVE_E_ARG;
+            }
+    psolve_opts o;
+    psolve_opts_default(&o);
+    if (opts) o = *opts;
+    for (int d = 0; d < 3; ++d)
+        if (o.blocks[d] < 1 || o.blocks[d] > grid[d]) {
+            set_error("blocks[%d] = %d outside [1, n]", d, o.blocks[d]);
+            return PSOLVE_E_ARG;
+        }
+    if (o.cheb_prec < PSOLVE_FP64 || o.cheb_prec > PSOLVE_BF16) {
+        set_error("unknown Chebyshev precision %d", o.cheb_prec);
+        return PSOLVE_E_ARG;
+    }
+    psolve_ctx *c = new psolve_ctx();
+    c->opts = o;
+    c->stream = (cudaStream_t)stream;
+    st = device_info(&c->di);
+    if (st != PSOLVE_OK) {
+        delete c;
+        return st;
+    }
+    Problem &P = c->P;
+    for (int d = 0; d < 3; ++d) {
+        P.n[d] = grid[d];
+        P.h[d] = h[d];
+        P.blocks[d] = o.blocks[d];
+    }
+    P.prec = o.cheb_prec;
+    P.have_rt = o.use_x0 != 0;
+    problem_geometry(P, c->di.sms);
+    P.mem_bytes = problem_bytes(P.n, P.prec, P.have_rt, c->di.sms);
+#define CREATE_CK(call)                                                                          \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            set_error("%s: %s", #call, cudaGetErrorString(e_));                                  \
+            psolve_destroy(c);                                                                   \
+            return e_ == cudaErrorMemoryAllocation ? PSOLVE_E_OOM : PSOLVE_E_CUDA;               \
+        }                                                                                        \
+    } while (0)
+    CREATE_CK(cudaMalloc(&P.mem, P.mem_bytes));
+    problem_bind(P, P.mem);
+    CREATE_CK(cudaMemset(P.d_sc, 0, sizeof(Scal)));
+    CREATE_CK(cudaMalloc(&c->d_desc, sizeof(Desc)));
+    CREATE_CK(cudaMalloc(&c->d_list, 4 * sizeof(int32_t)));
+    CREATE_CK(cudaHostAlloc(&c->h_desc, sizeof(Desc), cudaHostAllocDefault));
+    CREATE_CK(cudaHostAlloc(&c->h_sc, 3 * sizeof(Scal), cudaHostAllocDefault));
+    const int32_t list[4] = {1, P.desc.units, 0, 0};
+    CREATE_CK(cudaMemcpy(c->d_list, list, sizeof list, cudaMemcpyHostToDevice));
+    CREATE_CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    for (int s = 0; s < 2; ++s) CREATE_CK(cudaEventCreateWithFlags(&c->poll_ev[s], cudaEventDisableTiming));
+#undef CREATE_CK
+    c->grid = engine_grid(c->di.sms, P.desc.units);
+    *out = c;
+    return PSOLVE_OK;
+}
+
+static psolve_status upload_desc(psolve_ctx *c)
+{
+    *c->h_desc = c->P.desc;
+    PS_CK(cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(Desc), cudaMemcpyHostToDevice, c->stream));
+    return PSOLVE_OK;
+}
+
+psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double rtol, int32_t maxit,
+                           int32_t precond, int32_t degree, psolve_result *res)
+{
+    clear_error();
+    const double t0 = now_s();
+    if (!c || !rhs || !x) {
+        set_error("null argument");
+        return PSOLVE_E_ARG;
+    }
+    psolve_status st = check_solve_args(rtol, maxit, precond, degree);
+    if (st == PSOLVE_OK) st = check_blocks(c->P, precond);
+    if (st != PSOLVE_OK) return st;
+    PS_CK(cudaSetDevice(c->di.dev));
+    Problem &P = c->P;
+    st = problem_set_cheb(P, precond, degree, c->opts.lmin_scale, c->opts.lmax_scale);
+    if (st != PSOLVE_OK) return st;
+    const bool use_x0 = c->opts.use_x0 != 0;
+    Desc &D = P.desc;
+    D.rtol = rtol;
+    D.maxit = maxit;
+    D.half_check = c->opts.half_step_check ? 1 : 0;
+    D.vec[ROLE_B] = (void *)rhs;
+    D.vec[ROLE_X] = x;
+    D.vec[ROLE_RT] = use_x0 ? P.desc.vec[ROLE_RT] : (void *)rhs;
+    if (use_x0 && !P.have_rt) {
+        set_error("use_x0 needs a context created with opts.use_x0 = 1");
+        return PSOLVE_E_ARG;
+    }
+    D.vec[ROLE_U] = D.vec[ROLE_V] = nullptr;
+    st = upload_desc(c);
+    if (st != PSOLVE_OK) return st;
+
+    Runner R;
+    R.stream = c->stream;
+    R.cap = c->cap;
+    R.d_desc = c->d_desc;
+    R.d_list = c->d_list;
+    R.grid = c->grid;
+    R.plan.precond = precond;
+    R.plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
+    R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : P.prec;
+    R.use_graph = c->opts.use_graph != 0;
+    R.timing = c->opts.timing != 0;
+    R.npts = (double)P.npts();
+    R.graphs = &c->graphs;
+    R.events = &c->events;
+    R.d_sc = P.d_sc;
+    R.nsc = 1;
+    R.h_sc[0] = c->h_sc;
+    R.h_sc[1] = c->h_sc + 1;
+    R.poll_ev[0] = c->poll_ev[0];
+    R.poll_ev[1] = c->poll_ev[1];
+    {
+        std::vector<LaunchRec> recs;
+        Launcher Dry;
+        Dry.dry = true;
+        Dry.npts = R.npts;
+        Dry.recs = &recs;
+        Dry.iter = 2;
+        enqueue_iteration(Dry, R.plan);
+        double b = 0;
+        for (const LaunchRec &r : recs) b += r.bytes;
+        R.K = c->opts.poll_every > 0 ? c->opts.poll_every : auto_poll(b, (int)recs.size());
+    }
+
+    Launcher L = R.launcher();
+    L.iter = 0;
+    enqueue_init(L, use_x0);
+    R.launches += L.launches;
+    PS_CK(L.err);
+    st = run_loop(R, maxit);
+    if (st != PSOLVE_OK) return st;
+    Scal s = R.h_sc[R.last_slot][0];
+    if (s.zero_x) PS_CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)P.npts(), c->stream));
+    const bool tr = c->opts.true_residual != 0;
+    if (tr) {
+        Launcher T = R.launcher();
+        T.iter = -1;
+        enqueue_true_residual(T);
+        R.launches += T.launches;
+        PS_CK(T.err);
+    }
+    PS_CK(cudaMemcpyAsync(c->h_sc + 2, P.d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
+    PS_CK(cudaStreamSynchronize(c->stream));
+    s = c->h_sc[2];
+    psolve_result tmp;
+    std::memset(&tmp, 0, sizeof tmp);
+    if (R.timing) fill_timing(R.recs, s.iter, s.half_exit, &tmp);
+    fill_result(s, P, R.plan, use_x0, tr, t0, R.launches, &tmp);
+    if (res) *res = tmp;
+    return (psolve_status)s.status;
+}
+
+psolve_status psolve_solve_host(psolve_ctx *c, const double *rhs_host, double *x_host, double rtol,
+                                int32_t maxit, int32_t precond, int32_t degree, psolve_result *res)
+{
+    clear_error();
+    const double t0 = now_s();
+    if (!c || !rhs_host || !x_host) {
+        set_error("null argument");
+        return PSOLVE_E_ARG;
+    }
+    PS_CK(cudaSetDevice(c->di.dev));
+    const size_t bytes = sizeof(double) * (size_t)c->P.npts();
+    if (!c->d_hb) {
+        cudaError_t e = cudaMalloc(&c->d_hb, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_hx, bytes);
+        if (e != cudaSuccess) {
+            set_error("device buffers for host solve: %s", cudaGetErrorString(e));
+            return PSOLVE_E_OOM;
+        }
+    }
+    PS_CK(cudaMemcpyAsync(c->d_hb, rhs_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (c->opts.use_x0) PS_CK(cudaMemcpyAsync(c->d_hx, x_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    psolve_result r;
+    psolve_status st = psolve_solve(c, c->d_hb, c->d_hx, rtol, maxit, precond, degree, &r);
+    if (st == PSOLVE_E_ARG || st == PSOLVE_E_CUDA || st == PSOLVE_E_OOM || st == PSOLVE_TIMEOUT) return st;
+    PS_CK(cudaMemcpyAsync(x_host, c->d_hx, bytes, cudaMemcpyDeviceToHost, c->stream));
+    PS_CK(cudaStreamSynchronize(c->stream));
+    r.seconds = now_s() - t0;
+    if (res) *res = r;
+    return st;
+}
+
+psolve_status psolve_apply_A(psolve_ctx *c, const double *u, double *out, int32_t block_restricted)
+{
+    clear_error();
+    if (!c || !u || !out) {
+        set_error("null argument");
+        return PSOLVE_E_ARG;
+    }
+    if (block_restricted) {
+        psolve_status st = check_blocks(c->P, PSOLVE_PC_BJ_CHEB);
+        if (st != PSOLVE_OK) return st;
+    }
+    PS_CK(cudaSetDevice(c->di.dev));
+    c->P.desc.vec[ROLE_U] = (void *)u;
+    c->P.desc.vec[ROLE_V] = out;
+    psolve_status st = upload_desc(c);
+    if (st != PSOLVE_OK) return st;
+    Launcher L;
+    L.stream = c->stream;
+    L.grid = c->grid;
+    L.d_desc = c->d_desc;
+    L.d_list = c->d_list;
+    enqueue_apply_A(L, block_restricted != 0);
+    PS_CK(L.err);
+    PS_CK(cudaStreamSynchronize(c->stream));
+    return PSOLVE_OK;
+}
+
+psolve_status psolve_dot(psolve_ctx *c, const double *a, const double *b, double *result_host)
+{
+    clear_error();
+    if (!c || !a || !b || !result_host) {
+        set_error("null argument");
+        return PSOLVE_E_ARG;
+    }
+    PS_CK(cudaSetDevice(c->di.dev));
+    c->P.desc.vec[ROLE_U] = (void *)a;
+    c->P.desc.vec[ROLE_V] = (void *)b;
+    psolve_status st = upload_desc(c);
+    if (st != PSOLVE_OK) return st;
+    Launcher L;
+    L.stream = c->stream;
+    L.grid = c->grid;
+    L.d_desc = c->d_desc;
+    L.d_list = c->d_list;
+    enqueue_dot(L);
+    PS_CK(L.err);
+    PS_CK(cudaMemcpyAsync(c->h_sc + 2, c->P.d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
+    PS_CK(cudaStreamSynchronize(c->stream));
+    *result_host = c->h_sc[2].red[0];
+    return PSOLVE_OK;
+}
+
+psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, int32_t precond, int32_t degree)
+{
+    clear_error();
+    if (!c || !v || !out) {
+        set_error("null argument");
+        return PSOLVE_E_ARG;
+    }
+    psolve_status st = check_solve_args(0.0, 0, precond, degree);
+    if (st != PSOLVE_OK) return st;
+    if (precond == PSOLVE_PC_NONE) {
+        set_error("psolve_precond_apply needs a Chebyshev preconditioner");
+        return PSOLVE_E_ARG;
+    }
+    st = check_blocks(c->P, precond);
+    if (st != PSOLVE_OK) return st;
+    PS_CK(cudaSetDevice(c->di.dev));
+    Problem &P = c->P;
+    st = problem_set_cheb(P, precond, degree, c->opts.lmin_scale, c->opts.lmax_scale);
+    if (st != PSOLVE_OK) return st;
+    void *saved_r = P.desc.vec[ROLE_R];
+    P.desc.vec[ROLE_R] = (void *)v;
+    P.desc.vec[ROLE_V] = out;
+    st = upload_desc(c);
+    P.desc.vec[ROLE_R] = saved_r;
+    if (st != PSOLVE_OK) return st;
+    // first-iteration state: the direction update reads v as "r" and copies it
+    Scal *init = c->h_sc + 2;
+    std::memset(init, 0, sizeof(Scal));
+    init->first = 1;
+    PS_CK(cudaMemcpyAsync(P.d_sc, init, sizeof(Scal), cudaMemcpyHostToDevice, c->stream));
+    Plan plan;
+    plan.precond = precond;
+    plan.degree = degree;
+    plan.prec = P.prec;
+    Launcher L;
+    L.stream = c->stream;
+    L.grid = c->grid;
+    L.d_desc = c->d_desc;
+    L.d_list = c->d_list;
+    enqueue_precond(L, plan);
+    PS_CK(L.err);
+    PS_CK(cudaStreamSynchronize(c->stream));
+    return PSOLVE_OK;
+}
+
+psolve_status psolve_cheb_interval(psolve_ctx *c, int32_t precond, double *a, double *b)
+{
+    clear_error();
+    if (!c || !a || !b || precond < PSOLVE_PC_CHEB || precond > PSOLVE_PC_GNOCOMM_CHEB) {
+        set_error("bad argument");
+        return PSOLVE_E_ARG;
+    }
+    psolve_status st = check_blocks(c->P, precond);
+    if (st != PSOLVE_OK) return st;
+    return cheb_interval(c->P, precond, c->opts.lmin_scale, c->opts.lmax_scale, a, b);
+}
+
+// ==================================================================== batch
+psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const double *h,
+                                 const double *const *rhs, double *const *x, double rtol, int32_t maxit,
+                                 int32_t precond, int32_t degree, const psolve_opts *opts, uintptr_t stream,
+                                 psolve_result *results)
+{
+    clear_error();
+    const double t0 = now_s();
+    if (count < 1 || !grids || !h || !rhs || !x || !results) {
+        set_error("bad argument");
+        return PSOLVE_E_ARG;
+    }
+    psolve_status st = check_solve_args(rtol, maxit, precond, degree);
+    if (st != PSOLVE_OK) return st;
+    psolve_opts o;
+    psolve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.use_x0) {
+        set_error("batched solves start from x0 = 0");
+        return PSOLVE_E_ARG;
+    }
+    if (o.cheb_prec < PSOLVE_FP64 || o.cheb_prec > PSOLVE_BF16) {
+        set_error("unknown Chebyshev precision %d", o.cheb_prec);
+        return PSOLVE_E_ARG;
+    }
+    DevInfo di;
+    st = device_info(&di);
+    if (st != PSOLVE_OK) return st;
+
+    std::vector<Problem> probs((size_t)count);
+    size_t total_bytes = 0;
+    std::vector<size_t> offs((size_t)count);
+    long long total_units = 0;
+    for (int q = 0; q < count; ++q) {
+        Problem &P = probs[q];
+        st = check_grid(grids + 3 * q);
+        if (st != PSOLVE_OK) return st;
+        if (!valid_h(h + 3 * q) || !rhs[q] || !x[q]) {
+            set_error("problem %d: bad spacing or null vector", q);
+            return PSOLVE_E_ARG;
+        }
+        for (int d = 0; d < 3; ++d) {
+            P.n[d] = grids[3 * q + d];
+            P.h[d] = h[3 * q + d];
+            P.blocks[d] = o.blocks[d];
+        }
+        P.prec = o.cheb_prec;
+        st = check_blocks(P, precond);
+        if (st != PSOLVE_OK) return st;
+        problem_geometry(P, di.sms);
+        offs[q] = total_bytes;
+        total_bytes += problem_bytes(P.n, P.prec, false, di.sms);
+        total_units += P.desc.units;
+    }
+    if (total_units >= (1LL << 31)) {
+        set_error("batch too large");
+        return PSOLVE_E_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    char *mem = nullptr;
+    Scal *d_sc = nullptr;
+    Desc *d_desc = nullptr, *h_desc = nullptr;
+    int32_t *d_list = nullptr, *h_list = nullptr;
+    Scal *h_sc = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    std::vector<GraphEntry> graphs;
+    std::vector<cudaEvent_t> events;
+    const size_t list_bytes = sizeof(int32_t) * (2 + 2 * (size_t)count);
+    auto cleanup = [&]() {
+        if (s) cudaStreamSynchronize(s);
+        for (GraphEntry &g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cap) cudaStreamDestroy(cap);
+        if (mem) cudaFree(mem);
+        if (d_sc) cudaFree(d_sc);
+        if (d_desc) cudaFree(d_desc);
+        if (d_list) cudaFree(d_list);
+        if (h_desc) cudaFreeHost(h_desc);
+        if (h_list) cudaFreeHost(h_list);
+        if (h_sc) cudaFreeHost(h_sc);
+    };
+#define BATCH_CK(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            set_error("%s: %s", #call, cudaGetErrorString(e_));                              \
+            cleanup();                                                                       \
+            return e_ == cudaErrorMemoryAllocation ? PSOLVE_E_OOM : PSOLVE_E_CUDA;           \
+        }                                                                                    \
+    } while (0)
+    BATCH_CK(cudaMalloc(&mem, total_bytes));
+    BATCH_CK(cudaMalloc(&d_sc, sizeof(Scal) * count));
+    BATCH_CK(cudaMemsetAsync(d_sc, 0, sizeof(Scal) * count, s));
+    BATCH_CK(cudaMalloc(&d_desc, sizeof(Desc) * count));
+    BATCH_CK(cudaMalloc(&d_list, list_bytes));
+    BATCH_CK(cudaHostAlloc(&h_desc, sizeof(Desc) * count, cudaHostAllocDefault));
+    BATCH_CK(cudaHostAlloc(&h_list, list_bytes, cudaHostAllocDefault));
+    BATCH_CK(cudaHostAlloc(&h_sc, 2 * sizeof(Scal) * count, cudaHostAllocDefault));
+    BATCH_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) BATCH_CK(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
+    h_list[0] = count;
+    h_list[1] = (int32_t)total_units;
+    int32_t ub = 0;
+    for (int q = 0; q < count; ++q) {
+        Problem &P = probs[q];
+        problem_bind(P, mem + offs[q]);
+        P.desc.sc = d_sc + q;
+        st = problem_set_cheb(P, precond, degree, o.lmin_scale, o.lmax_scale);
+        if (st != PSOLVE_OK) {
+            cleanup();
+            return st;
+        }
+        P.desc.rtol = rtol;
+        P.desc.maxit = maxit;
+        P.desc.half_check = o.half_step_check ? 1 : 0;
+        P.desc.vec[ROLE_B] = (void *)rhs[q];
+        P.desc.vec[ROLE_X] = x[q];
+        P.desc.vec[ROLE_RT] = (void *)rhs[q];
+        h_desc[q] = P.desc;
+        h_list[2 + 2 * q] = q;
+        h_list[3 + 2 * q] = ub;
+        ub += P.desc.units;
+    }
+    BATCH_CK(cudaMemcpyAsync(d_desc, h_desc, sizeof(Desc) * count, cudaMemcpyHostToDevice, s));
+    BATCH_CK(cudaMemcpyAsync(d_list, h_list, list_bytes, cudaMemcpyHostToDevice, s));
+
+    Runner R;
+    R.stream = s;
+    R.cap = cap;
+    R.d_desc = d_desc;
+    R.d_list = d_list;
+    R.grid = engine_grid(di.sms, total_units);
+    R.plan.precond = precond;
+    R.plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
+    R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : o.cheb_prec;
+    R.use_graph = o.use_graph != 0;
+    R.timing = o.timing != 0;
+    R.npts = 0;
+    for (const Problem &P : probs) R.npts += (double)P.npts();
+    R.graphs = &graphs;
+    R.events = &events;
+    R.d_sc = d_sc;
+    R.nsc = count;
+    R.h_sc[0] = h_sc;
+    R.h_sc[1] = h_sc + count;
+    R.poll_ev[0] = ev[0];
+    R.poll_ev[1] = ev[1];
+    R.K = o.poll_every > 0 ? o.poll_every : 4;
+
+    Launcher L = R.launcher();
+    L.iter = 0;
+    enqueue_init(L, false);
+    R.launches += L.launches;
+    BATCH_CK(L.err);
+    st = run_loop(R, maxit);
+    if (st != PSOLVE_OK) {
+        cleanup();
+        return st;
+    }
+    const bool tr = o.true_residual != 0;
+    if (tr) {
+        Launcher T = R.launcher();
+        T.iter = -1;
+        enqueue_true_residual(T);
+        R.launches += T.launches;
+        BATCH_CK(T.err);
+    }
+    BATCH_CK(cudaMemcpyAsync(h_sc, d_sc, sizeof(Scal) * count, cudaMemcpyDeviceToHost, s));
+    BATCH_CK(cudaStreamSynchronize(s));
+    psolve_status worst = PSOLVE_OK;
+    for (int q = 0; q < count; ++q) {
+        std::memset(&results[q], 0, sizeof(psolve_result));
+        fill_result(h_sc[q], probs[q], R.plan, false, tr, t0, R.launches, &results[q]);
+        if (h_sc[q].status != PSOLVE_OK && worst == PSOLVE_OK) worst = (psolve_status)h_sc[q].status;
+    }
+    if (R.timing) {
+        psolve_result tm;
+        std::memset(&tm, 0, sizeof tm);
+        fill_timing(R.recs, 1 << 30, 0, &tm);
+        for (int c = 0; c < PSOLVE_K_NCLASS; ++c) {
+            results[0].kclass_ms[c] = tm.kclass_ms[c];
+            results[0].kclass_launches[c] = tm.kclass_launches[c];
+        }
+    }
+#undef BATCH_CK
+    cleanup();
+    return worst;
+}
+
+} // extern "C"

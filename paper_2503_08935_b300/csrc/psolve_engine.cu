@@ -1,0 +1,434 @@
+// psolve_engine.cu -- kernel sequencing, workspace layout, Chebyshev set-up.
+#include "psolve_engine.cuh"
+
+namespace psolve {
+
+static thread_local std::string g_error;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+}
+void clear_error() { g_error.clear(); }
+const char *last_error() { return g_error.c_str(); }
+
+psolve_status device_info(DevInfo *out)
+{
+    int dev = 0;
+    PS_CK(cudaGetDevice(&dev));
+    int sms = 0;
+    PS_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    out->dev = dev;
+    out->sms = sms;
+    return PSOLVE_OK;
+}
+
+// ----------------------------------------------------------------- launch --
+cudaEvent_t Launcher::next_event()
+{
+    if (*event_next >= event_pool->size()) {
+        cudaEvent_t e;
+        cudaError_t st = cudaEventCreate(&e);
+        if (st != cudaSuccess) {
+            err = st;
+            return nullptr;
+        }
+        event_pool->push_back(e);
+    }
+    return (*event_pool)[(*event_next)++];
+}
+
+template <class Op>
+void Launcher::go(int cls, int side, KArgs a, double bytes_per_pt, double half_bytes_per_pt, int is_update)
+{
+    LaunchRec rec{};
+    rec.cls = cls;
+    rec.side = side;
+    rec.iter = iter;
+    rec.is_update = is_update;
+    rec.bytes = bytes_per_pt * npts;
+    rec.bytes_half = half_bytes_per_pt * npts;
+    if (dry) {
+        if (recs) recs->push_back(rec);
+        return;
+    }
+    a.descs = d_desc;
+    a.list = d_list;
+    if (timing) {
+        rec.ev0 = next_event();
+        rec.ev1 = next_event();
+        if (err != cudaSuccess) return;
+        cudaEventRecord(rec.ev0, stream);
+    }
+    k_engine<Op><<<grid, NTHREADS, 0, stream>>>(a);
+    cudaError_t st = cudaGetLastError();
+    if (st != cudaSuccess && err == cudaSuccess) err = st;
+    if (timing) cudaEventRecord(rec.ev1, stream);
+    ++launches;
+    if (recs) recs->push_back(rec);
+}
+
+int engine_grid(int sms, long long units)
+{
+    // 4 CTAs of 256 threads per SM (the kernels' launch bounds), capped by the work
+    long long g = 4LL * sms;
+    if (units < g) g = units;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// --------------------------------------------------- per-iteration kernels --
+template <class T>
+static constexpr bool is_mixed() { return !std::is_same<T, double>::value; }
+
+// Chebyshev sweeps k = 2..d (Algorithm 2 loop).  y_k overwrites y_{k-2}'s
+// buffer (read only at the same point), and the last sweep writes `final_role`.
+template <class T, class TB, bool BLK>
+static void sweeps(Launcher &L, int d, int side, int brole, int final_role, int skip)
+{
+    const double c = sizeof(T), cb = sizeof(TB);
+    for (int k = 2; k <= d; ++k) {
+        KArgs a{};
+        a.k = k;
+        a.skip = skip;
+        a.in = (k % 2 == 0) ? ROLE_YA : ROLE_YB;
+        a.z = (k % 2 == 0) ? ROLE_YB : ROLE_YA;
+        a.out = (k == d) ? final_role : a.z;
+        a.b = brole;
+        if (k == 2) L.go<OpCiSweep<T, TB, BLK>>(PSOLVE_K_CI_SWEEP3, side, a, c + cb + c);
+        else L.go<OpCiSweep<T, TB, BLK>>(PSOLVE_K_CI_SWEEP4, side, a, c + cb + c + c);
+    }
+}
+
+template <class T, bool BLK>
+static void iteration_cheb(Launcher &L, int d)
+{
+    using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
+    constexpr bool MIX = is_mixed<T>();
+    const double c = sizeof(T);
+    // p side: p_{i-1} = r + beta (p_{i-2} - omega w) fused with CI sweep 1
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_PCUR;
+        a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
+        const double rd = (L.iter == 1) ? 8.0 : 24.0;
+        L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, rd + 8.0 + (MIX ? c : 0.0) + c);
+    }
+    sweeps<T, TB, BLK>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP);
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_PH;
+        L.go<OpStencilDot<T>>(PSOLVE_K_STENCIL_DOT, 0, a, c + 16.0);
+    }
+    // s side: s = r - alpha w fused with CI sweep 1 and ||s||^2
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_S;
+        a.out = (d <= 1) ? ROLE_RH : ROLE_YA;
+        L.go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, 24.0 + (MIX ? c : 0.0) + c);
+    }
+    sweeps<T, TB, BLK>(L, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF);
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP | SKIP_HALF;
+        a.in = ROLE_RH;
+        L.go<OpStencil2Dot<T>>(PSOLVE_K_STENCIL_2DOT, 1, a, c + 16.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_PH;
+        a.aux = ROLE_RH;
+        L.go<OpUpdate<T>>(PSOLVE_K_UPDATE, 0, a, 48.0 + 2 * c, 16.0 + c, 1);
+    }
+}
+
+static void iteration_none(Launcher &L)
+{
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        L.go<OpPUpdate>(PSOLVE_K_OTHER, 0, a, L.iter == 1 ? 16.0 : 32.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_P;
+        L.go<OpStencilDot<double>>(PSOLVE_K_STENCIL_DOT, 0, a, 24.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        L.go<OpSUpdate>(PSOLVE_K_OTHER, 0, a, 24.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP | SKIP_HALF;
+        a.in = ROLE_S;
+        L.go<OpStencil2Dot<double>>(PSOLVE_K_STENCIL_2DOT, 1, a, 16.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_P;
+        a.aux = ROLE_S;
+        L.go<OpUpdate<double>>(PSOLVE_K_UPDATE, 0, a, 56.0, 24.0, 1);
+    }
+}
+
+void enqueue_iteration(Launcher &L, const Plan &plan)
+{
+    if (plan.precond == PSOLVE_PC_NONE) {
+        iteration_none(L);
+        return;
+    }
+    const bool blk = plan.precond != PSOLVE_PC_CHEB;
+    switch (plan.prec) {
+    case PSOLVE_FP32:
+        if (blk) iteration_cheb<float, true>(L, plan.degree);
+        else iteration_cheb<float, false>(L, plan.degree);
+        break;
+    case PSOLVE_BF16:
+        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree);
+        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree);
+        break;
+    default:
+        if (blk) iteration_cheb<double, true>(L, plan.degree);
+        else iteration_cheb<double, false>(L, plan.degree);
+        break;
+    }
+}
+
+void enqueue_init(Launcher &L, bool use_x0)
+{
+    KArgs a{};
+    a.skip = 0;
+    if (use_x0) L.go<OpResidual<true>>(PSOLVE_K_INIT, 0, a, 32.0);
+    else L.go<OpInit0>(PSOLVE_K_INIT, 0, a, 24.0);
+}
+
+void enqueue_true_residual(Launcher &L)
+{
+    KArgs a{};
+    a.skip = 0;
+    L.go<OpResidual<false>>(PSOLVE_K_OTHER, 0, a, 16.0);
+}
+
+// Building blocks use the same kernels as the solve.
+void enqueue_apply_A(Launcher &L, bool blocked)
+{
+    KArgs a{};
+    a.in = ROLE_U;
+    a.out = ROLE_V;
+    if (blocked) L.go<OpApplyA<true>>(PSOLVE_K_OTHER, 0, a, 16.0);
+    else L.go<OpApplyA<false>>(PSOLVE_K_OTHER, 0, a, 16.0);
+}
+
+void enqueue_dot(Launcher &L)
+{
+    KArgs a{};
+    a.in = ROLE_U;
+    a.aux = ROLE_V;
+    L.go<OpDot>(PSOLVE_K_OTHER, 0, a, 16.0);
+}
+
+// M^-1 v with the solve's own kernels: sweep 1 in its first-iteration form
+// reads v through ROLE_R (the caller points ROLE_R at v and sets first = 1,
+// iter = 0), then the sweeps, then a widening copy of p^ into ROLE_V.
+template <class T, bool BLK>
+static void precond_cheb(Launcher &L, int d)
+{
+    using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
+    constexpr bool MIX = is_mixed<T>();
+    KArgs a{};
+    a.skip = 0;
+    a.in = ROLE_PCUR;
+    a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
+    L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
+    sweeps<T, TB, BLK>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0);
+    KArgs w{};
+    w.in = ROLE_PH;
+    w.out = ROLE_V;
+    L.go<OpWiden<T>>(PSOLVE_K_OTHER, 0, w, 0.0);
+}
+
+void enqueue_precond(Launcher &L, const Plan &plan)
+{
+    const bool blk = plan.precond != PSOLVE_PC_CHEB;
+    switch (plan.prec) {
+    case PSOLVE_FP32:
+        if (blk) precond_cheb<float, true>(L, plan.degree);
+        else precond_cheb<float, false>(L, plan.degree);
+        break;
+    case PSOLVE_BF16:
+        if (blk) precond_cheb<__nv_bfloat16, true>(L, plan.degree);
+        else precond_cheb<__nv_bfloat16, false>(L, plan.degree);
+        break;
+    default:
+        if (blk) precond_cheb<double, true>(L, plan.degree);
+        else precond_cheb<double, false>(L, plan.degree);
+        break;
+    }
+}
+
+bool launch_did_work(const LaunchRec &r, int final_iter, int half_exit)
+{
+    if (r.iter > final_iter) return false;
+    if (r.iter == final_iter && half_exit && r.side == 1) return false;
+    return true;
+}
+
+double model_bytes_for(const std::vector<LaunchRec> &recs, int final_iter, int half_exit)
+{
+    double sum = 0.0;
+    for (const LaunchRec &r : recs) {
+        if (!launch_did_work(r, final_iter, half_exit)) continue;
+        if (r.iter == final_iter && half_exit && r.is_update) sum += r.bytes_half;
+        else sum += r.bytes;
+    }
+    return sum;
+}
+
+// ------------------------------------------------------------- workspace --
+static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+void problem_geometry(Problem &P, int sms)
+{
+    Desc &D = P.desc;
+    D.nx = (int)P.n[0];
+    D.ny = (int)P.n[1];
+    D.nz = (int)P.n[2];
+    D.tiles_x = ceil_div(D.nx, TILE_X);
+    D.tiles_y = ceil_div(D.ny, TILE_Y);
+    const long long tiles = (long long)D.tiles_x * D.tiles_y;
+    // Chunk length: about 6 units per CTA of a full-device launch, at most
+    // 8 planes; a function of the grid shape and the GPU only.
+    long long zc = (long long)D.nz * tiles / (6LL * 4 * sms);
+    if (zc < 1) zc = 1;
+    if (zc > 8) zc = 8;
+    D.zc = (int)zc;
+    D.nzc = ceil_div(D.nz, D.zc);
+    D.units = (int)(tiles * D.nzc);
+    D.bx = D.nx / P.blocks[0];
+    D.by = D.ny / P.blocks[1];
+    D.bz = D.nz / P.blocks[2];
+    if (D.bx < 1) D.bx = 1;
+    if (D.by < 1) D.by = 1;
+    if (D.bz < 1) D.bz = 1;
+    D.cx = 1.0 / (P.h[0] * P.h[0]);
+    D.cy = 1.0 / (P.h[1] * P.h[1]);
+    D.cz = 1.0 / (P.h[2] * P.h[2]);
+    D.cc = 2.0 * (D.cx + D.cy + D.cz);
+}
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static int units_for(const int64_t n[3], int sms)
+{
+    Problem tmp;
+    for (int d = 0; d < 3; ++d) {
+        tmp.n[d] = n[d];
+        tmp.h[d] = 1.0;
+    }
+    problem_geometry(tmp, sms);
+    return tmp.desc.units;
+}
+
+size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms)
+{
+    const size_t N = (size_t)(n[0] * n[1] * n[2]);
+    const size_t v64 = align_up(N * 8), vci = align_up(N * ci_elem_bytes(prec));
+    size_t b = v64 * (6 + (with_rt ? 1 : 0)) + vci * (4 + (prec != PSOLVE_FP64 ? 1 : 0));
+    b += align_up(sizeof(Scal)) + align_up((size_t)units_for(n, sms) * MAX_DOTS * sizeof(double));
+    return b;
+}
+
+void problem_bind(Problem &P, char *base)
+{
+    const size_t N = (size_t)P.npts();
+    const size_t v64 = align_up(N * 8), vci = align_up(N * ci_elem_bytes(P.prec));
+    char *q = base;
+    Desc &D = P.desc;
+    for (int r = 0; r < NROLES; ++r) D.vec[r] = nullptr;
+    const int f64[] = {ROLE_R, ROLE_P, ROLE_P2, ROLE_W, ROLE_S, ROLE_T};
+    for (int r : f64) {
+        D.vec[r] = q;
+        q += v64;
+    }
+    if (P.have_rt) {
+        D.vec[ROLE_RT] = q;
+        q += v64;
+    }
+    const int fci[] = {ROLE_PH, ROLE_RH, ROLE_YA, ROLE_YB};
+    for (int r : fci) {
+        D.vec[r] = q;
+        q += vci;
+    }
+    if (P.prec != PSOLVE_FP64) {
+        D.vec[ROLE_BC] = q;
+        q += vci;
+    }
+    P.d_sc = reinterpret_cast<Scal *>(q);
+    q += align_up(sizeof(Scal));
+    P.d_partials = reinterpret_cast<double *>(q);
+    D.sc = P.d_sc;
+    D.partials = P.d_partials;
+}
+
+static double mu_dirichlet(long long i, long long n)
+{
+    const double s = std::sin((double)i * M_PI / (2.0 * (double)(n + 1)));
+    return 4.0 * s * s; // Eq. 9
+}
+
+psolve_status cheb_interval(const Problem &P, int precond, double lmin_scale, double lmax_scale,
+                            double *a, double *b)
+{
+    // Eq. 10 / Eq. 11 over the whole grid (G, GNoComm) or one block (BJ)
+    double lo = 0.0, hi = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        long long m = P.n[d];
+        if (precond == PSOLVE_PC_BJ_CHEB) m = P.n[d] / P.blocks[d];
+        const double ih2 = 1.0 / (P.h[d] * P.h[d]);
+        lo += mu_dirichlet(1, m) * ih2;
+        hi += mu_dirichlet(m, m) * ih2;
+    }
+    *a = lmin_scale * lo;
+    *b = lmax_scale * hi;
+    if (!(*a > 0.0) || !(*b > *a) || !std::isfinite(*a) || !std::isfinite(*b)) {
+        set_error("empty Chebyshev interval [%g, %g] (lambda in [%g, %g], scales %g, %g)", *a, *b, lo,
+                  hi, lmin_scale, lmax_scale);
+        return PSOLVE_E_ARG;
+    }
+    return PSOLVE_OK;
+}
+
+psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_scale, double lmax_scale)
+{
+    Desc &D = P.desc;
+    D.degree = degree;
+    if (precond == PSOLVE_PC_NONE) {
+        D.theta_inv = D.two_over_delta = D.two_sigma = 0.0;
+        return PSOLVE_OK;
+    }
+    double a, b;
+    psolve_status st = cheb_interval(P, precond, lmin_scale, lmax_scale, &a, &b);
+    if (st != PSOLVE_OK) return st;
+    // Eq. 15 and the rho recurrence of Algorithm 2
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+    D.theta_inv = 1.0 / theta;
+    D.two_over_delta = 2.0 / delta;
+    D.two_sigma = 2.0 * sigma;
+    D.rho[0] = 1.0 / sigma;
+    for (int k = 1; k <= MAX_DEGREE; ++k) D.rho[k] = 1.0 / (2.0 * sigma - D.rho[k - 1]);
+    return PSOLVE_OK;
+}
+
+} // namespace psolve

@@ -1,0 +1,133 @@
+// psolve_engine.cuh -- host-side engine shared by the single-grid context, the
+// batched solve and the server: per-problem workspaces and descriptors,
+// kernel sequencing for one outer iteration and per-kernel-class accounting.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/psolve.h"
+#include "psolve_kernels.cuh"
+
+namespace psolve {
+
+// ---------------------------------------------------------------- errors --
+void set_error(const char *fmt, ...);
+void clear_error();
+const char *last_error();
+
+#define PS_CK(call)                                                                      \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            psolve::set_error("%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                              __LINE__);                                                 \
+            return PSOLVE_E_CUDA;                                                        \
+        }                                                                                \
+    } while (0)
+
+// ------------------------------------------------------------ device info --
+struct DevInfo {
+    int dev = -1;
+    int sms = 0;
+};
+psolve_status device_info(DevInfo *out);
+
+// ------------------------------------------------------------- the plan --
+// Static description of the kernels of one outer iteration.
+struct Plan {
+    int precond = PSOLVE_PC_NONE;
+    int degree = 0;
+    int prec = PSOLVE_FP64;
+    bool operator==(const Plan &o) const
+    {
+        return precond == o.precond && degree == o.degree && prec == o.prec;
+    }
+};
+
+inline size_t ci_elem_bytes(int prec) { return prec == PSOLVE_FP64 ? 8 : (prec == PSOLVE_FP32 ? 4 : 2); }
+
+// One kernel launch as the host sees it (for timing and byte accounting).
+struct LaunchRec {
+    int cls;
+    int side;          // 0: always runs; 1: skipped after a passed half-step test
+    int iter;          // outer iteration (1-based); 0 = set-up, -1 = after the loop
+    int is_update;
+    double bytes;      // algorithmic bytes if the kernel does its full work
+    double bytes_half; // update kernel after a passed half-step test
+    cudaEvent_t ev0, ev1;
+};
+
+// Issues kernels (or only records what it would issue, dry = true).
+struct Launcher {
+    cudaStream_t stream = 0;
+    int grid = 1;
+    const Desc *d_desc = nullptr;
+    const int32_t *d_list = nullptr;
+    bool dry = false;
+    bool timing = false;
+    int iter = 0;       // outer iteration being issued (byte model only)
+    int64_t launches = 0;
+    double npts = 0;    // points per problem for the byte model
+    std::vector<LaunchRec> *recs = nullptr;
+    std::vector<cudaEvent_t> *event_pool = nullptr;
+    size_t *event_next = nullptr;
+    cudaError_t err = cudaSuccess;
+
+    cudaEvent_t next_event();
+    template <class Op>
+    void go(int cls, int side, KArgs a, double bytes_per_pt, double half_bytes_per_pt = 0.0,
+            int is_update = 0);
+};
+
+// ----------------------------------------------------------- a problem --
+struct Problem {
+    int64_t n[3] = {0, 0, 0};
+    double h[3] = {0, 0, 0};
+    int blocks[3] = {1, 1, 1};
+    int prec = PSOLVE_FP64;
+    bool have_rt = false;  // r~ buffer allocated (x0 != 0 support)
+    Desc desc{};           // host copy (vec[] of b, x filled per solve)
+    char *mem = nullptr;   // one device allocation for all workspace vectors
+    size_t mem_bytes = 0;
+    Scal *d_sc = nullptr;
+    double *d_partials = nullptr;
+    int64_t npts() const { return n[0] * n[1] * n[2]; }
+};
+
+// Bytes one problem's workspace needs (vectors + partials + scalars).
+size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms);
+// Fill the geometry fields of P.desc from P.n, P.h, P.blocks.
+void problem_geometry(Problem &P, int sms);
+// Lay out P's workspace inside `base` (device, problem_bytes long).
+void problem_bind(Problem &P, char *base);
+// Chebyshev interval [a, b] (Eq. 9-11 times the scales) for precond.
+psolve_status cheb_interval(const Problem &P, int precond, double lmin_scale, double lmax_scale,
+                            double *a, double *b);
+// Chebyshev coefficients for (precond, degree) into P.desc.
+psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_scale,
+                               double lmax_scale);
+
+// Enqueue the kernels of one outer iteration for `plan`.
+void enqueue_iteration(Launcher &L, const Plan &plan);
+void enqueue_init(Launcher &L, bool use_x0);
+void enqueue_true_residual(Launcher &L);
+void enqueue_apply_A(Launcher &L, bool blocked);
+void enqueue_dot(Launcher &L);
+void enqueue_precond(Launcher &L, const Plan &plan);
+
+// Grid size (CTAs) for a launch covering `units` units.
+int engine_grid(int sms, long long units);
+
+// Algorithmic bytes of the launches in `recs` that did work, given the exit
+// iteration and whether it was a half-step exit.
+double model_bytes_for(const std::vector<LaunchRec> &recs, int final_iter, int half_exit);
+// Whether a recorded launch did work.
+bool launch_did_work(const LaunchRec &r, int final_iter, int half_exit);
+
+} // namespace psolve

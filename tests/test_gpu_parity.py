@@ -1,0 +1,366 @@
+"""GPU parity of the CUDA path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (FP64 path):
+* stencil: |A u (GPU) - A u (oracle)| <= 1e-14 * (2 cc) * max|u|, i.e. a few
+  units in the last place of the largest term (cc = 2 sum 1/h_d^2);
+* dot: |error| <= N * 2^-53 * sum|a_i b_i| (recursive-summation bound);
+* Chebyshev preconditioner: max error <= 1e-11 * max|M^-1 v| for degree <= 16
+  (the three-term recurrence is stable; errors grow ~linearly with degree);
+* solves at rtol 1e-10: relative L2 of x <= 1e-8 and iterations within +-2;
+  at a fixed iteration count (rtol = 0) the iterates agree to 1e-10, which is
+  what "the same computation" means given a condition number up to ~1e4.
+Mixed precision changes the preconditioner, so it is compared to the FP64
+oracle solution at the same rtol by relative L2 (reported, bounded loosely)
+and by the true residual.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2503_08935_b300 import binding as B
+from paper_2503_08935_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+# ragged shapes (nz, ny, nx): partial x tiles (32), partial y tiles (8), short z
+SHAPES = [(1, 1, 1), (2, 3, 5), (7, 9, 33), (19, 24, 37), (16, 16, 16), (33, 18, 5), (5, 40, 70),
+          (64, 64, 64)]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.lib()
+
+
+def stencil_tol(h, u):
+    cc = 2.0 * sum(1.0 / v ** 2 for v in h)
+    return 1e-14 * 2 * cc * max(np.max(np.abs(u)), 1e-300)
+
+
+# ---------------------------------------------------------------- stencil --
+@pytest.mark.parametrize("shape", SHAPES)
+def test_apply_A_matches_oracle(shape):
+    h = (0.7 / (shape[2] + 1), 1.3 / (shape[1] + 1), 1.0 / (shape[0] + 1))
+    u = I.rhs_uniform(shape, seed=3)
+    out = torch.empty(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h) as s:
+        s.apply_A(dev(u), out)
+    ref = O.apply_A(u, h)
+    assert np.max(np.abs(host(out) - ref)) <= stencil_tol(h, u)
+
+
+@pytest.mark.parametrize("shape,blocks", [((8, 6, 4), (2, 3, 2)), ((16, 24, 40), (5, 3, 4)),
+                                          ((32, 32, 64), (4, 4, 2)), ((9, 9, 9), (3, 3, 3)),
+                                          ((4, 4, 4), (4, 4, 4))])
+def test_block_restricted_apply_A_matches_oracle(shape, blocks):
+    h = I.default_h(shape)
+    u = I.rhs_uniform(shape, seed=4)
+    out = torch.empty(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h, blocks=blocks) as s:
+        s.apply_A(dev(u), out, block_restricted=True)
+    ref = O.apply_A(u, h, blocks)
+    assert np.max(np.abs(host(out) - ref)) <= stencil_tol(h, u)
+
+
+def test_apply_A_full_size_256():
+    shape = (256, 256, 256)
+    h = I.default_h(shape)
+    u = I.rhs_uniform(shape, seed=1)
+    out = torch.empty(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h) as s:
+        s.apply_A(dev(u), out)
+    ref = O.apply_A(u, h)
+    assert np.max(np.abs(host(out) - ref)) <= stencil_tol(h, u)
+
+
+# -------------------------------------------------------------------- dot --
+@pytest.mark.parametrize("shape", [(1, 1, 1), (19, 24, 37), (64, 64, 64), (128, 128, 130)])
+def test_dot_matches_oracle(shape):
+    a = I.rhs_uniform(shape, seed=5)
+    b = I.rhs_uniform(shape, seed=6)
+    with B.Solver(shape) as s:
+        got = s.dot(dev(a), dev(b))
+    ref = O.dot(a, b)
+    n = a.size
+    assert abs(got - ref) <= n * 2.0 ** -53 * float(np.sum(np.abs(a * b)))
+
+
+def test_dot_is_deterministic():
+    shape = (40, 50, 60)
+    a, b = dev(I.rhs_uniform(shape, seed=7)), dev(I.rhs_uniform(shape, seed=8))
+    with B.Solver(shape) as s:
+        vals = {s.dot(a, b) for _ in range(5)}
+    assert len(vals) == 1
+
+
+# ---------------------------------------------------------- preconditioner --
+@pytest.mark.parametrize("precond,blocks", [(B.PC_CHEB, (1, 1, 1)), (B.PC_BJ_CHEB, (2, 3, 1)),
+                                            (B.PC_GNOCOMM_CHEB, (2, 3, 1))])
+@pytest.mark.parametrize("degree", [0, 1, 2, 3, 8, 16])
+def test_precond_fp64_matches_oracle(precond, blocks, degree):
+    shape = (20, 24, 38)
+    h = I.default_h(shape)
+    v = I.rhs_uniform(shape, seed=9)
+    out = torch.empty(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h, blocks=blocks) as s:
+        s.precond_apply(dev(v), out, precond, degree)
+    ref = O.precond_apply(v, h, precond, degree, blocks)
+    assert np.max(np.abs(host(out) - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec,tol", [(B.FP32, 2e-5), (B.BF16, 3e-2)])
+@pytest.mark.parametrize("degree", [1, 4, 8])
+def test_precond_mixed_close_to_oracle(prec, tol, degree):
+    shape = (24, 24, 40)
+    h = I.default_h(shape)
+    v = I.rhs_uniform(shape, seed=10)
+    out = torch.empty(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h, cheb_prec=prec) as s:
+        s.precond_apply(dev(v), out, B.PC_CHEB, degree)
+    ref = O.precond_apply(v, h, O.PC_CHEB, degree)
+    assert rel(host(out), ref) <= tol
+
+
+def test_cheb_interval_matches_oracle():
+    shape = (20, 24, 36)
+    h = (0.05, 0.04, 0.03)
+    with B.Solver(shape, h, blocks=(3, 2, 4), lmin_scale=2.0, lmax_scale=0.9) as s:
+        for pc in (B.PC_CHEB, B.PC_BJ_CHEB, B.PC_GNOCOMM_CHEB):
+            a, b = s.cheb_interval(pc)
+            ra, rb = O.cheb_interval(shape, h, pc, (3, 2, 4), 2.0, 0.9)
+            assert abs(a - ra) <= 1e-13 * rb and abs(b - rb) <= 1e-13 * rb
+
+
+# ------------------------------------------------------------------ solves --
+SOLVE_CASES = [
+    # (shape, precond, degree, blocks, scales)
+    ((24, 20, 36), B.PC_NONE, 0, (1, 1, 1), (1.0, 1.0)),
+    ((24, 20, 36), B.PC_CHEB, 4, (1, 1, 1), (1.0, 1.0)),
+    ((24, 20, 36), B.PC_CHEB, 8, (1, 1, 1), (1.0, 1.0)),
+    ((24, 20, 36), B.PC_CHEB, 0, (1, 1, 1), (1.0, 1.0)),
+    ((24, 20, 36), B.PC_CHEB, 1, (1, 1, 1), (1.0, 1.0)),
+    ((24, 20, 36), B.PC_BJ_CHEB, 3, (2, 2, 2), (1.0, 1.0)),
+    ((24, 20, 36), B.PC_GNOCOMM_CHEB, 4, (2, 2, 3), (1.0, 1.0)),
+    ((33, 17, 45), B.PC_CHEB, 5, (1, 1, 1), (3.0, 1.0 - 1e-4)),
+    ((40, 40, 40), B.PC_GNOCOMM_CHEB, 8, (2, 2, 2), (10.0, 1.0 - 1e-4)),
+    ((1, 7, 1), B.PC_CHEB, 2, (1, 1, 1), (1.0, 1.0)),
+]
+
+
+def _solve_both(shape, precond, degree, blocks, scales, rtol=1e-10, maxit=500, x0=None, **opt_kw):
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=11)
+    x = dev(x0) if x0 is not None else torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h, blocks=blocks, lmin_scale=scales[0], lmax_scale=scales[1],
+                  use_x0=1 if x0 is not None else 0, **opt_kw) as s:
+        info = s.solve(dev(b), x, rtol=rtol, maxit=maxit, precond=precond, degree=degree)
+    xo, ro = O.bicgstab(b, h, rtol=rtol, maxit=maxit, precond=precond, degree=degree, blocks=blocks,
+                        lmin_scale=scales[0], lmax_scale=scales[1], x0=x0)
+    return host(x), info, xo, ro
+
+
+@pytest.mark.parametrize("case", SOLVE_CASES)
+def test_solve_matches_oracle(case):
+    x, info, xo, ro = _solve_both(*case)
+    assert info.status == B.OK and ro.status == O.OK
+    assert abs(info.iterations - ro.iterations) <= 2
+    assert rel(x, xo) <= 1e-8
+    assert info.rel_res_recursive <= 1e-10 and info.rel_res_true <= 2e-10
+    assert abs(info.rel_res_true - info.rel_res_recursive) <= 0.1 * 1e-10
+
+
+@pytest.mark.parametrize("case", SOLVE_CASES[:8])
+def test_fixed_iterations_match_oracle(case):
+    """rtol = 0: both sides run exactly maxit iterations of the same recurrence."""
+    x, info, xo, ro = _solve_both(*case, rtol=0.0, maxit=4)
+    assert info.status == B.NOT_CONVERGED and info.iterations == 4 == ro.iterations
+    assert rel(x, xo) <= 1e-10
+
+
+def test_solve_with_initial_guess():
+    shape = (18, 21, 34)
+    x0 = I.rhs_uniform(shape, seed=12)
+    x, info, xo, ro = _solve_both(shape, B.PC_CHEB, 4, (1, 1, 1), (1.0, 1.0), x0=x0)
+    assert info.status == B.OK and abs(info.iterations - ro.iterations) <= 2
+    assert rel(x, xo) <= 1e-8
+
+
+def test_config_32cubed_manufactured_half_step():
+    """32^3, h = 1/33, f = 3 pi^2 sin sin sin, no preconditioner: the RHS is a
+    discrete eigenvector, so the first half step converges; x = f / lambda_111."""
+    shape = (32, 32, 32)
+    h = I.default_h(shape)
+    f = I.rhs_manufactured(shape)
+    x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h) as s:
+        info = s.solve(dev(f), x, rtol=1e-10, maxit=2000, precond=B.PC_NONE)
+    lam111 = 3 * 4.0 / h[0] ** 2 * math.sin(math.pi * h[0] / 2) ** 2
+    assert info.status == B.OK and info.iterations == 1 and info.half_step_exit
+    assert rel(host(x), f / lam111) <= 1e-12
+
+
+def test_graph_eager_and_timing_are_bitwise_equal():
+    shape = (30, 26, 44)
+    h = I.default_h(shape)
+    b = dev(I.rhs_uniform(shape, seed=13))
+    outs = []
+    for kw in (dict(use_graph=1), dict(use_graph=0), dict(timing=1), dict(poll_every=3)):
+        x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+        with B.Solver(shape, h, **kw) as s:
+            info = s.solve(b, x, rtol=1e-10, maxit=300, precond=B.PC_CHEB, degree=6)
+        outs.append((host(x), info))
+    for x, info in outs[1:]:
+        assert np.array_equal(x, outs[0][0]) and info.iterations == outs[0][1].iterations
+    tm = outs[2][1].kclass
+    assert tm["ci_sweep4"]["launches"] > 0 and tm["ci_sweep4"]["ms"] > 0
+    assert tm["stencil_dot"]["launches"] == outs[2][1].iterations
+
+
+def test_solve_host_equals_device_solve():
+    shape = (20, 22, 24)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=14)
+    x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    xh = torch.zeros(shape, dtype=torch.float64).pin_memory()
+    bh = torch.from_numpy(b).pin_memory()
+    with B.Solver(shape, h) as s:
+        i1 = s.solve(dev(b), x, rtol=1e-10, maxit=300, precond=B.PC_CHEB, degree=4)
+        i2 = s.solve_host(bh, xh, rtol=1e-10, maxit=300, precond=B.PC_CHEB, degree=4)
+    assert i1.iterations == i2.iterations and np.array_equal(host(x), xh.numpy())
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.BF16])
+def test_mixed_precision_reaches_rtol(prec):
+    """Both sides stop at ||r||/||b|| <= 1e-10; their solutions may differ by up to
+    kappa * 1e-10 (kappa ~ 700 here), so the bound on x is 1e-7."""
+    shape = (32, 30, 40)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=15)
+    x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h, cheb_prec=prec) as s:
+        info = s.solve(dev(b), x, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8)
+    xo, ro = O.bicgstab(b, h, rtol=1e-10, maxit=500, precond=O.PC_CHEB, degree=8)
+    assert info.status == B.OK and info.rel_res_true <= 2e-10
+    assert rel(host(x), xo) <= 1e-7
+
+
+# ------------------------------------------------------------- edge cases --
+def test_zero_rhs():
+    shape = (8, 9, 10)
+    x = torch.ones(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape) as s:
+        info = s.solve(torch.zeros(shape, dtype=torch.float64, device=DEV), x, precond=B.PC_CHEB, degree=3)
+    assert info.status == B.OK and info.iterations == 0 and not host(x).any()
+
+
+def test_zero_rhs_with_initial_guess_returns_zero():
+    shape = (8, 9, 10)
+    x = torch.ones(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, use_x0=1) as s:
+        info = s.solve(torch.zeros(shape, dtype=torch.float64, device=DEV), x, precond=B.PC_CHEB, degree=3)
+    assert info.status == B.OK and info.iterations == 0 and not host(x).any()
+
+
+def test_nonfinite_rhs():
+    shape = (8, 9, 10)
+    b = I.rhs_uniform(shape)
+    b[3, 4, 5] = np.inf
+    x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape) as s:
+        info = s.solve(dev(b), x, precond=B.PC_CHEB, degree=3)
+    assert info.status == B.NONFINITE
+
+
+def test_maxit_and_zero_maxit():
+    shape = (16, 16, 16)
+    b = dev(I.rhs_uniform(shape))
+    with B.Solver(shape) as s:
+        x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+        assert s.solve(b, x, rtol=1e-14, maxit=0, precond=B.PC_CHEB, degree=2).status == B.NOT_CONVERGED
+        info = s.solve(b, x, rtol=1e-14, maxit=2, precond=B.PC_CHEB, degree=2)
+        assert info.status == B.NOT_CONVERGED and info.iterations == 2
+
+
+def test_argument_errors():
+    shape = (10, 12, 14)
+    b = dev(I.rhs_uniform(shape))
+    x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, blocks=(3, 1, 1)) as s:
+        with pytest.raises(B.PsolveError):  # 3 blocks do not divide nx = 14
+            s.solve(b, x, precond=B.PC_BJ_CHEB, degree=2)
+        with pytest.raises(B.PsolveError):
+            s.solve(b, x, precond=B.PC_CHEB, degree=65)
+        with pytest.raises(B.PsolveError):
+            s.solve(b, x, rtol=-1.0)
+    with B.Solver((4, 4, 4), lmin_scale=100.0, lmax_scale=1 - 1e-4) as s:
+        with pytest.raises(B.PsolveError):  # empty interval on a tiny grid
+            s.solve(torch.ones((4, 4, 4), dtype=torch.float64, device=DEV),
+                    torch.zeros((4, 4, 4), dtype=torch.float64, device=DEV), precond=B.PC_CHEB, degree=2)
+
+
+def test_repeated_solves_reuse_context():
+    shape = (20, 20, 20)
+    h = I.default_h(shape)
+    with B.Solver(shape, h) as s:
+        res = []
+        for seed in (1, 2, 1):
+            x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+            s.solve(dev(I.rhs_uniform(shape, seed=seed)), x, precond=B.PC_CHEB, degree=4)
+            res.append(host(x))
+    assert np.array_equal(res[0], res[2]) and not np.array_equal(res[0], res[1])
+
+
+# ------------------------------------------------------------------ batch --
+def test_batch_bitwise_equals_alone_and_matches_oracle():
+    shapes = [(16, 24, 40), (32, 16, 16), (9, 33, 17), (24, 24, 24), (8, 8, 64)]
+    bs = [I.rhs_uniform(sh, seed=20 + q) for q, sh in enumerate(shapes)]
+    xs = [torch.zeros(sh, dtype=torch.float64, device=DEV) for sh in shapes]
+    infos = B.solve_batch([dev(b) for b in bs], xs, rtol=1e-10, maxit=300, precond=B.PC_CHEB, degree=4)
+    for q, sh in enumerate(shapes):
+        xa = torch.zeros(sh, dtype=torch.float64, device=DEV)
+        with B.Solver(sh) as s:
+            ia = s.solve(dev(bs[q]), xa, rtol=1e-10, maxit=300, precond=B.PC_CHEB, degree=4)
+        assert infos[q].status == B.OK and infos[q].iterations == ia.iterations
+        assert np.array_equal(host(xs[q]), host(xa))
+        xo, ro = O.bicgstab(bs[q], I.default_h(sh), rtol=1e-10, maxit=300, precond=O.PC_CHEB, degree=4)
+        assert rel(host(xs[q]), xo) <= 1e-8 and abs(ro.iterations - ia.iterations) <= 2
+
+
+# ------------------------------------------------------ full-size configs --
+def test_full_size_256_cheb8_fixed_iterations_and_residual():
+    """256^3, Chebyshev degree 8, in the benchmark's launch configuration:
+    two fixed iterations against the oracle, then a full solve whose true and
+    recursive residuals must agree."""
+    shape = (256, 256, 256)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=1)
+    bt = dev(b)
+    x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h) as s:
+        info = s.solve(bt, x, rtol=0.0, maxit=2, precond=B.PC_CHEB, degree=8)
+        assert info.iterations == 2
+        xo, ro = O.bicgstab(b, h, rtol=0.0, maxit=2, precond=O.PC_CHEB, degree=8)
+        assert rel(host(x), xo) <= 1e-10
+        info = s.solve(bt, x, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8)
+    assert info.status == B.OK
+    assert info.rel_res_true <= 2e-10 and abs(info.rel_res_true - info.rel_res_recursive) <= 1e-11
