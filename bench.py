@@ -1,0 +1,353 @@
+"""Benchmark: 256^3 Poisson solve, Bi-CGSTAB with the Chebyshev preconditioner.
+
+One step = one complete solve of the 256^3 problem (h = 1/257, zero Dirichlet,
+b ~ U[-1, 1) splitmix64 seed 1, x0 = 0, G(CI) degree 8 with exact closed-form
+eigenvalue bounds, FP64, rtol 1e-10): every row of the hot path (initial
+residual, fused direction update + Chebyshev sweep 1, sweeps 2..8, stencil +
+dot, half-step update + sweeps, stencil + 2 dots, x/r update + 2 dots, true
+residual) runs in the library's CUDA kernels.  `value` is solves per second
+with b resident in HBM; `e2e` is the same through psolve_solve_host with the
+host->device copy of b and the device->host copy of x inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With torchrun (N > 1) every rank solves its own replica (no collective on the
+data path: the solve does not shard without a halo exchange), timing is the
+max over ranks and `value` is the total solves/s.  `--impl reference` times
+the FP64 CPU oracle on this host on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "256³ time-to-rtol 1e-10 & HBM GB/s; batched solves/s; p50/p99 serve latency"
+SHAPE = (256, 256, 256)
+RTOL = 1e-10
+MAXIT = 500
+DEGREE = 8
+WORKLOAD = "poisson 256^3 FP64, Bi-CGSTAB + G(CI) Chebyshev degree 8, exact bounds, rtol 1e-10"
+GOLDEN_256 = os.path.join(ROOT, "tests", "golden", "oracle_256_cheb8.json")
+NCU_SUMMARY = os.path.join(ROOT, "profiles", "ncu_ci_sweep4_256.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2503_08935_b300", "csrc", "psolve_kernels.cuh")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic_per_point():
+    """DRAM bytes per grid point of one ci_sweep4 launch from the committed ncu
+    summary, or None if there is none or the kernel source changed since."""
+    try:
+        txt = open(NCU_SUMMARY).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_point"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/psolve_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][2]),
+                "power_w_max": max(power) if power else None, "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------- reference --
+def oracle_sample(shape=SHAPE):
+    """Bounded oracle sample on the full problem: the oracle's solve with
+    maxit = 0 (set-up + true residual) and maxit = 1 (one more outer
+    iteration).  Returns (t_setup, t_iteration) in seconds."""
+    import oracle as O
+    from paper_2503_08935_b300 import inputs as I
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=1)
+    t = time.perf_counter()
+    O.bicgstab(b, h, rtol=0.0, maxit=0, precond=O.PC_CHEB, degree=DEGREE)
+    t0 = time.perf_counter() - t
+    t = time.perf_counter()
+    O.bicgstab(b, h, rtol=0.0, maxit=1, precond=O.PC_CHEB, degree=DEGREE)
+    t1 = time.perf_counter() - t
+    return t0, max(t1 - t0, 1e-9)
+
+
+def oracle_iterations(default):
+    try:
+        with open(GOLDEN_256) as f:
+            return int(json.load(f)["iterations"]), "stored oracle run (tests/golden/oracle_256_cheb8.json)"
+    except Exception:
+        return default, "iteration count of the GPU solve"
+
+
+def cpu_baseline_record(iters_gpu):
+    t_setup, t_iter = oracle_sample()
+    iters, src = oracle_iterations(iters_gpu)
+    t_solve = t_setup + iters * t_iter
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"serial FP64 oracle on the full 256^3 problem: set-up + true residual "
+                       f"({t_setup:.2f} s) and one outer iteration ({t_iter:.2f} s), timed on this host; "
+                       f"a solve is extrapolated as set-up + {iters} iterations ({src})"),
+            "seconds_per_solve_extrapolated": t_solve}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    # warm-up steps on a small sample (code and page cache), timed steps on the full problem
+    for _ in range(args.warmup):
+        oracle_sample((64, 64, 64))
+    times = []
+    iters, src = oracle_iterations(30)
+    for _ in range(args.steps):
+        t_setup, t_iter = oracle_sample()
+        times.append(t_setup + iters * t_iter)
+    t = statistics.mean(times)
+    value = 1.0 / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "256x256x256", "h": "1/257", "rhs": "U[-1,1) splitmix64 seed 1",
+                   "precond": "G(CI) degree 8, bounds (1,1)", "rtol": RTOL},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": (f"each step: serial FP64 oracle, set-up + one outer iteration on the full "
+                                    f"256^3 problem, extrapolated to set-up + {iters} iterations ({src})")},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU --
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2503_08935_b300 import binding as B
+    from paper_2503_08935_b300 import inputs as I
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    h = I.default_h(SHAPE)
+    b_host = torch.from_numpy(I.rhs_uniform(SHAPE, seed=1)).pin_memory()
+    b = b_host.to(dev)
+    x = torch.zeros(SHAPE, dtype=torch.float64, device=dev)
+    x_host = torch.empty(SHAPE, dtype=torch.float64).pin_memory()
+    npts = b.numel()
+
+    solver = B.Solver(SHAPE, h, timing=1 if args.kernel_timing else 0, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    def timed(fn, steps):
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        infos = [fn() for _ in range(steps)]
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos
+
+    def solve_dev():
+        info = solver.solve(b, x, rtol=RTOL, maxit=MAXIT, precond=B.PC_CHEB, degree=DEGREE)
+        if info.status != B.OK:
+            raise RuntimeError(f"solve status {info.status_name}")
+        return info
+
+    def solve_e2e():
+        info = solver.solve_host(b_host, x_host, rtol=RTOL, maxit=MAXIT, precond=B.PC_CHEB, degree=DEGREE)
+        if info.status != B.OK:
+            raise RuntimeError(f"solve status {info.status_name}")
+        return info
+
+    for _ in range(args.warmup):
+        solve_dev()
+    with ClockSampler(dev.index) as clk:
+        ms, infos = timed(solve_dev, args.steps)
+    clocks = clk.summary()
+    for _ in range(max(1, args.warmup // 2)):
+        solve_e2e()
+    ms_e2e, infos_e2e = timed(solve_e2e, args.steps)
+
+    per_step = ms / args.steps
+    value = world * 1e3 / per_step
+    iters = infos[-1].iterations
+    model_bytes = statistics.mean(i.model_bytes for i in infos)
+    launches = sum(i.kernel_launches for i in infos)
+
+    # dominant kernel: Chebyshev sweep k >= 3 (reads y_{k-1}, b, y_{k-2}; writes y_k)
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if args.kernel_timing:
+        k = "ci_sweep4"
+        kms = sum(i.kclass[k]["ms"] for i in infos)
+        kn = sum(i.kclass[k]["launches"] for i in infos)
+        kbytes = sum(i.kclass[k]["bytes"] for i in infos)
+        avg_ms = kms / max(kn, 1)
+        per_launch = kbytes / max(kn, 1)
+        achieved = per_launch / (avg_ms * 1e-3) / 1e9
+        tpp = ncu_traffic_per_point()
+        roof = {"bound": "hbm", "kernel": "k_engine<OpCiSweep<double,double,false>> (CI sweep k>=3)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy test)",
+                "traffic": (tpp * npts) if tpp is not None else None,
+                "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms, "launches": kn,
+                "share_of_step": kms / ms if ms > 0 else None}
+        breakdown = {}
+        for name in B.K_NAMES:
+            kms_c = sum(i.kclass[name]["ms"] for i in infos)
+            kb_c = sum(i.kclass[name]["bytes"] for i in infos)
+            kn_c = sum(i.kclass[name]["launches"] for i in infos)
+            if kn_c:
+                breakdown[name] = {"ms_per_step": kms_c / args.steps, "launches_per_step": kn_c / args.steps,
+                                   "GB/s": kb_c / (kms_c * 1e-3) / 1e9 if kms_c > 0 else None}
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "256x256x256", "h": "1/257",
+                   "rhs": "U[-1,1) splitmix64 seed 1", "precond": "G(CI) degree 8, bounds (1,1)", "rtol": RTOL,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2: ~10 FP64 vectors of 134 MB each"},
+        "iterations": iters, "time_to_rtol_ms": per_step,
+        "hbm_gbs_solve": model_bytes / (per_step * 1e-3) / 1e9,
+        "model_bytes_per_solve": model_bytes,
+        "rel_res_true": infos[-1].rel_res_true,
+        "roofline": roof,
+        "e2e": {"value": world * 1e3 * args.steps / ms_e2e, "unit": "solves/s",
+                "h2d_bytes_per_step": 8 * npts, "d2h_bytes_per_step": 8 * npts,
+                "ms_per_step": ms_e2e / args.steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "kernel_timing": "CUDA events around every kernel launch (plain launches)" if args.kernel_timing
+        else "off (CUDA-graph replay)",
+    }
+    if roof is not None:
+        line["kernel_breakdown"] = breakdown
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_record(iters)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel-timing", type=int, default=1,
+                    help="1: plain launches with CUDA events per kernel (roofline); 0: graph replay")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -97,11 +97,16 @@ typedef struct {
     int32_t true_residual;   /* 1: recompute ||b - A x||/||b|| at exit        */
     int32_t rr_every;        /* mixed precision: replace r by b - A x every
                                 rr_every iterations (0 = never)              */
-    int32_t reserved[5];
+    int32_t engine;          /* stencil kernels: 0 = TMA ring where possible
+                                (nx % 8 == 0, 16-byte aligned vectors), else
+                                the general engine; 1 = always the general
+                                engine (no tensor copies)                     */
+    int32_t reserved[4];
 } psolve_opts;
 
 /* Fill *o with the defaults: scales 1, 1; blocks 1,1,1; FP64; half-step check
- * on; x0 = 0; poll auto; graphs on; timing off; true residual on; rr off. */
+ * on; x0 = 0; poll auto; graphs on; timing off; true residual on; rr off;
+ * engine auto. */
 PSOLVE_API void psolve_opts_default(psolve_opts *o);
 
 /* Kernel classes reported by timing mode (psolve_result.kclass_*). */
@@ -122,7 +127,7 @@ typedef struct {
     int32_t status;            /* psolve_status of the solve                   */
     int32_t iterations;        /* outer index i at exit (0 if r0 passes)       */
     int32_t half_step_exit;    /* 1 if the exit was the ||s|| half-step test   */
-    int32_t pad_;
+    int32_t engine;            /* stencil engine used: 1 TMA ring, 0 general   */
     double rel_res_recursive;  /* ||r||/||b|| of the recursive residual        */
     double rel_res_true;       /* ||b - A x||/||b|| at exit (if enabled)       */
     double seconds;            /* wall time of the call                        */

@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
         ("timing", ctypes.c_int32),
         ("true_residual", ctypes.c_int32),
         ("rr_every", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("engine", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -56,7 +57,7 @@ class Result(ctypes.Structure):
         ("status", ctypes.c_int32),
         ("iterations", ctypes.c_int32),
         ("half_step_exit", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("engine", ctypes.c_int32),
         ("rel_res_recursive", ctypes.c_double),
         ("rel_res_true", ctypes.c_double),
         ("seconds", ctypes.c_double),
@@ -68,7 +69,7 @@ class Result(ctypes.Structure):
     ]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad_", "kclass_ms", "kclass_launches",
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("kclass_ms", "kclass_launches",
                                                                         "kclass_bytes")}
         d["status_name"] = STATUS_NAMES[self.status] if 0 <= self.status < len(STATUS_NAMES) else "?"
         d["kclass"] = {K_NAMES[c]: {"ms": self.kclass_ms[c], "launches": self.kclass_launches[c],
@@ -175,6 +176,7 @@ class SolveInfo:
     model_bytes: float
     kernel_launches: int
     kclass: dict
+    engine: int = 0
 
     @property
     def status_name(self):
@@ -184,7 +186,7 @@ class SolveInfo:
 def _info(r: Result) -> SolveInfo:
     d = r.as_dict()
     return SolveInfo(r.status, r.iterations, bool(r.half_step_exit), r.rel_res_recursive, r.rel_res_true,
-                     r.seconds, r.model_bytes, r.kernel_launches, d["kclass"])
+                     r.seconds, r.model_bytes, r.kernel_launches, d["kclass"], r.engine)
 
 
 class Solver:

@@ -36,7 +36,8 @@ struct Runner {
     cudaStream_t stream = 0, cap = 0;
     const Desc *d_desc = nullptr;
     const int32_t *d_list = nullptr;
-    int grid = 1;
+    int sms = 1;
+    long long units = 1;
     Plan plan;
     int K = 1;
     bool use_graph = true;
@@ -58,7 +59,8 @@ struct Runner {
     {
         Launcher L;
         L.stream = stream;
-        L.grid = grid;
+        L.sms = sms;
+        L.units = units;
         L.d_desc = d_desc;
         L.d_list = d_list;
         L.timing = timing;
@@ -79,10 +81,18 @@ psolve_status get_graph(Runner &R, int k, GraphEntry **out)
         }
     Launcher C;
     C.stream = R.cap;
-    C.grid = R.grid;
+    C.sms = R.sms;
+    C.units = R.units;
     C.d_desc = R.d_desc;
     C.d_list = R.d_list;
     C.iter = 2;
+    {
+        // kernel attributes are set outside the capture
+        Launcher cfg = C;
+        cfg.configure = true;
+        enqueue_iteration(cfg, R.plan);
+        PS_CK(cfg.err);
+    }
     PS_CK(cudaStreamBeginCapture(R.cap, cudaStreamCaptureModeThreadLocal));
     for (int j = 0; j < k; ++j) enqueue_iteration(C, R.plan);
     cudaGraph_t g = nullptr;
@@ -248,6 +258,7 @@ void fill_result(const Scal &s, const Problem &P, const Plan &plan, bool use_x0,
     r.status = s.status;
     r.iterations = s.iter;
     r.half_step_exit = s.half_exit;
+    r.engine = P.desc.tma;
     r.rel_res_recursive = s.nb2 > 0 ? std::sqrt(s.rr / s.nb2) : 0.0;
     r.rel_res_true = !true_res ? -1.0 : (s.nb2 > 0 ? std::sqrt(s.true_rr / s.nb2) : 0.0);
     r.seconds = now_s() - t0;
@@ -292,11 +303,11 @@ struct psolve_ctx {
     Desc *d_desc = nullptr;
     int32_t *d_list = nullptr;
     Desc *h_desc = nullptr;
+    CUtensorMap *d_tmap = nullptr, *h_tmap = nullptr; // TMA descriptors of the workspace roles
     Scal *h_sc = nullptr; // 3 pinned slots: 2 for polling, 1 for set-up
     cudaEvent_t poll_ev[2] = {nullptr, nullptr};
     std::vector<GraphEntry> graphs;
     std::vector<cudaEvent_t> events;
-    int grid = 1;
     double *d_hb = nullptr, *d_hx = nullptr; // device copies for psolve_solve_host
 };
 
@@ -339,6 +350,8 @@ void psolve_destroy(psolve_ctx *c)
     if (c->d_hb) cudaFree(c->d_hb);
     if (c->d_hx) cudaFree(c->d_hx);
     if (c->h_desc) cudaFreeHost(c->h_desc);
+    if (c->d_tmap) cudaFree(c->d_tmap);
+    if (c->h_tmap) cudaFreeHost(c->h_tmap);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
@@ -410,21 +423,38 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
     CREATE_CK(cudaMalloc(&c->d_list, 4 * sizeof(int32_t)));
     CREATE_CK(cudaHostAlloc(&c->h_desc, sizeof(Desc), cudaHostAllocDefault));
     CREATE_CK(cudaHostAlloc(&c->h_sc, 3 * sizeof(Scal), cudaHostAllocDefault));
+    CREATE_CK(cudaMalloc(&c->d_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM));
+    CREATE_CK(cudaHostAlloc(&c->h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM, cudaHostAllocDefault));
+    P.desc.tmap = c->d_tmap;
     const int32_t list[4] = {1, P.desc.units, 0, 0};
     CREATE_CK(cudaMemcpy(c->d_list, list, sizeof list, cudaMemcpyHostToDevice));
     CREATE_CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     for (int s = 0; s < 2; ++s) CREATE_CK(cudaEventCreateWithFlags(&c->poll_ev[s], cudaEventDisableTiming));
 #undef CREATE_CK
-    c->grid = engine_grid(c->di.sms, P.desc.units);
     *out = c;
     return PSOLVE_OK;
 }
 
 static psolve_status upload_desc(psolve_ctx *c)
 {
+    problem_encode_tmaps(c->P, c->h_tmap, c->opts.engine != 1);
     *c->h_desc = c->P.desc;
+    if (c->P.desc.tma)
+        PS_CK(cudaMemcpyAsync(c->d_tmap, c->h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM,
+                              cudaMemcpyHostToDevice, c->stream));
     PS_CK(cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(Desc), cudaMemcpyHostToDevice, c->stream));
     return PSOLVE_OK;
+}
+
+static Launcher ctx_launcher(psolve_ctx *c)
+{
+    Launcher L;
+    L.stream = c->stream;
+    L.sms = c->di.sms;
+    L.units = c->P.desc.units;
+    L.d_desc = c->d_desc;
+    L.d_list = c->d_list;
+    return L;
 }
 
 psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double rtol, int32_t maxit,
@@ -464,7 +494,8 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     R.cap = c->cap;
     R.d_desc = c->d_desc;
     R.d_list = c->d_list;
-    R.grid = c->grid;
+    R.sms = c->di.sms;
+    R.units = P.desc.units;
     R.plan.precond = precond;
     R.plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
     R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : P.prec;
@@ -567,11 +598,7 @@ psolve_status psolve_apply_A(psolve_ctx *c, const double *u, double *out, int32_
     c->P.desc.vec[ROLE_V] = out;
     psolve_status st = upload_desc(c);
     if (st != PSOLVE_OK) return st;
-    Launcher L;
-    L.stream = c->stream;
-    L.grid = c->grid;
-    L.d_desc = c->d_desc;
-    L.d_list = c->d_list;
+    Launcher L = ctx_launcher(c);
     enqueue_apply_A(L, block_restricted != 0);
     PS_CK(L.err);
     PS_CK(cudaStreamSynchronize(c->stream));
@@ -590,11 +617,7 @@ psolve_status psolve_dot(psolve_ctx *c, const double *a, const double *b, double
     c->P.desc.vec[ROLE_V] = (void *)b;
     psolve_status st = upload_desc(c);
     if (st != PSOLVE_OK) return st;
-    Launcher L;
-    L.stream = c->stream;
-    L.grid = c->grid;
-    L.d_desc = c->d_desc;
-    L.d_list = c->d_list;
+    Launcher L = ctx_launcher(c);
     enqueue_dot(L);
     PS_CK(L.err);
     PS_CK(cudaMemcpyAsync(c->h_sc + 2, c->P.d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
@@ -637,11 +660,7 @@ psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, 
     plan.precond = precond;
     plan.degree = degree;
     plan.prec = P.prec;
-    Launcher L;
-    L.stream = c->stream;
-    L.grid = c->grid;
-    L.d_desc = c->d_desc;
-    L.d_list = c->d_list;
+    Launcher L = ctx_launcher(c);
     enqueue_precond(L, plan);
     PS_CK(L.err);
     PS_CK(cudaStreamSynchronize(c->stream));
@@ -722,6 +741,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     char *mem = nullptr;
     Scal *d_sc = nullptr;
     Desc *d_desc = nullptr, *h_desc = nullptr;
+    CUtensorMap *d_tmap = nullptr, *h_tmap = nullptr;
     int32_t *d_list = nullptr, *h_list = nullptr;
     Scal *h_sc = nullptr;
     cudaStream_t cap = nullptr;
@@ -742,6 +762,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         if (d_desc) cudaFree(d_desc);
         if (d_list) cudaFree(d_list);
         if (h_desc) cudaFreeHost(h_desc);
+        if (d_tmap) cudaFree(d_tmap);
+        if (h_tmap) cudaFreeHost(h_tmap);
         if (h_list) cudaFreeHost(h_list);
         if (h_sc) cudaFreeHost(h_sc);
     };
@@ -760,6 +782,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     BATCH_CK(cudaMalloc(&d_desc, sizeof(Desc) * count));
     BATCH_CK(cudaMalloc(&d_list, list_bytes));
     BATCH_CK(cudaHostAlloc(&h_desc, sizeof(Desc) * count, cudaHostAllocDefault));
+    BATCH_CK(cudaMalloc(&d_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * count));
+    BATCH_CK(cudaHostAlloc(&h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * count, cudaHostAllocDefault));
     BATCH_CK(cudaHostAlloc(&h_list, list_bytes, cudaHostAllocDefault));
     BATCH_CK(cudaHostAlloc(&h_sc, 2 * sizeof(Scal) * count, cudaHostAllocDefault));
     BATCH_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -782,11 +806,15 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         P.desc.vec[ROLE_B] = (void *)rhs[q];
         P.desc.vec[ROLE_X] = x[q];
         P.desc.vec[ROLE_RT] = (void *)rhs[q];
+        P.desc.tmap = d_tmap + (size_t)TMAPS_PER_PROBLEM * q;
+        problem_encode_tmaps(P, h_tmap + (size_t)TMAPS_PER_PROBLEM * q, o.engine != 1);
         h_desc[q] = P.desc;
         h_list[2 + 2 * q] = q;
         h_list[3 + 2 * q] = ub;
         ub += P.desc.units;
     }
+    BATCH_CK(cudaMemcpyAsync(d_tmap, h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * count,
+                             cudaMemcpyHostToDevice, s));
     BATCH_CK(cudaMemcpyAsync(d_desc, h_desc, sizeof(Desc) * count, cudaMemcpyHostToDevice, s));
     BATCH_CK(cudaMemcpyAsync(d_list, h_list, list_bytes, cudaMemcpyHostToDevice, s));
 
@@ -795,7 +823,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     R.cap = cap;
     R.d_desc = d_desc;
     R.d_list = d_list;
-    R.grid = engine_grid(di.sms, total_units);
+    R.sms = di.sms;
+    R.units = total_units;
     R.plan.precond = precond;
     R.plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
     R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : o.cheb_prec;

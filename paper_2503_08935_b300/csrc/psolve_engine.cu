@@ -1,6 +1,8 @@
 // psolve_engine.cu -- kernel sequencing, workspace layout, Chebyshev set-up.
 #include "psolve_engine.cuh"
 
+#include <cudaTypedefs.h>
+
 namespace psolve {
 
 static thread_local std::string g_error;
@@ -43,6 +45,25 @@ cudaEvent_t Launcher::next_event()
     return (*event_pool)[(*event_next)++];
 }
 
+// Per-kernel launch set-up, done once per process: the dynamic shared memory
+// of the TMA ring and the resident CTAs per SM that size the grid.
+template <class Op>
+static cudaError_t op_config(int *occ_out)
+{
+    static int occ = 0;
+    if (!occ) {
+        const int dyn = engine_dyn_smem<Op>();
+        cudaError_t e = cudaFuncSetAttribute(k_engine<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_engine<Op>, NTHREADS, dyn);
+        if (e != cudaSuccess) return e;
+        occ = n < 1 ? 1 : n;
+    }
+    *occ_out = occ;
+    return cudaSuccess;
+}
+
 template <class Op>
 void Launcher::go(int cls, int side, KArgs a, double bytes_per_pt, double half_bytes_per_pt, int is_update)
 {
@@ -57,6 +78,16 @@ void Launcher::go(int cls, int side, KArgs a, double bytes_per_pt, double half_b
         if (recs) recs->push_back(rec);
         return;
     }
+    int occ = 1;
+    cudaError_t st = op_config<Op>(&occ);
+    if (st != cudaSuccess) {
+        if (err == cudaSuccess) err = st;
+        return;
+    }
+    if (configure) return;
+    long long g = (long long)occ * sms;
+    if (units < g) g = units;
+    if (g < 1) g = 1;
     a.descs = d_desc;
     a.list = d_list;
     if (timing) {
@@ -65,20 +96,66 @@ void Launcher::go(int cls, int side, KArgs a, double bytes_per_pt, double half_b
         if (err != cudaSuccess) return;
         cudaEventRecord(rec.ev0, stream);
     }
-    k_engine<Op><<<grid, NTHREADS, 0, stream>>>(a);
-    cudaError_t st = cudaGetLastError();
+    k_engine<Op><<<(int)g, NTHREADS, engine_dyn_smem<Op>(), stream>>>(a);
+    st = cudaGetLastError();
     if (st != cudaSuccess && err == cudaSuccess) err = st;
     if (timing) cudaEventRecord(rec.ev1, stream);
     ++launches;
     if (recs) recs->push_back(rec);
 }
 
-int engine_grid(int sms, long long units)
+// ------------------------------------------------------------ tensor maps --
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
-    // 4 CTAs of 256 threads per SM (the kernels' launch bounds), capped by the work
-    long long g = 4LL * sms;
-    if (units < g) g = units;
-    return (int)(g < 1 ? 1 : g);
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+static bool role_is_ci(int r)
+{
+    return r == ROLE_PH || r == ROLE_RH || r == ROLE_YA || r == ROLE_YB || r == ROLE_BC;
+}
+
+void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
+{
+    Desc &D = P.desc;
+    D.tma = 0;
+    if (!allow || D.nx % 8 != 0) return;
+    for (int r = 0; r < NROLES; ++r)
+        if (D.vec[r] && (reinterpret_cast<uintptr_t>(D.vec[r]) % 16) != 0) return;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return;
+    std::memset(maps, 0, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM);
+    for (int r = 0; r < NROLES; ++r) {
+        if (!D.vec[r]) continue;
+        const bool ci = role_is_ci(r);
+        const size_t es = ci ? ci_elem_bytes(P.prec) : 8;
+        const CUtensorMapDataType dt = !ci || P.prec == PSOLVE_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                       : P.prec == PSOLVE_FP32      ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        const cuuint64_t dims[3] = {(cuuint64_t)D.nx, (cuuint64_t)D.ny, (cuuint64_t)D.nz};
+        const cuuint64_t strides[2] = {(cuuint64_t)D.nx * es, (cuuint64_t)D.nx * D.ny * es};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        const cuuint32_t halo[3] = {(cuuint32_t)(TILE_X + 2 * (16 / es)), (cuuint32_t)(TILE_Y + 2), 1};
+        const cuuint32_t plain[3] = {(cuuint32_t)TILE_X, (cuuint32_t)TILE_Y, 1};
+        for (int v = 0; v < 2; ++v) {
+            CUresult e = fn(&maps[2 * r + v], dt, 3, D.vec[r], dims, strides, v == 0 ? halo : plain, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (e != CUDA_SUCCESS) return;
+        }
+    }
+    D.tma = 1;
 }
 
 // --------------------------------------------------- per-iteration kernels --

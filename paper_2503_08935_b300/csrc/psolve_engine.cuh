@@ -66,7 +66,9 @@ struct LaunchRec {
 // Issues kernels (or only records what it would issue, dry = true).
 struct Launcher {
     cudaStream_t stream = 0;
-    int grid = 1;
+    int sms = 1;               // SMs of the device
+    long long units = 1;       // units of the launch list (upper bound)
+    bool configure = false;    // only set up the kernels' launch attributes
     const Desc *d_desc = nullptr;
     const int32_t *d_list = nullptr;
     bool dry = false;
@@ -121,8 +123,10 @@ void enqueue_apply_A(Launcher &L, bool blocked);
 void enqueue_dot(Launcher &L);
 void enqueue_precond(Launcher &L, const Plan &plan);
 
-// Grid size (CTAs) for a launch covering `units` units.
-int engine_grid(int sms, long long units);
+// Encode the tensor maps of every bound vector of P into maps[0..2*NROLES)
+// and set P.desc.tma (1 when the TMA engine can run this problem: nx % 8 == 0,
+// every vector 16-byte aligned, and `allow`).
+void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow);
 
 // Algorithmic bytes of the launches in `recs` that did work, given the exit
 // iteration and whether it was a half-step exit.

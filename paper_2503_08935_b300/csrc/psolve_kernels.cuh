@@ -2,14 +2,19 @@
 // (sm_103a).  No tensor cores: the 7-point operator is a streaming stencil,
 // bound by HBM bandwidth.
 //
-// Engine.  A CTA of TILE_X x TILE_Y threads owns an xy tile; each thread owns
-// one z column and marches along z keeping u(k-1), u(k), u(k+1) in registers.
-// The x/y neighbours of plane k come from a shared-memory copy of the plane
-// (tile plus a one-cell halo, double-buffered), so every input value is read
-// from HBM once per sweep; the next planes (own column, halo and pointwise
-// operands) are prefetched into registers one step ahead.  Zero Dirichlet
-// ghosts (Eq. 4) are zero-filled halo cells; the block-restricted operator
-// R_s A R_s^T of Eq. 14 zeroes neighbours across block faces.
+// Engines.  A CTA of TILE_X x TILE_Y threads owns an xy tile; each thread owns
+// one z column and marches along z.  Two engines compute bitwise the same
+// values (same thread mapping, same expressions):
+//  * the TMA ring (march_tma, used when nx % 8 == 0 and the vectors are
+//    16-byte aligned): one thread stages whole plane tiles, halo included,
+//    several planes ahead with cp.async.bulk.tensor into a shared-memory ring
+//    tracked by mbarriers, so the bytes in flight do not depend on registers;
+//  * the general engine (march_stencil, any size): u(k-1), u(k), u(k+1) in
+//    registers, the x/y neighbours of plane k from a double-buffered shared
+//    copy of the plane, the next planes prefetched one step ahead.
+// Either way every input value is read from HBM once per sweep.  Zero
+// Dirichlet ghosts (Eq. 4) are zero-filled halo cells; the block-restricted
+// operator R_s A R_s^T of Eq. 14 zeroes neighbours across block faces.
 //
 // Work is split into units (tile x z-chunk); a launch covers every unit of
 // every problem in the launch list, each CTA taking one contiguous range.
@@ -35,12 +40,14 @@ template <class T> struct Elem;
 template <> struct Elem<double> {
     using C = double;
     static __device__ __forceinline__ double ld(const void *p, int i) { return __ldg((const double *)p + i); }
+    static __device__ __forceinline__ double lds(const void *p, int i) { return ((const double *)p)[i]; }
     static __device__ __forceinline__ void st(void *p, int i, double v) { ((double *)p)[i] = v; }
     static __device__ __forceinline__ double round(double v) { return v; }
 };
 template <> struct Elem<float> {
     using C = float;
     static __device__ __forceinline__ float ld(const void *p, int i) { return __ldg((const float *)p + i); }
+    static __device__ __forceinline__ float lds(const void *p, int i) { return ((const float *)p)[i]; }
     static __device__ __forceinline__ void st(void *p, int i, float v) { ((float *)p)[i] = v; }
     static __device__ __forceinline__ float round(double v) { return (float)v; }
 };
@@ -49,6 +56,10 @@ template <> struct Elem<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const void *p, int i)
     {
         return __bfloat162float(__ldg((const __nv_bfloat16 *)p + i));
+    }
+    static __device__ __forceinline__ float lds(const void *p, int i)
+    {
+        return __bfloat162float(((const __nv_bfloat16 *)p)[i]);
     }
     static __device__ __forceinline__ void st(void *p, int i, float v)
     {
@@ -366,17 +377,285 @@ __device__ __forceinline__ void march_point(Op &op, const Desc &D, int tile, int
     }
 }
 
+
+// ------------------------------------------------------------------------
+// TMA ring engine (problems with desc.tma = 1).
+//
+// Thread 0 stages plane q of every operand with one cp.async.bulk.tensor per
+// array: the stencil input as a (TILE_X + 2 HX) x (TILE_Y + 2) halo box
+// starting at (i0 - HX, j0 - 1) with HX = 16 / sizeof(element) (so the x start
+// is 16-byte aligned), the pointwise operands as TILE_X x TILE_Y boxes.  Out of
+// range elements are zero-filled by the copy engine: those zeros are exactly
+// the Dirichlet ghosts of Eq. 4, including planes -1 and nz.  A ring of
+// STAGES planes, one mbarrier each, keeps STAGES - 3 planes in flight ahead of
+// the three (k-1, k, k+1) the stencil reads.  Every wait is bounded; on
+// time-out the problem stops with status TIMEOUT and the CTA stops waiting.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the completion of phase `parity`: gives up after about
+// 2^31 clock cycles (about a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+                 "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+constexpr int align128(int b) { return (b + 127) & ~127; }
+
+// Shared-memory geometry of one ring stage for an operation.
+template <class Op>
+struct Ring {
+    using TH = typename Op::TH;
+    using TP = typename Op::TP;
+    using C = typename Op::C;
+    static constexpr int HX = 16 / (int)sizeof(TH);      // halo columns each side
+    static constexpr int W = TILE_X + 2 * HX;            // halo box width
+    static constexpr int HBOX = W * (TILE_Y + 2);        // halo box elements
+    static constexpr int HBYTES = HBOX * (int)sizeof(TH);
+    static constexpr int PBYTES = TILE_X * TILE_Y * (int)sizeof(TP);
+    static constexpr int HSTRIDE = align128(HBYTES);
+    static constexpr int PSTRIDE = align128(PBYTES);
+    static constexpr int STAGE = Op::NH * HSTRIDE + Op::NP * PSTRIDE;
+    static constexpr int XBYTES = Op::XFORM ? align128(HBOX * (int)sizeof(C)) : 0; // one u plane
+    static constexpr int STAGES_RAW = (48 * 1024 - 3 * XBYTES) / (STAGE > 0 ? STAGE : 1);
+    static constexpr int STAGES = STAGES_RAW < 4 ? 4 : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+    static constexpr int BYTES = STAGES * STAGE + 3 * XBYTES; // dynamic shared memory
+};
+
+// Issue the copies of plane q into stage `st` (thread 0 only).
+template <class Op>
+__device__ __forceinline__ void ring_issue(const Op &op, const Desc &D, unsigned char *stage, uint64_t *bar,
+                                           int i0, int j0, int q, bool with_pw)
+{
+    using R = Ring<Op>;
+    const uint32_t bytes = op.nh * R::HBYTES + (with_pw ? op.np * R::PBYTES : 0);
+    mbar_expect_tx(bar, bytes);
+    for (int a = 0; a < op.nh; ++a)
+        tma_load_3d(stage + a * R::HSTRIDE, D.tmap + 2 * op.hrole[a], i0 - R::HX, j0 - 1, q, bar);
+    if (with_pw)
+        for (int a = 0; a < op.np; ++a)
+            tma_load_3d(stage + Op::NH * R::HSTRIDE + a * R::PSTRIDE, D.tmap + 2 * op.prole[a] + 1, i0, j0, q,
+                        bar);
+}
+
+template <class Op>
+__device__ __forceinline__ void stage_ptrs(unsigned char *stage, const void *(&h)[Op::NH > 0 ? Op::NH : 1],
+                                           const void *(&p)[Op::NP > 0 ? Op::NP : 1])
+{
+    using R = Ring<Op>;
+#pragma unroll
+    for (int a = 0; a < Op::NH; ++a) h[a] = stage + a * R::HSTRIDE;
+#pragma unroll
+    for (int a = 0; a < Op::NP; ++a) p[a] = stage + Op::NH * R::HSTRIDE + a * R::PSTRIDE;
+}
+
+// Stencil march over chunks [c0, c1) of one tile, operands staged by TMA.
+// `seq` counts the planes this CTA has staged so far (all threads agree); plane
+// number n lives in stage n % STAGES and completes phase (n / STAGES) & 1.
+template <class Op>
+__device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c0, int c1,
+                                          unsigned char *ring, uint64_t *bars, uint32_t &seq,
+                                          double *sred, int *s_dead)
+{
+    using R = Ring<Op>;
+    using C = typename Op::C;
+    using U = typename Op::U;
+    using PW = typename Op::PW;
+    constexpr int S = R::STAGES;
+    constexpr int W = R::W;
+    constexpr int ND = Op::ND;
+    constexpr int NDA = ND > 0 ? ND : 1;
+    constexpr int NHA = Op::NH > 0 ? Op::NH : 1;
+    constexpr int NPA = Op::NP > 0 ? Op::NP : 1;
+
+    const int nx = D.nx, ny = D.ny, nz = D.nz, zc = D.zc;
+    const int plane = nx * ny;
+    const int tid = threadIdx.x, tx = tid % TILE_X, ty = tid / TILE_X;
+    const int i0 = (tile % D.tiles_x) * TILE_X, j0 = (tile / D.tiles_x) * TILE_Y;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool in = (i < nx) && (j < ny);
+    const int col = in ? j * nx + i : 0;
+    const int me = (ty + 1) * W + tx + R::HX; // this point in a halo box
+    const int mp = ty * TILE_X + tx;          // this point in a plain box
+
+    bool okw = true, oke = true, oks = true, okn = true;
+    if constexpr (Op::BLOCKED) {
+        okw = (i % D.bx) != 0;
+        oke = (i % D.bx) != D.bx - 1;
+        oks = (j % D.by) != 0;
+        okn = (j % D.by) != D.by - 1;
+    }
+    const C cx = (C)D.cx, cy = (C)D.cy, cz = (C)D.cz, cc = (C)D.cc;
+
+    const int kb = c0 * zc;
+    const int ke = min(nz, c1 * zc);
+    const int q0 = kb - 1, q1 = ke; // stencil-input planes q0..q1, pointwise planes kb..ke-1
+    const int nplanes = q1 - q0 + 1;
+    const uint32_t seq0 = seq;
+    C *xring = reinterpret_cast<C *>(ring + S * R::STAGE); // transformed u planes (XFORM only)
+
+    auto stage_of = [&](int q) { return ring + ((seq0 + (q - q0)) % S) * R::STAGE; };
+    auto bar_of = [&](int q) { return bars + (seq0 + (q - q0)) % S; };
+    auto parity_of = [&](int q) { return (uint32_t)(((seq0 + (q - q0)) / S) & 1u); };
+    auto wait_plane = [&](int q) {
+        if (*s_dead) return;
+        if (!mbar_wait(bar_of(q), parity_of(q))) {
+            *s_dead = 1;
+            D.sc->status = ST_TIMEOUT;
+            D.sc->stop = 1;
+        }
+    };
+    // u of plane q at halo-box index x, from the staged arrays
+    auto u_at = [&](int q, int x) -> C {
+        if constexpr (Op::XFORM) {
+            return xring[((q - q0) % 3) * R::HBOX + x];
+        } else {
+            const void *h[NHA], *p[NPA];
+            stage_ptrs<Op>(stage_of(q), h, p);
+            return op.sv(op.load_s(h, x));
+        }
+    };
+    auto transform = [&](int q) {
+        if constexpr (Op::XFORM) {
+            const void *h[NHA], *p[NPA];
+            stage_ptrs<Op>(stage_of(q), h, p);
+            C *dst = xring + ((q - q0) % 3) * R::HBOX;
+            for (int x = tid; x < R::HBOX; x += NTHREADS) dst[x] = op.sv(op.load_s(h, x));
+        }
+    };
+
+    __syncthreads(); // the previous run's readers of the ring are done
+    if (tid == 0) {
+        for (int n = 0; n < S && n < nplanes; ++n) {
+            const int q = q0 + n;
+            ring_issue<Op>(op, D, stage_of(q), bar_of(q), i0, j0, q, q >= kb && q < ke);
+        }
+    }
+    wait_plane(q0);
+    wait_plane(kb);
+    transform(q0);
+    transform(kb);
+
+    double acc[NDA];
+#pragma unroll
+    for (int a = 0; a < NDA; ++a) acc[a] = 0.0;
+    int kk = 0;
+    if constexpr (Op::BLOCKED) kk = kb % D.bz;
+    int unit = tile * D.nzc + c0;
+    int cend = min(nz, (c0 + 1) * zc);
+
+    for (int k = kb; k < ke; ++k) {
+        wait_plane(k + 1);
+        transform(k + 1);
+        if constexpr (Op::XFORM) __syncthreads();
+        if (in && !*s_dead) {
+            C w = u_at(k, me - 1), e = u_at(k, me + 1), so = u_at(k, me - W), no = u_at(k, me + W);
+            C dn = u_at(k - 1, me), un = u_at(k + 1, me);
+            if constexpr (Op::BLOCKED) {
+                if (!okw) w = C(0);
+                if (!oke) e = C(0);
+                if (!oks) so = C(0);
+                if (!okn) no = C(0);
+                if (kk == 0) dn = C(0);
+                if (kk == D.bz - 1) un = C(0);
+            }
+            const void *h[NHA], *p[NPA];
+            stage_ptrs<Op>(stage_of(k), h, p);
+            const U uc = op.load_s(h, me);
+            const PW pw = op.pw_s(p, mp);
+            const C au = cc * op.sv(uc) - cx * (w + e) - cy * (so + no) - cz * (dn + un);
+            op.emit(col + k * plane, au, uc, pw, acc);
+        }
+        __syncthreads(); // stage of plane k-1 (and its u plane) is free
+        if (tid == 0 && k - 1 + S <= q1 && !*s_dead) {
+            const int q = k - 1 + S;
+            ring_issue<Op>(op, D, stage_of(q), bar_of(q), i0, j0, q, q >= kb && q < ke);
+        }
+        if constexpr (Op::BLOCKED) {
+            if (++kk == D.bz) kk = 0;
+        }
+        if constexpr (ND > 0) {
+            if (k + 1 == cend) {
+                flush_unit<ND>(acc, sred, D.partials, unit);
+                ++unit;
+                cend = min(nz, cend + zc);
+            }
+        }
+    }
+    // drain: planes issued but not consumed in this run (q1 is always waited
+    // above; planes beyond it are never issued), so nothing is left in flight.
+    seq = seq0 + nplanes;
+}
+
 // ------------------------------------------------------------------------
 // The generic kernel: walk this CTA's unit range over the launch list.
 // ------------------------------------------------------------------------
+template <class Op>
+constexpr int ring_stages()
+{
+    if constexpr (Op::STENCIL) return Ring<Op>::STAGES;
+    else return 1;
+}
+
 template <class Op>
 __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
 {
     using C = typename Op::C;
     constexpr int SPL = (TILE_X + 2) * (TILE_Y + 2);
-    __shared__ C sp[Op::STENCIL ? 2 * SPL : 1];
+    constexpr int NB = ring_stages<Op>();
     __shared__ double sred[(NTHREADS / 32) * MAX_DOTS];
-    __shared__ int s_last;
+    __shared__ alignas(8) uint64_t bars[NB];
+    __shared__ int s_last, s_dead;
+    // the TMA ring, or the general engine's double-buffered plane: a CTA runs
+    // one engine at a time, and each march starts with a barrier
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    C *sp = reinterpret_cast<C *>(dyn_smem);
+    (void)SPL;
 
     const ListHdr hdr = *reinterpret_cast<const ListHdr *>(a.list);
     const int2 *ent = reinterpret_cast<const int2 *>(a.list + 2);
@@ -384,6 +663,16 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
     int u0 = (int)(total * blockIdx.x / gridDim.x);
     const int u1 = (int)(total * (blockIdx.x + 1) / gridDim.x);
     if (u0 >= u1) return;
+
+    if constexpr (Op::STENCIL) {
+        if (threadIdx.x == 0) {
+            for (int b = 0; b < NB; ++b) mbar_init(&bars[b], 1);
+            mbar_init_fence();
+            s_dead = 0;
+        }
+        __syncthreads();
+    }
+    uint32_t seq = 0;
 
     int lo = 0, hi = hdr.n - 1; // last entry whose first unit <= u0
     while (lo < hi) {
@@ -405,13 +694,18 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
 
         Op op(D, a, sc);
         const int nzc = D.nzc;
+        const bool use_tma = D.tma != 0;
         for (int pu = pu0; pu < pu1;) {
             const int tile = pu / nzc;
             const int c0 = pu - tile * nzc;
             const int run_end = min(pu1, (tile + 1) * nzc);
             const int c1 = c0 + (run_end - pu);
-            if constexpr (Op::STENCIL) march_stencil<Op>(op, D, tile, c0, c1, sp, sred);
-            else march_point<Op>(op, D, tile, c0, c1, sred);
+            if constexpr (Op::STENCIL) {
+                if (use_tma) march_tma<Op>(op, D, tile, c0, c1, dyn_smem, bars, seq, sred, &s_dead);
+                else march_stencil<Op>(op, D, tile, c0, c1, sp, sred);
+            } else {
+                march_point<Op>(op, D, tile, c0, c1, sred);
+            }
             pu = run_end;
         }
         if constexpr (Op::ND > 0) {
@@ -443,6 +737,18 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
     }
 }
 
+// Dynamic shared memory a launch of k_engine<Op> needs.
+template <class Op>
+constexpr int engine_dyn_smem()
+{
+    if constexpr (Op::STENCIL) {
+        constexpr int lsu = 2 * (TILE_X + 2) * (TILE_Y + 2) * (int)sizeof(typename Op::C);
+        return Ring<Op>::BYTES > lsu ? Ring<Op>::BYTES : lsu;
+    } else {
+        return 0;
+    }
+}
+
 // ------------------------------------------------------------------------
 // Operations.
 // ------------------------------------------------------------------------
@@ -466,6 +772,12 @@ struct OpCiFirst {
     static constexpr int EPI = SIDE == SIDE_S ? EPI_SNORM : EPI_NONE;
     static constexpr bool STENCIL = true, BLOCKED = BLK;
     static constexpr bool MIXED = !std::is_same<T, double>::value;
+    // staged form: halo boxes of r (and w, p_{i-2}); u is formed once per plane
+    using TH = double;
+    using TP = double;
+    static constexpr int NH = SIDE == SIDE_S ? 2 : 3, NP = 0;
+    static constexpr bool XFORM = true;
+    int nh, np, hrole[NH], prole[1];
     const double *r, *pold, *w;
     double *uout;
     void *bc, *out;
@@ -478,13 +790,24 @@ struct OpCiFirst {
         r = (const double *)D.vec[ROLE_R];
         w = (const double *)D.vec[ROLE_W];
         pold = (const double *)D.vec[resolve_role(ROLE_POLD, iter)];
+        first = ld_flag(&sc->first);
+        np = 0;
+        prole[0] = 0;
+        hrole[0] = ROLE_R;
+        if constexpr (SIDE == SIDE_S) {
+            nh = 2;
+            hrole[1] = ROLE_W;
+        } else {
+            nh = first ? 1 : 3;
+            hrole[1] = resolve_role(ROLE_POLD, iter);
+            hrole[2] = ROLE_W;
+        }
         uout = (double *)D.vec[resolve_role(a.in, iter)];
         bc = D.vec[ROLE_BC];
         out = D.vec[a.out];
         beta = ld_scal(&sc->beta);
         omega = ld_scal(&sc->omega);
         alpha = ld_scal(&sc->alpha);
-        first = ld_flag(&sc->first);
         degree = D.degree;
         tinv = (C)D.theta_inv;
         coef1 = (C)(D.two_over_delta * D.rho[1]);
@@ -498,8 +821,19 @@ struct OpCiFirst {
             return r[idx] + beta * (pold[idx] - omega * w[idx]);
         }
     }
+    __device__ __forceinline__ double load_s(const void *const *h, int x) const
+    {
+        if constexpr (SIDE == SIDE_S) {
+            return Elem<double>::lds(h[0], x) - alpha * Elem<double>::lds(h[1], x);
+        } else {
+            if (first) return Elem<double>::lds(h[0], x);
+            return Elem<double>::lds(h[0], x) +
+                   beta * (Elem<double>::lds(h[1], x) - omega * Elem<double>::lds(h[2], x));
+        }
+    }
     __device__ __forceinline__ C sv(double u) const { return (C)E::round(u); }
     __device__ __forceinline__ PW pw(bool, int) const { return PW{}; }
+    __device__ __forceinline__ PW pw_s(const void *const *, int) const { return PW{}; }
     template <int NA>
     __device__ __forceinline__ void emit(int idx, C au, double uc, const PW &, double (&acc)[NA]) const
     {
@@ -525,6 +859,13 @@ struct OpCiSweep {
     struct PW { C b, z; };
     static constexpr int ND = 0, EPI = EPI_NONE;
     static constexpr bool STENCIL = true, BLOCKED = BLK;
+    static_assert(sizeof(TB) == sizeof(T), "CI right-hand side and iterates share one type");
+    // staged form: halo box of y_{k-1}, plain boxes of b and y_{k-2}
+    using TH = T;
+    using TP = T;
+    static constexpr int NH = 1, NP = 2;
+    static constexpr bool XFORM = false;
+    int nh, np, hrole[NH], prole[NP];
     const void *y, *bv, *zv;
     void *out;
     C tinv, tod, tsig, rk, rk1;
@@ -537,6 +878,11 @@ struct OpCiSweep {
         zv = D.vec[a.z];
         out = D.vec[a.out];
         k = a.k;
+        nh = 1;
+        hrole[0] = a.in;
+        np = a.k >= 3 ? 2 : 1;
+        prole[0] = resolve_role(a.b, iter);
+        prole[1] = a.z;
         tinv = (C)D.theta_inv;
         tod = (C)D.two_over_delta;
         tsig = (C)D.two_sigma;
@@ -544,6 +890,7 @@ struct OpCiSweep {
         rk1 = (C)D.rho[a.k - 1];
     }
     __device__ __forceinline__ C load(int idx) const { return E::ld(y, idx); }
+    __device__ __forceinline__ C load_s(const void *const *h, int x) const { return E::lds(h[0], x); }
     __device__ __forceinline__ C sv(C u) const { return u; }
     __device__ __forceinline__ PW pw(bool valid, int idx) const
     {
@@ -553,6 +900,12 @@ struct OpCiSweep {
             if (k >= 3) p.z = E::ld(zv, idx);
         }
         return p;
+    }
+    __device__ __forceinline__ PW pw_s(const void *const *p, int x) const
+    {
+        PW v{(C)EB::lds(p[0], x), C(0)};
+        if (k >= 3) v.z = E::lds(p[1], x);
+        return v;
     }
     template <int NA>
     __device__ __forceinline__ void emit(int idx, C au, C yc, const PW &p, double (&)[NA]) const
@@ -570,6 +923,11 @@ struct OpStencilDot {
     using PW = double;
     static constexpr int ND = 1, EPI = EPI_ALPHA;
     static constexpr bool STENCIL = true, BLOCKED = false;
+    using TH = T;
+    using TP = double;
+    static constexpr int NH = 1, NP = 1;
+    static constexpr bool XFORM = false;
+    int nh = 1, np = 1, hrole[NH], prole[NP];
     const void *ph;
     const double *rt;
     double *w;
@@ -578,8 +936,15 @@ struct OpStencilDot {
         ph = D.vec[a.in];
         rt = (const double *)D.vec[ROLE_RT];
         w = (double *)D.vec[ROLE_W];
+        hrole[0] = a.in;
+        prole[0] = ROLE_RT;
     }
     __device__ __forceinline__ double load(int idx) const { return (double)Elem<T>::ld(ph, idx); }
+    __device__ __forceinline__ double load_s(const void *const *h, int x) const
+    {
+        return (double)Elem<T>::lds(h[0], x);
+    }
+    __device__ __forceinline__ double pw_s(const void *const *p, int x) const { return Elem<double>::lds(p[0], x); }
     __device__ __forceinline__ double sv(double u) const { return u; }
     __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? __ldg(rt + idx) : 0.0; }
     template <int NA>
@@ -598,6 +963,11 @@ struct OpStencil2Dot {
     using PW = double;
     static constexpr int ND = 2, EPI = EPI_OMEGA;
     static constexpr bool STENCIL = true, BLOCKED = false;
+    using TH = T;
+    using TP = double;
+    static constexpr int NH = 1, NP = 1;
+    static constexpr bool XFORM = false;
+    int nh = 1, np = 1, hrole[NH], prole[NP];
     const void *rh;
     const double *s;
     double *t;
@@ -606,8 +976,15 @@ struct OpStencil2Dot {
         rh = D.vec[a.in];
         s = (const double *)D.vec[ROLE_S];
         t = (double *)D.vec[ROLE_T];
+        hrole[0] = a.in;
+        prole[0] = ROLE_S;
     }
     __device__ __forceinline__ double load(int idx) const { return (double)Elem<T>::ld(rh, idx); }
+    __device__ __forceinline__ double load_s(const void *const *h, int x) const
+    {
+        return (double)Elem<T>::lds(h[0], x);
+    }
+    __device__ __forceinline__ double pw_s(const void *const *p, int x) const { return Elem<double>::lds(p[0], x); }
     __device__ __forceinline__ double sv(double u) const { return u; }
     __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? s[idx] : 0.0; }
     template <int NA>
@@ -627,16 +1004,25 @@ struct OpApplyA {
     using PW = NoPW;
     static constexpr int ND = 0, EPI = EPI_NONE;
     static constexpr bool STENCIL = true, BLOCKED = BLK;
+    using TH = double;
+    using TP = double;
+    static constexpr int NH = 1, NP = 0;
+    static constexpr bool XFORM = false;
+    int nh = 1, np = 0, hrole[NH], prole[1];
     const double *u;
     double *v;
     __device__ OpApplyA(const Desc &D, const KArgs &a, Scal *)
     {
         u = (const double *)D.vec[a.in];
         v = (double *)D.vec[a.out];
+        hrole[0] = a.in;
+        prole[0] = 0;
     }
     __device__ __forceinline__ double load(int idx) const { return __ldg(u + idx); }
+    __device__ __forceinline__ double load_s(const void *const *h, int x) const { return Elem<double>::lds(h[0], x); }
     __device__ __forceinline__ double sv(double x) const { return x; }
     __device__ __forceinline__ PW pw(bool, int) const { return PW{}; }
+    __device__ __forceinline__ PW pw_s(const void *const *, int) const { return PW{}; }
     template <int NA>
     __device__ __forceinline__ void emit(int idx, double au, double, const PW &, double (&)[NA]) const
     {
@@ -654,6 +1040,11 @@ struct OpResidual {
     static constexpr int ND = INIT ? 2 : 1;
     static constexpr int EPI = INIT ? EPI_INITX0 : EPI_TRUE;
     static constexpr bool STENCIL = true, BLOCKED = false;
+    using TH = double;
+    using TP = double;
+    static constexpr int NH = 1, NP = 1;
+    static constexpr bool XFORM = false;
+    int nh = 1, np = 1, hrole[NH], prole[NP];
     const double *x, *b;
     double *r, *rt;
     __device__ OpResidual(const Desc &D, const KArgs &, Scal *)
@@ -662,8 +1053,12 @@ struct OpResidual {
         b = (const double *)D.vec[ROLE_B];
         r = (double *)D.vec[ROLE_R];
         rt = (double *)D.vec[ROLE_RT];
+        hrole[0] = ROLE_X;
+        prole[0] = ROLE_B;
     }
     __device__ __forceinline__ double load(int idx) const { return x[idx]; }
+    __device__ __forceinline__ double load_s(const void *const *h, int x_) const { return Elem<double>::lds(h[0], x_); }
+    __device__ __forceinline__ double pw_s(const void *const *p, int x_) const { return Elem<double>::lds(p[0], x_); }
     __device__ __forceinline__ double sv(double u) const { return u; }
     __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? __ldg(b + idx) : 0.0; }
     template <int NA>

@@ -10,6 +10,8 @@
 // last CTA to finish the problem), so every reduction result depends only on
 // the problem's own shape, never on the launch size or the batch mix.
 #pragma once
+#include <cuda.h> // CUtensorMap (type only; the library does not link libcuda)
+
 #include <cstdint>
 
 namespace psolve {
@@ -91,6 +93,12 @@ struct Desc {
     void *vec[NROLES];
     Scal *sc;
     double *partials;   // units * MAX_DOTS doubles
+    // TMA engine: 1 if every stencil operand of this problem can be staged by
+    // tensor copies (nx % 8 == 0, 16-byte aligned vectors); tmap[2*role] is the
+    // role's halo-box map, tmap[2*role + 1] its plain-box map.
+    int32_t tma;
+    int32_t pad_;
+    const CUtensorMap *tmap;
 };
 
 // Header of a device-side launch list: `n` entries of (problem, first unit)
@@ -108,6 +116,9 @@ struct KArgs {
     int32_t skip;        // SKIP_* bits
     int32_t in, b, z, out, aux; // roles used by the operation
 };
+
+constexpr int TMAPS_PER_PROBLEM = 2 * NROLES;
+constexpr int ST_TIMEOUT = 7; // a bounded wait of the TMA ring gave up
 
 constexpr int SKIP_STOP = 1; // skip problems whose `stop` is set
 constexpr int SKIP_HALF = 2; // skip problems whose `half` is set

@@ -48,14 +48,14 @@ def test_struct_layout_matches_c(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "psolve.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(psolve_opts), sizeof(psolve_result),"
         " offsetof(psolve_result, kernel_launches), offsetof(psolve_result, kclass_bytes),"
-        " offsetof(psolve_opts, rr_every)); return 0;}\n")
+        " offsetof(psolve_opts, engine)); return 0;}\n")
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     so, sr, okl, okb, orr = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
                                                     check=True).stdout.split())
     assert so == ctypes.sizeof(B.Opts) and sr == ctypes.sizeof(B.Result)
     assert okl == B.Result.kernel_launches.offset and okb == B.Result.kclass_bytes.offset
-    assert orr == B.Opts.rr_every.offset
+    assert orr == B.Opts.engine.offset
 
 
 def test_default_opts(L):
