@@ -202,6 +202,25 @@ PSOLVE_API psolve_status psolve_dot(psolve_ctx *ctx, const double *a_dev, const 
  * preconditioner (Eq. 9-11 with the context's scales and blocks). */
 PSOLVE_API psolve_status psolve_cheb_interval(psolve_ctx *ctx, int32_t precond, double *a, double *b);
 
+/* *result_host = a . b over a grid of grid[3] = (nx, ny, nz) points, the same
+ * deterministic reduction as psolve_dot, without any context and without
+ * allocating device memory.  The paper has no counterpart: this exists for
+ * callers that must not allocate, e.g. code running while a framework's
+ * caching allocator or a serving process owns the device memory budget, or
+ * host paths that cannot afford the synchronisation cudaMalloc/cudaFree may
+ * cause.  Its scratch (descriptor, scalars, per-unit partial sums) is one
+ * fixed 4 MiB device array inside the library, held by every GPU that loads
+ * it until the process exits; grids whose partial sums do not fit (more than
+ * about 2.6e5 work units, roughly 800^3 points) return PSOLVE_E_ARG.  The first
+ * call on a device looks the array's address up (cudaGetSymbolAddress) and
+ * should come before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU (other streams, other host threads) race.  a_dev,
+ * b_dev: device vectors of nx*ny*nz doubles; work is ordered on `stream`
+ * and the call returns after the result is copied to *result_host. */
+PSOLVE_API psolve_status psolve_dot_noalloc(const int64_t grid[3], const double *a_dev,
+                                            const double *b_dev, uintptr_t stream,
+                                            double *result_host);
+
 /* ---- many independent grids at once ----------------------------------- */
 
 /* Solve `count` independent problems of (possibly) different sizes together:

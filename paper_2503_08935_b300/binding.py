@@ -30,7 +30,7 @@ EXPORTS = [
     "psolve_opts_default", "psolve_create", "psolve_solve", "psolve_solve_host", "psolve_destroy",
     "psolve_apply_A", "psolve_precond_apply", "psolve_dot", "psolve_cheb_interval", "psolve_solve_batch",
     "psolve_server_create", "psolve_submit", "psolve_poll", "psolve_server_destroy", "psolve_last_error",
-    "psolve_version",
+    "psolve_version", "psolve_dot_noalloc",
 ]
 
 
@@ -113,6 +113,8 @@ def lib():
         L.psolve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(Result)]
         L.psolve_server_destroy.argtypes = [P]
         L.psolve_server_destroy.restype = None
+        L.psolve_dot_noalloc.argtypes = [I64P, P, P, ctypes.c_void_p, DP]
+        L.psolve_dot_noalloc.restype = ctypes.c_int32
         L.psolve_last_error.restype = ctypes.c_char_p
         L.psolve_last_error.argtypes = []
         L.psolve_version.restype = ctypes.c_char_p
@@ -308,3 +310,18 @@ def solve_batch(bs, xs, hs=None, rtol=1e-10, maxit=2000, precond=PC_CHEB, degree
     if st in (E_ARG, E_OOM, E_CUDA, TIMEOUT):
         raise PsolveError(st, "psolve_solve_batch")
     return [_info(r) for r in res]
+
+
+def dot_noalloc(a, b, stream=None) -> float:
+    """psolve_dot_noalloc on two float64 CUDA tensors of shape (nz, ny, nx):
+    the library's deterministic dot product without a context or any device
+    allocation (for callers that must not allocate)."""
+    nz, ny, nx = a.shape
+    _check_vec(a, a.shape)
+    _check_vec(b, a.shape)
+    grid = (ctypes.c_int64 * 3)(nx, ny, nz)
+    res = ctypes.c_double()
+    st = lib().psolve_dot_noalloc(grid, _ptr(a), _ptr(b), _stream_handle(stream), ctypes.byref(res))
+    if st != OK:
+        raise PsolveError(st, "psolve_dot_noalloc")
+    return res.value
