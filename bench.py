@@ -37,8 +37,11 @@ MAXIT = 500
 DEGREE = 8
 WORKLOAD = "poisson 256^3 FP64, Bi-CGSTAB + G(CI) Chebyshev degree 8, exact bounds, rtol 1e-10"
 GOLDEN_256 = os.path.join(ROOT, "tests", "golden", "oracle_256_cheb8.json")
-NCU_SUMMARY = os.path.join(ROOT, "profiles", "ncu_ci_sweep4_256.md")
+NCU_SUMMARY = os.path.join(ROOT, "profiles", "ncu_ci_sweep4_256_{prec}.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2503_08935_b300", "csrc", "psolve_kernels.cuh")
+# FP64 instructions per point of a Chebyshev sweep k >= 3 as the kernel writes it:
+# three neighbour-pair sums, one multiply and five fused multiply-adds.
+SWEEP_FP64_OPS_PER_POINT = 9
 
 
 def dist_env():
@@ -60,11 +63,11 @@ def kernel_source_hash():
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic_per_point():
+def ncu_traffic_per_point(prec):
     """DRAM bytes per grid point of one ci_sweep4 launch from the committed ncu
     summary, or None if there is none or the kernel source changed since."""
     try:
-        txt = open(NCU_SUMMARY).read()
+        txt = open(NCU_SUMMARY.format(prec=prec)).read()
     except OSError:
         return None
     vals = {}
@@ -227,7 +230,9 @@ def run_gpu(args):
     x_host = torch.empty(SHAPE, dtype=torch.float64).pin_memory()
     npts = b.numel()
 
-    solver = B.Solver(SHAPE, h, timing=1 if args.kernel_timing else 0, stream=stream)
+    prec = {"fp64": B.FP64, "fp32": B.FP32, "bf16": B.BF16}[args.prec]
+    solver = B.Solver(SHAPE, h, timing=1 if args.kernel_timing else 0, stream=stream, cheb_prec=prec)
+    x_fp64 = None
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -278,6 +283,7 @@ def run_gpu(args):
     # dominant kernel: Chebyshev sweep k >= 3 (reads y_{k-1}, b, y_{k-2}; writes y_k)
     peak, peak_kind = measured_peaks()
     roof = None
+    breakdown = {}
     if args.kernel_timing:
         k = "ci_sweep4"
         kms = sum(i.kclass[k]["ms"] for i in infos)
@@ -285,15 +291,29 @@ def run_gpu(args):
         kbytes = sum(i.kclass[k]["bytes"] for i in infos)
         avg_ms = kms / max(kn, 1)
         per_launch = kbytes / max(kn, 1)
-        achieved = per_launch / (avg_ms * 1e-3) / 1e9
-        tpp = ncu_traffic_per_point()
-        roof = {"bound": "hbm", "kernel": "k_engine<OpCiSweep<double,double,false>> (CI sweep k>=3)",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy test)",
+        gbs = per_launch / (avg_ms * 1e-3) / 1e9
+        tpp = ncu_traffic_per_point(args.prec)
+        ctype = {"fp64": "double", "fp32": "float", "bf16": "__nv_bfloat16"}[args.prec]
+        roof = {"kernel": f"k_engine<OpCiSweep<{ctype},{ctype},false>> (Chebyshev sweep k>=3)",
                 "traffic": (tpp * npts) if tpp is not None else None,
                 "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms, "launches": kn,
-                "share_of_step": kms / ms if ms > 0 else None}
-        breakdown = {}
+                "share_of_step": kms / ms if ms > 0 else None,
+                "hbm_view": {"achieved_GBps": gbs, "peak_GBps": peak, "frac": gbs / peak,
+                             "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy test)"}}
+        if args.prec == "fp64":
+            # B300's FP64 pipe: 2 FP64 instructions (add, mul or fma) per clock per SM
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2032.0
+            peak_ops = 2.0 * sms * mhz * 1e6
+            ops = SWEEP_FP64_OPS_PER_POINT * npts / (avg_ms * 1e-3)
+            roof.update({"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12, "unit": "TFP64op/s",
+                         "frac": ops / peak_ops,
+                         "peak_kind": (f"derived: 2 FP64 pipe instructions/clock/SM x {sms} SMs x "
+                                       f"{mhz:.0f} MHz median SM clock of this run"),
+                         "ops_per_point": SWEEP_FP64_OPS_PER_POINT})
+        else:
+            roof.update({"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy test)"})
         for name in B.K_NAMES:
             kms_c = sum(i.kclass[name]["ms"] for i in infos)
             kb_c = sum(i.kclass[name]["bytes"] for i in infos)
@@ -304,8 +324,10 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": "256x256x256", "h": "1/257",
+        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else f"f64 outer / {args.prec} Chebyshev",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.prec == "fp64" else WORKLOAD + f", Chebyshev vectors {args.prec}",
+                   "grid": "256x256x256", "h": "1/257",
                    "rhs": "U[-1,1) splitmix64 seed 1", "precond": "G(CI) degree 8, bounds (1,1)", "rtol": RTOL,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: ~10 FP64 vectors of 134 MB each"},
@@ -322,8 +344,11 @@ def run_gpu(args):
         "kernel_timing": "CUDA events around every kernel launch (plain launches)" if args.kernel_timing
         else "off (CUDA-graph replay)",
     }
-    if roof is not None:
+    if breakdown:
         line["kernel_breakdown"] = breakdown
+    if args.variants and rank == 0:
+        x_ref = x.clone()
+        line["variants"] = run_variants(args, b, x_ref, stream, B, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_record(iters)
     solver.close()
@@ -332,6 +357,44 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_variants(args, b, x_ref, stream, B, torch):
+    """The same 256^3 problem with the Chebyshev vectors in FP32 and in BF16
+    (FP64 outer iteration), and with the rescaled bounds of the experimental
+    set-up (lambda_min x 100, lambda_max x (1 - 1e-4)); each reports time to
+    rtol 1e-10 (CUDA events, graph replay), iterations, the true residual and
+    the relative L2 difference from the FP64 solution of the headline run."""
+    out = {}
+    cases = [("fp32_cheb8", dict(cheb_prec=B.FP32), B.PC_CHEB, 8),
+             ("bf16_cheb8", dict(cheb_prec=B.BF16), B.PC_CHEB, 8),
+             ("fp32_cheb16", dict(cheb_prec=B.FP32), B.PC_CHEB, 16),
+             ("fp64_cheb8_paper_scaled", dict(lmin_scale=100.0, lmax_scale=1 - 1e-4), B.PC_CHEB, 8),
+             ("fp32_cheb8_paper_scaled", dict(cheb_prec=B.FP32, lmin_scale=100.0, lmax_scale=1 - 1e-4),
+              B.PC_CHEB, 8),
+             ("fp64_gnocomm8_4x4x4", dict(blocks=(4, 4, 4)), B.PC_GNOCOMM_CHEB, 8),
+             ("fp64_bj8_4x4x4", dict(blocks=(4, 4, 4)), B.PC_BJ_CHEB, 8),
+             ("fp64_none", dict(), B.PC_NONE, 0)]
+    h = (1.0 / 257,) * 3
+    x = torch.zeros_like(b)
+    for name, kw, pc, deg in cases:
+        with B.Solver(SHAPE, h, stream=stream, **kw) as s:
+            maxit = 5000 if pc == B.PC_NONE else MAXIT
+            s.solve(b, x, rtol=RTOL, maxit=maxit, precond=pc, degree=deg)  # warm-up (graph capture)
+            steps = max(1, min(args.steps, 3))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                info = s.solve(b, x, rtol=RTOL, maxit=maxit, precond=pc, degree=deg)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+        rel = float(torch.linalg.vector_norm(x - x_ref) / torch.linalg.vector_norm(x_ref))
+        out[name] = {"status": info.status_name, "time_to_rtol_ms": ms, "iterations": info.iterations,
+                     "rel_res_true": info.rel_res_true, "rel_l2_vs_fp64_solution": rel,
+                     "model_gb_per_s": info.model_bytes / (ms * 1e-3) / 1e9, "engine": info.engine}
+    return out
 
 
 def main():
@@ -343,6 +406,10 @@ def main():
     ap.add_argument("--kernel-timing", type=int, default=1,
                     help="1: plain launches with CUDA events per kernel (roofline); 0: graph replay")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16"],
+                    help="storage of the Chebyshev vectors in the timed solve (default FP64 throughout)")
+    ap.add_argument("--variants", type=int, default=1,
+                    help="1: also time FP32/BF16 Chebyshev and other preconditioners on the same problem")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

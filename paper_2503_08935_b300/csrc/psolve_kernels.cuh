@@ -234,7 +234,11 @@ __device__ __forceinline__ void flush_unit(double (&acc)[ND], double *sred, doub
 // Stencil march over chunks [c0, c1) of one tile.
 // Op provides: types C (arithmetic), U (own-column value), PW (pointwise
 // operands); ND; BLOCKED; U load(idx); C sv(U); PW pw(bool, idx);
-// void emit(idx, C au, U uc, PW, acc).
+// void emit(idx, C u, C sx, C sy, C sz, U uc, PW, acc) with u the centre value
+// and sx, sy, sz the sums of its two neighbours along x, y, z, so that
+// (A u) = cc u - cx sx - cy sy - cz sz (Eq. 3 / Eq. 6).  Each operation folds
+// its own constants into these terms: on B300 the FP64 pipe (2 FMA per clock
+// per SM), not HBM, bounds the FP64 kernels, so every FP64 instruction counts.
 // ------------------------------------------------------------------------
 template <class Op>
 __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, int c0, int c1,
@@ -280,8 +284,6 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
         oks = (j % D.by) != 0;
         okn = (j % D.by) != D.by - 1;
     }
-    const C cx = (C)D.cx, cy = (C)D.cy, cz = (C)D.cz, cc = (C)D.cc;
-
     const int kb = c0 * zc;
     const int ke = min(nz, c1 * zc);
 
@@ -321,8 +323,7 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
                 if (kk == 0) dn = C(0);
                 if (kk == D.bz - 1) un = C(0);
             }
-            const C au = cc * op.sv(uc) - cx * (w + e) - cy * (so + no) - cz * (dn + un);
-            op.emit(col + k * plane, au, uc, pw, acc);
+            op.emit(col + k * plane, op.sv(uc), w + e, so + no, dn + un, uc, pw, acc);
         }
         C *sn = sp + (buf ^ 1) * SPL;
         sn[me] = op.sv(up);
@@ -530,8 +531,6 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
         oks = (j % D.by) != 0;
         okn = (j % D.by) != D.by - 1;
     }
-    const C cx = (C)D.cx, cy = (C)D.cy, cz = (C)D.cz, cc = (C)D.cc;
-
     const int kb = c0 * zc;
     const int ke = min(nz, c1 * zc);
     const int q0 = kb - 1, q1 = ke; // stencil-input planes q0..q1, pointwise planes kb..ke-1
@@ -608,8 +607,7 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
             stage_ptrs<Op>(stage_of(k), h, p);
             const U uc = op.load_s(h, me);
             const PW pw = op.pw_s(p, mp);
-            const C au = cc * op.sv(uc) - cx * (w + e) - cy * (so + no) - cz * (dn + un);
-            op.emit(col + k * plane, au, uc, pw, acc);
+            op.emit(col + k * plane, op.sv(uc), w + e, so + no, dn + un, uc, pw, acc);
         }
         __syncthreads(); // stage of plane k-1 (and its u plane) is free
         if (tid == 0 && k - 1 + S <= q1 && !*s_dead) {
@@ -754,6 +752,13 @@ constexpr int engine_dyn_smem()
 // ------------------------------------------------------------------------
 struct NoPW {};
 
+// A u = cc u - cx sx - cy sy - cz sz: 1 multiply + 3 fused multiply-adds.
+template <class C>
+__device__ __forceinline__ C apply_A_terms(C cc, C cx, C cy, C cz, C u, C sx, C sy, C sz)
+{
+    return fma(-cz, sz, fma(-cy, sy, fma(-cx, sx, cc * u)));
+}
+
 // Chebyshev sweep 1 (Algorithm 2, first two steps) on a right-hand side u
 // that is itself formed point by point from FP64 vectors:
 //   SIDE_P: u = p_{i-1} = r + beta (p_{i-2} - omega w)   (Alg. 1, last line;
@@ -783,7 +788,7 @@ struct OpCiFirst {
     void *bc, *out;
     double beta, omega, alpha;
     int first, degree;
-    C tinv, coef1;
+    C tinv, a_u, a_x, a_y, a_z;
     __device__ OpCiFirst(const Desc &D, const KArgs &a, Scal *sc)
     {
         const int iter = ld_flag(&sc->iter);
@@ -810,7 +815,13 @@ struct OpCiFirst {
         alpha = ld_scal(&sc->alpha);
         degree = D.degree;
         tinv = (C)D.theta_inv;
-        coef1 = (C)(D.two_over_delta * D.rho[1]);
+        // y_1 = (2 rho_1/delta)(2u - A u / theta)
+        //     = c (2 - cc/theta) u + (c/theta)(cx sx + cy sy + cz sz),  c = 2 rho_1/delta
+        const double c = D.two_over_delta * D.rho[1];
+        a_u = (C)(c * (2.0 - D.cc * D.theta_inv));
+        a_x = (C)(c * D.theta_inv * D.cx);
+        a_y = (C)(c * D.theta_inv * D.cy);
+        a_z = (C)(c * D.theta_inv * D.cz);
     }
     __device__ __forceinline__ double load(int idx) const
     {
@@ -835,14 +846,14 @@ struct OpCiFirst {
     __device__ __forceinline__ PW pw(bool, int) const { return PW{}; }
     __device__ __forceinline__ PW pw_s(const void *const *, int) const { return PW{}; }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, C au, double uc, const PW &, double (&acc)[NA]) const
+    __device__ __forceinline__ void emit(int idx, C b, C sx, C sy, C sz, double uc, const PW &,
+                                         double (&acc)[NA]) const
     {
         uout[idx] = uc;
         if constexpr (SIDE == SIDE_S) acc[0] += uc * uc;
-        const C b = sv(uc);
         if constexpr (MIXED) E::st(bc, idx, b);
         if (degree == 0) E::st(out, idx, b * tinv);
-        else E::st(out, idx, coef1 * (C(2) * b - au * tinv));
+        else E::st(out, idx, fma(a_z, sz, fma(a_y, sy, fma(a_x, sx, a_u * b))));
     }
 };
 
@@ -868,7 +879,7 @@ struct OpCiSweep {
     int nh, np, hrole[NH], prole[NP];
     const void *y, *bv, *zv;
     void *out;
-    C tinv, tod, tsig, rk, rk1;
+    C c_y, c_b, c_z, c_x, c_yy, c_zz;
     int k;
     __device__ OpCiSweep(const Desc &D, const KArgs &a, Scal *sc)
     {
@@ -883,11 +894,16 @@ struct OpCiSweep {
         np = a.k >= 3 ? 2 : 1;
         prole[0] = resolve_role(a.b, iter);
         prole[1] = a.z;
-        tinv = (C)D.theta_inv;
-        tod = (C)D.two_over_delta;
-        tsig = (C)D.two_sigma;
-        rk = (C)D.rho[a.k];
-        rk1 = (C)D.rho[a.k - 1];
+        // w = rho_k (2 sigma y + (2/delta)(b - A y) - rho_{k-1} z) with A y expanded:
+        //   = rho_k (2 sigma - (2/delta) cc) y + rho_k (2/delta) b - rho_k rho_{k-1} z
+        //     + rho_k (2/delta)(cx sx + cy sy + cz sz);  z = b/theta when k = 2
+        const double rk = D.rho[a.k], rk1 = D.rho[a.k - 1], tod = D.two_over_delta;
+        c_y = (C)(rk * (D.two_sigma - tod * D.cc));
+        c_b = (C)(a.k == 2 ? rk * tod - rk * rk1 * D.theta_inv : rk * tod);
+        c_z = (C)(-rk * rk1);
+        c_x = (C)(rk * tod * D.cx);
+        c_yy = (C)(rk * tod * D.cy);
+        c_zz = (C)(rk * tod * D.cz);
     }
     __device__ __forceinline__ C load(int idx) const { return E::ld(y, idx); }
     __device__ __forceinline__ C load_s(const void *const *h, int x) const { return E::lds(h[0], x); }
@@ -908,10 +924,11 @@ struct OpCiSweep {
         return v;
     }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, C au, C yc, const PW &p, double (&)[NA]) const
+    __device__ __forceinline__ void emit(int idx, C yc, C sx, C sy, C sz, C, const PW &p, double (&)[NA]) const
     {
-        const C z = (k == 2) ? p.b * tinv : p.z;
-        E::st(out, idx, rk * (tsig * yc + tod * (p.b - au) - rk1 * z));
+        C v = fma(c_b, p.b, c_y * yc);
+        if (k >= 3) v = fma(c_z, p.z, v);
+        E::st(out, idx, fma(c_zz, sz, fma(c_yy, sy, fma(c_x, sx, v))));
     }
 };
 
@@ -931,6 +948,7 @@ struct OpStencilDot {
     const void *ph;
     const double *rt;
     double *w;
+    double cc, cx, cy, cz;
     __device__ OpStencilDot(const Desc &D, const KArgs &a, Scal *)
     {
         ph = D.vec[a.in];
@@ -938,6 +956,7 @@ struct OpStencilDot {
         w = (double *)D.vec[ROLE_W];
         hrole[0] = a.in;
         prole[0] = ROLE_RT;
+        cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
     }
     __device__ __forceinline__ double load(int idx) const { return (double)Elem<T>::ld(ph, idx); }
     __device__ __forceinline__ double load_s(const void *const *h, int x) const
@@ -948,8 +967,10 @@ struct OpStencilDot {
     __device__ __forceinline__ double sv(double u) const { return u; }
     __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? __ldg(rt + idx) : 0.0; }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, double au, double, double rtv, double (&acc)[NA]) const
+    __device__ __forceinline__ void emit(int idx, double u, double sx, double sy, double sz, double, double rtv,
+                                         double (&acc)[NA]) const
     {
+        const double au = apply_A_terms(cc, cx, cy, cz, u, sx, sy, sz);
         w[idx] = au;
         acc[0] += rtv * au;
     }
@@ -971,6 +992,7 @@ struct OpStencil2Dot {
     const void *rh;
     const double *s;
     double *t;
+    double cc, cx, cy, cz;
     __device__ OpStencil2Dot(const Desc &D, const KArgs &a, Scal *)
     {
         rh = D.vec[a.in];
@@ -978,6 +1000,7 @@ struct OpStencil2Dot {
         t = (double *)D.vec[ROLE_T];
         hrole[0] = a.in;
         prole[0] = ROLE_S;
+        cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
     }
     __device__ __forceinline__ double load(int idx) const { return (double)Elem<T>::ld(rh, idx); }
     __device__ __forceinline__ double load_s(const void *const *h, int x) const
@@ -988,8 +1011,10 @@ struct OpStencil2Dot {
     __device__ __forceinline__ double sv(double u) const { return u; }
     __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? s[idx] : 0.0; }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, double au, double, double sv_, double (&acc)[NA]) const
+    __device__ __forceinline__ void emit(int idx, double u, double sx, double sy, double sz, double, double sv_,
+                                         double (&acc)[NA]) const
     {
+        const double au = apply_A_terms(cc, cx, cy, cz, u, sx, sy, sz);
         t[idx] = au;
         acc[0] += au * sv_;
         acc[1] += au * au;
@@ -1011,12 +1036,14 @@ struct OpApplyA {
     int nh = 1, np = 0, hrole[NH], prole[1];
     const double *u;
     double *v;
+    double cc, cx, cy, cz;
     __device__ OpApplyA(const Desc &D, const KArgs &a, Scal *)
     {
         u = (const double *)D.vec[a.in];
         v = (double *)D.vec[a.out];
         hrole[0] = a.in;
         prole[0] = 0;
+        cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
     }
     __device__ __forceinline__ double load(int idx) const { return __ldg(u + idx); }
     __device__ __forceinline__ double load_s(const void *const *h, int x) const { return Elem<double>::lds(h[0], x); }
@@ -1024,9 +1051,10 @@ struct OpApplyA {
     __device__ __forceinline__ PW pw(bool, int) const { return PW{}; }
     __device__ __forceinline__ PW pw_s(const void *const *, int) const { return PW{}; }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, double au, double, const PW &, double (&)[NA]) const
+    __device__ __forceinline__ void emit(int idx, double uu, double sx, double sy, double sz, double, const PW &,
+                                         double (&)[NA]) const
     {
-        v[idx] = au;
+        v[idx] = apply_A_terms(cc, cx, cy, cz, uu, sx, sy, sz);
     }
 };
 
@@ -1047,6 +1075,7 @@ struct OpResidual {
     int nh = 1, np = 1, hrole[NH], prole[NP];
     const double *x, *b;
     double *r, *rt;
+    double cc, cx, cy, cz;
     __device__ OpResidual(const Desc &D, const KArgs &, Scal *)
     {
         x = (const double *)D.vec[ROLE_X];
@@ -1055,6 +1084,7 @@ struct OpResidual {
         rt = (double *)D.vec[ROLE_RT];
         hrole[0] = ROLE_X;
         prole[0] = ROLE_B;
+        cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
     }
     __device__ __forceinline__ double load(int idx) const { return x[idx]; }
     __device__ __forceinline__ double load_s(const void *const *h, int x_) const { return Elem<double>::lds(h[0], x_); }
@@ -1062,9 +1092,10 @@ struct OpResidual {
     __device__ __forceinline__ double sv(double u) const { return u; }
     __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? __ldg(b + idx) : 0.0; }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, double au, double, double bv, double (&acc)[NA]) const
+    __device__ __forceinline__ void emit(int idx, double u, double sx, double sy, double sz, double, double bv,
+                                         double (&acc)[NA]) const
     {
-        const double rv = bv - au;
+        const double rv = bv - apply_A_terms(cc, cx, cy, cz, u, sx, sy, sz);
         if constexpr (INIT) {
             r[idx] = rv;
             rt[idx] = rv;
