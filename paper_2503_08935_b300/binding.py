@@ -325,3 +325,75 @@ def dot_noalloc(a, b, stream=None) -> float:
     if st != OK:
         raise PsolveError(st, "psolve_dot_noalloc")
     return res.value
+
+
+class Server:
+    """Continuous-batching server (psolve_server_create / submit / poll / destroy).
+
+    Requests of different grid sizes share every kernel launch; they are
+    admitted at round boundaries while slots and the memory budget allow.
+    The caller keeps b and x alive until the request's poll is final, and must
+    make b ready on the server's stream before submitting."""
+
+    def __init__(self, budget_bytes, max_slots=64, precond=PC_CHEB, degree=8, cheb_prec=FP64, stream=None):
+        srv = ctypes.c_void_p()
+        self._stream = _stream_handle(stream)
+        st = lib().psolve_server_create(float(budget_bytes), int(max_slots), int(precond), int(degree),
+                                        int(cheb_prec), self._stream, ctypes.byref(srv))
+        if st != OK:
+            raise PsolveError(st, "psolve_server_create")
+        self.srv = srv
+
+    def submit(self, b, x, h=None, rtol=1e-10, maxit=2000, opts: Opts | None = None, **opt_kw) -> int:
+        nz, ny, nx = b.shape
+        _check_vec(b, b.shape)
+        _check_vec(x, b.shape)
+        if h is None:
+            h = (1.0 / (nx + 1), 1.0 / (ny + 1), 1.0 / (nz + 1))
+        grid = (ctypes.c_int64 * 3)(nx, ny, nz)
+        hh = (ctypes.c_double * 3)(*[float(v) for v in h])
+        o = opts if opts is not None else default_opts(**opt_kw)
+        t = ctypes.c_uint64()
+        st = lib().psolve_submit(self.srv, grid, hh, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(o),
+                                 ctypes.byref(t))
+        if st != OK:
+            raise PsolveError(st, "psolve_submit")
+        return t.value
+
+    def poll(self, ticket):
+        """(status, SolveInfo or None): status PENDING while the request runs."""
+        r = Result()
+        st = lib().psolve_poll(self.srv, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if st == PENDING:
+            return st, None
+        if st == E_ARG:
+            raise PsolveError(st, "psolve_poll")
+        return st, _info(r)
+
+    def wait(self, ticket, timeout=120.0, interval=1e-4):
+        import time
+        t0 = time.monotonic()
+        while True:
+            st, info = self.poll(ticket)
+            if st != PENDING:
+                return info
+            if time.monotonic() - t0 > timeout:
+                raise TimeoutError(f"request {ticket} still pending after {timeout} s")
+            time.sleep(interval)
+
+    def close(self):
+        if getattr(self, "srv", None):
+            lib().psolve_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

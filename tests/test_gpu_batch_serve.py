@@ -1,0 +1,100 @@
+"""Batched and served solves: each problem's result is bitwise the result of
+solving it alone, whatever else shares the launches; the server admits work
+as memory frees up and rejects requests that cannot fit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2503_08935_b300 import binding as B
+from paper_2503_08935_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.lib()
+
+
+def solo(shape, b, precond, degree, prec, rtol=1e-10, **kw):
+    x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, cheb_prec=prec, **kw) as s:
+        info = s.solve(b, x, rtol=rtol, maxit=500, precond=precond, degree=degree)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+def test_served_results_bitwise_equal_alone(prec):
+    shapes = [(24, 16, 40), (17, 9, 33), (32, 32, 32), (8, 40, 16), (20, 20, 21), (48, 24, 64)]
+    bs = [torch.from_numpy(I.rhs_uniform(sh, seed=50 + q)).to(DEV) for q, sh in enumerate(shapes)]
+    xs = [torch.zeros(sh, dtype=torch.float64, device=DEV) for sh in shapes]
+    torch.cuda.synchronize()
+    with B.Server(budget_bytes=2 << 30, max_slots=4, precond=B.PC_CHEB, degree=6, cheb_prec=prec) as srv:
+        tickets = [srv.submit(b, x, rtol=1e-10, maxit=500) for b, x in zip(bs, xs)]
+        infos = [srv.wait(t) for t in tickets]
+    torch.cuda.synchronize()
+    for q, sh in enumerate(shapes):
+        xa, ia = solo(sh, bs[q], B.PC_CHEB, 6, prec)
+        assert infos[q].status == B.OK and infos[q].iterations == ia.iterations
+        assert np.array_equal(xs[q].cpu().numpy(), xa)
+        assert infos[q].rel_res_true <= 2e-10
+
+
+def test_server_admits_under_a_tight_budget_and_rejects_oversized():
+    shapes = [(32, 32, 40), (32, 32, 40), (24, 24, 24), (32, 32, 40)]
+    bs = [torch.from_numpy(I.rhs_uniform(sh, seed=60 + q)).to(DEV) for q, sh in enumerate(shapes)]
+    xs = [torch.zeros(sh, dtype=torch.float64, device=DEV) for sh in shapes]
+    torch.cuda.synchronize()
+    one = 12 * 8 * 32 * 32 * 40  # roughly one 32x32x40 workspace: forces one-at-a-time admission
+    with B.Server(budget_bytes=1.6 * one, max_slots=8, precond=B.PC_CHEB, degree=4) as srv:
+        tickets = [srv.submit(b, x, rtol=1e-10) for b, x in zip(bs, xs)]
+        big = torch.zeros((64, 64, 64), dtype=torch.float64, device=DEV)
+        with pytest.raises(B.PsolveError) as e:
+            srv.submit(big, big)
+        assert e.value.status == B.REJECTED
+        infos = [srv.wait(t) for t in tickets]
+    for q, sh in enumerate(shapes):
+        assert infos[q].status == B.OK
+        xo, ro = O.bicgstab(bs[q].cpu().numpy(), I.default_h(sh), rtol=1e-10, maxit=500, precond=O.PC_CHEB,
+                            degree=4)
+        x = xs[q].cpu().numpy()
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def test_served_requests_join_while_others_run():
+    """A request submitted while a large one is on the GPU finishes first."""
+    big_shape, small_shape = (192, 192, 192), (16, 16, 16)
+    bb = torch.from_numpy(I.rhs_uniform(big_shape, seed=70)).to(DEV)
+    xb = torch.zeros(big_shape, dtype=torch.float64, device=DEV)
+    bsm = torch.from_numpy(I.rhs_uniform(small_shape, seed=71)).to(DEV)
+    xsm = torch.zeros(small_shape, dtype=torch.float64, device=DEV)
+    torch.cuda.synchronize()
+    with B.Server(budget_bytes=4 << 30, max_slots=8, precond=B.PC_CHEB, degree=8) as srv:
+        tb = srv.submit(bb, xb, rtol=1e-12, maxit=2000)
+        import time
+        time.sleep(0.02)
+        ts = srv.submit(bsm, xsm, rtol=1e-10)
+        ism = srv.wait(ts)
+        st_big, _ = srv.poll(tb)
+        ib = srv.wait(tb)
+    assert ism.status == B.OK and ib.status == B.OK
+    assert st_big == B.PENDING  # the small one completed while the big one was still running
+    xa, ia = solo(small_shape, bsm, B.PC_CHEB, 8, B.FP64)
+    assert np.array_equal(xsm.cpu().numpy(), xa)
+
+
+def test_batch_of_mixed_sizes_config_shapes():
+    """A smaller version of the 64-grid batch: sides from {32, 48, 64, 96, 128}."""
+    shapes = I.batch_shapes(count=6, seed=2)
+    bs = [torch.from_numpy(I.rhs_uniform(sh, seed=1 + q)).to(DEV) for q, sh in enumerate(shapes)]
+    xs = [torch.zeros(sh, dtype=torch.float64, device=DEV) for sh in shapes]
+    infos = B.solve_batch(bs, xs, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8)
+    for q, sh in enumerate(shapes):
+        xa, ia = solo(sh, bs[q], B.PC_CHEB, 8, B.FP64)
+        assert infos[q].status == B.OK and infos[q].iterations == ia.iterations
+        assert np.array_equal(xs[q].cpu().numpy(), xa)
