@@ -349,6 +349,8 @@ def run_gpu(args):
     if args.variants and rank == 0:
         x_ref = x.clone()
         line["variants"] = run_variants(args, b, x_ref, stream, B, torch)
+    if args.extras != "none" and rank == 0:
+        line["configs"] = run_extras(args, B, I, torch, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_record(iters)
     solver.close()
@@ -397,6 +399,156 @@ def run_variants(args, b, x_ref, stream, B, torch):
     return out
 
 
+# --------------------------------------------------------------- extras --
+def _timed_cuda(fn, stream, torch, reps=1):
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def extra_small_latency(B, I, torch, stream, reps=200):
+    """32^3, h = 1/33, f = 3 pi^2 sin sin sin, no preconditioner, rtol 1e-10:
+    the first half step converges, so this measures per-solve latency."""
+    import math
+    shape = (32, 32, 32)
+    h = I.default_h(shape)
+    f = I.rhs_manufactured(shape)
+    b = torch.from_numpy(f).cuda()
+    x = torch.zeros_like(b)
+    with B.Solver(shape, h, stream=stream) as s:
+        for _ in range(10):
+            info = s.solve(b, x, rtol=1e-10, maxit=2000, precond=B.PC_NONE)
+        ms, info = _timed_cuda(lambda: s.solve(b, x, rtol=1e-10, maxit=2000, precond=B.PC_NONE), stream, torch,
+                               reps)
+    xh = x.cpu().numpy()
+    lam111 = 3 * 4.0 / h[0] ** 2 * math.sin(math.pi * h[0] / 2) ** 2
+    exact_discrete = f / lam111
+    exact_cont = f / (3 * math.pi ** 2)
+    import numpy as np
+    return {"workload": "32^3 manufactured sine, no preconditioner, rtol 1e-10", "us_per_solve": ms * 1e3,
+            "solves_per_s": 1e3 / ms, "iterations": info.iterations, "half_step_exit": info.half_step_exit,
+            "rel_err_vs_exact_discrete": float(np.linalg.norm(xh - exact_discrete) / np.linalg.norm(exact_discrete)),
+            "max_err_vs_continuous": float(np.max(np.abs(xh - exact_cont))),
+            "kernel_launches_per_solve": info.kernel_launches}
+
+
+def extra_batch(B, I, torch, stream, count=64):
+    """64 independent grids, sides drawn (seed 2) from {32, 48, 64, 96, 128},
+    G(CI) degree 8, FP64, rtol 1e-10: one batched solve (every launch covers
+    all unfinished grids, iterations replayed from one CUDA graph) against a
+    sequential loop of single solves of the same grids on the same GPU."""
+    shapes = I.batch_shapes(count=count, seed=2)
+    bs = [torch.from_numpy(I.rhs_uniform(sh, seed=1 + q)).cuda() for q, sh in enumerate(shapes)]
+    xs = [torch.zeros_like(b) for b in bs]
+    npts = sum(b.numel() for b in bs)
+    run = lambda: B.solve_batch(bs, xs, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8, stream=stream)
+    run()
+    ms_b, infos = _timed_cuda(run, stream, torch, 2)
+    solvers = [B.Solver(sh, stream=stream) for sh in shapes]
+
+    def seq():
+        out = []
+        for s_, b, x in zip(solvers, bs, xs):
+            out.append(s_.solve(b, x, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8))
+        return out
+    seq()
+    ms_s, infos_s = _timed_cuda(seq, stream, torch, 1)
+    for s_ in solvers:
+        s_.close()
+    same = all(a.iterations == c.iterations for a, c in zip(infos, infos_s))
+    return {"workload": f"batch of {count} grids, sides from {{32,48,64,96,128}} (seed 2), G(CI) d=8 FP64, rtol 1e-10",
+            "points_total": npts, "batched_ms": ms_b, "batched_solves_per_s": count * 1e3 / ms_b,
+            "sequential_ms": ms_s, "sequential_solves_per_s": count * 1e3 / ms_s, "speedup": ms_s / ms_b,
+            "all_ok": all(i.status == B.OK for i in infos), "iterations_equal_to_solo": same,
+            "max_iterations": max(i.iterations for i in infos)}
+
+
+def extra_serve(B, I, torch, stream, n_req, factors=(0.8,), budget=120e9, max_slots=128):
+    """Serving stream: n_req requests, sides log-uniform on [16, 256] (seed 3),
+    Poisson arrivals, FP64 outer / FP32 Chebyshev degree 8, rtol 1e-8, HBM
+    admission budget 120 GB.  The service rate mu is calibrated by submitting
+    a burst at once; the stream then runs at factor * mu.  Latency is submit
+    to result-ready, measured by the server."""
+    import time
+    import numpy as np
+    shapes, gaps = I.serving_stream(count=n_req, seed=3)
+    bs = [torch.from_numpy(I.rhs_uniform(sh, seed=4 + q)).cuda() for q, sh in enumerate(shapes)]
+    xs = [torch.zeros_like(b) for b in bs]
+    torch.cuda.synchronize()
+    out = {"workload": f"{n_req} requests, sides log-uniform [16,256] (seed 3), FP32 Chebyshev d=8, rtol 1e-8, "
+                       f"budget {budget / 1e9:.0f} GB", "mean_points": float(np.mean([b.numel() for b in bs]))}
+    with B.Server(budget, max_slots=max_slots, precond=B.PC_CHEB, degree=8, cheb_prec=B.FP32,
+                  stream=stream) as srv:
+        ncal = min(200, n_req)
+        t0 = time.perf_counter()
+        ts = [srv.submit(bs[q], xs[q], rtol=1e-8, maxit=2000) for q in range(ncal)]
+        for t in ts:
+            srv.wait(t)
+        mu = ncal / (time.perf_counter() - t0)
+        out["calibrated_mu_solves_per_s"] = mu
+        for f in factors:
+            lam = f * mu
+            arrivals = np.cumsum(gaps) / lam
+            tickets = []
+            start = time.perf_counter()
+            for q in range(n_req):
+                delay = start + arrivals[q] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(srv.submit(bs[q], xs[q], rtol=1e-8, maxit=2000))
+            infos = [srv.wait(t, timeout=600) for t in tickets]
+            wall = time.perf_counter() - start
+            lat = np.array([i.seconds for i in infos]) * 1e3
+            out[f"at_{f:.1f}_mu"] = {"offered_rate": lam, "solves_per_s": n_req / wall,
+                                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                     "mean_ms": float(lat.mean()),
+                                     "all_ok": all(i.status == B.OK for i in infos),
+                                     "max_true_residual": max(i.rel_res_true for i in infos)}
+    return out
+
+
+def extra_512_mixed(B, I, torch, stream):
+    """512^3, RHS = manufactured sine + 1e-3 U[-1,1) (seed 1), FP64 outer with
+    the Chebyshev vectors in FP64 (reference), FP32 and BF16, degree 8 and 16,
+    rtol 1e-10; error of each against the FP64 solution."""
+    shape = (512, 512, 512)
+    h = I.default_h(shape)
+    b = torch.from_numpy(I.rhs_manufactured_noisy(shape, seed=1)).cuda()
+    res = {}
+    x_ref = None
+    for name, prec, deg in [("fp64_d8", B.FP64, 8), ("fp32_d8", B.FP32, 8), ("fp32_d16", B.FP32, 16),
+                            ("bf16_d8", B.BF16, 8), ("bf16_d16", B.BF16, 16)]:
+        x = torch.zeros_like(b)
+        with B.Solver(shape, h, stream=stream, cheb_prec=prec) as s:
+            maxit = 300 if prec == B.BF16 else 1000  # BF16 storage does not converge here (see DESIGN)
+            ms, info = _timed_cuda(lambda: s.solve(b, x, rtol=1e-10, maxit=maxit, precond=B.PC_CHEB, degree=deg),
+                                   stream, torch, 1)
+        if x_ref is None:
+            x_ref = x.clone()
+        rel = float(torch.linalg.vector_norm(x - x_ref) / torch.linalg.vector_norm(x_ref))
+        res[name] = {"status": info.status_name, "time_to_rtol_ms": ms, "iterations": info.iterations,
+                     "rel_res_true": info.rel_res_true, "rel_l2_vs_fp64": rel,
+                     "model_gb_per_s": info.model_bytes / (ms * 1e-3) / 1e9}
+        del x
+    return res
+
+
+def run_extras(args, B, I, torch, stream):
+    out = {"config1_32cubed": extra_small_latency(B, I, torch, stream),
+           "config4_batch64": extra_batch(B, I, torch, stream)}
+    if args.extras == "full":
+        out["config3_512_mixed"] = extra_512_mixed(B, I, torch, stream)
+        out["config5_serving"] = extra_serve(B, I, torch, stream, 2000, factors=(0.8, 1.2))
+    else:
+        out["config5_serving"] = extra_serve(B, I, torch, stream, 300, factors=(0.8,))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,6 +560,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="storage of the Chebyshev vectors in the timed solve (default FP64 throughout)")
+    ap.add_argument("--extras", default="quick", choices=["none", "quick", "full"],
+                    help="also measure the 32^3 latency, batch-of-64 and serving configurations "
+                         "(full: 2000 served requests at 0.8 and 1.2 mu, and the 512^3 mixed-precision runs)")
     ap.add_argument("--variants", type=int, default=1,
                     help="1: also time FP32/BF16 Chebyshev and other preconditioners on the same problem")
     args = ap.parse_args()

@@ -199,6 +199,7 @@ __device__ void epilogue(const Desc &D, Scal *sc, const double (&v)[ND])
             sc->rr = rr;
             if (!isfinite(rr) || !isfinite(rho_new)) stop_with(sc, ST_NONFINITE);
             else if (rr <= sc->thr2) stop_with(sc, ST_OK);
+            else if (rr > 1e16 * sc->nb2) stop_with(sc, ST_NOT_CONVERGED); // diverged: ||r|| > 1e8 ||b||
             else if (rho_new == 0.0) stop_with(sc, ST_BREAKDOWN);
             else {
                 sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
