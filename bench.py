@@ -40,8 +40,9 @@ GOLDEN_256 = os.path.join(ROOT, "tests", "golden", "oracle_256_cheb8.json")
 NCU_SUMMARY = os.path.join(ROOT, "profiles", "ncu_ci_sweep4_256_{prec}.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2503_08935_b300", "csrc", "psolve_kernels.cuh")
 # FP64 instructions per point of a Chebyshev sweep k >= 3 as the kernel writes it:
-# three neighbour-pair sums, one multiply and five fused multiply-adds.
-SWEEP_FP64_OPS_PER_POINT = 9
+# three neighbour-pair sums, one multiply and four fused multiply-adds (exact bounds:
+# the y coefficient vanishes, see OpCiSweep).
+SWEEP_FP64_OPS_PER_POINT = 8
 
 
 def dist_env():

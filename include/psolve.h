@@ -221,6 +221,15 @@ PSOLVE_API psolve_status psolve_dot_noalloc(const int64_t grid[3], const double 
                                             const double *b_dev, uintptr_t stream,
                                             double *result_host);
 
+/* Self-check of the library's exact FP32<->FP64 conversions.  B300 runs FP64
+ * conversion instructions on its narrow FP64 pipe, so the mixed-precision
+ * kernels widen and round with integer bit operations instead (IEEE-754
+ * round to nearest even); this compares them bit for bit with the hardware
+ * conversions on `count` seeded bit patterns (including rounding ties) and
+ * stores the number of differences in *mismatches (0 expected).  No
+ * counterpart in the paper (an implementation check). */
+PSOLVE_API psolve_status psolve_selfcheck_conversions(uint64_t seed, int64_t count, int64_t *mismatches);
+
 /* ---- many independent grids at once ----------------------------------- */
 
 /* Solve `count` independent problems of (possibly) different sizes together:
@@ -252,7 +261,9 @@ PSOLVE_API psolve_status psolve_server_create(double hbm_budget_bytes, int32_t m
 
 /* Queue one solve.  grid/h as in psolve_create; rhs_dev/x_dev device
  * pointers that stay valid until psolve_poll returns non-PENDING.  opts may
- * be NULL (scales, blocks and half-step check are taken from it; x0 = 0).
+ * be NULL (blocks and half-step check are taken from it; x0 = 0; its
+ * Chebyshev scales must be 1, 1: served problems share launches, and all use
+ * the exact closed-form bounds, else PSOLVE_E_ARG).
  * *ticket identifies the request.  PSOLVE_REJECTED if the request alone
  * exceeds the memory budget. */
 PSOLVE_API psolve_status psolve_submit(psolve_server *srv, const int64_t grid[3], const double h[3],

@@ -30,7 +30,7 @@ EXPORTS = [
     "psolve_opts_default", "psolve_create", "psolve_solve", "psolve_solve_host", "psolve_destroy",
     "psolve_apply_A", "psolve_precond_apply", "psolve_dot", "psolve_cheb_interval", "psolve_solve_batch",
     "psolve_server_create", "psolve_submit", "psolve_poll", "psolve_server_destroy", "psolve_last_error",
-    "psolve_version", "psolve_dot_noalloc",
+    "psolve_version", "psolve_dot_noalloc", "psolve_selfcheck_conversions",
 ]
 
 
@@ -113,6 +113,8 @@ def lib():
         L.psolve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(Result)]
         L.psolve_server_destroy.argtypes = [P]
         L.psolve_server_destroy.restype = None
+        L.psolve_selfcheck_conversions.argtypes = [ctypes.c_uint64, ctypes.c_int64, I64P]
+        L.psolve_selfcheck_conversions.restype = ctypes.c_int32
         L.psolve_dot_noalloc.argtypes = [I64P, P, P, ctypes.c_void_p, DP]
         L.psolve_dot_noalloc.restype = ctypes.c_int32
         L.psolve_last_error.restype = ctypes.c_char_p
@@ -310,6 +312,16 @@ def solve_batch(bs, xs, hs=None, rtol=1e-10, maxit=2000, precond=PC_CHEB, degree
     if st in (E_ARG, E_OOM, E_CUDA, TIMEOUT):
         raise PsolveError(st, "psolve_solve_batch")
     return [_info(r) for r in res]
+
+
+def selfcheck_conversions(seed=1, count=1 << 26) -> int:
+    """Number of differences between the library's integer-pipe FP32<->FP64
+    conversions and the hardware conversions on `count` bit patterns."""
+    bad = ctypes.c_int64()
+    st = lib().psolve_selfcheck_conversions(int(seed), int(count), ctypes.byref(bad))
+    if st != OK:
+        raise PsolveError(st, "psolve_selfcheck_conversions")
+    return bad.value
 
 
 def dot_noalloc(a, b, stream=None) -> float:

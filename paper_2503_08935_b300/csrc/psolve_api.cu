@@ -499,6 +499,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     R.plan.precond = precond;
     R.plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
     R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : P.prec;
+    R.plan.exact_bounds = c->opts.lmin_scale == 1.0 && c->opts.lmax_scale == 1.0;
     R.use_graph = c->opts.use_graph != 0;
     R.timing = c->opts.timing != 0;
     R.npts = (double)P.npts();
@@ -660,6 +661,7 @@ psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, 
     plan.precond = precond;
     plan.degree = degree;
     plan.prec = P.prec;
+    plan.exact_bounds = c->opts.lmin_scale == 1.0 && c->opts.lmax_scale == 1.0;
     Launcher L = ctx_launcher(c);
     enqueue_precond(L, plan);
     PS_CK(L.err);
@@ -828,6 +830,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     R.plan.precond = precond;
     R.plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
     R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : o.cheb_prec;
+    R.plan.exact_bounds = o.lmin_scale == 1.0 && o.lmax_scale == 1.0;
     R.use_graph = o.use_graph != 0;
     R.timing = o.timing != 0;
     R.npts = 0;

@@ -164,8 +164,8 @@ static constexpr bool is_mixed() { return !std::is_same<T, double>::value; }
 
 // Chebyshev sweeps k = 2..d (Algorithm 2 loop).  y_k overwrites y_{k-2}'s
 // buffer (read only at the same point), and the last sweep writes `final_role`.
-template <class T, class TB, bool BLK>
-static void sweeps(Launcher &L, int d, int side, int brole, int final_role, int skip)
+template <class T, class TB, bool BLK, bool WY>
+static void sweeps_impl(Launcher &L, int d, int side, int brole, int final_role, int skip)
 {
     const double c = sizeof(T), cb = sizeof(TB);
     for (int k = 2; k <= d; ++k) {
@@ -176,13 +176,20 @@ static void sweeps(Launcher &L, int d, int side, int brole, int final_role, int 
         a.z = (k % 2 == 0) ? ROLE_YB : ROLE_YA;
         a.out = (k == d) ? final_role : a.z;
         a.b = brole;
-        if (k == 2) L.go<OpCiSweep<T, TB, BLK>>(PSOLVE_K_CI_SWEEP3, side, a, c + cb + c);
-        else L.go<OpCiSweep<T, TB, BLK>>(PSOLVE_K_CI_SWEEP4, side, a, c + cb + c + c);
+        if (k == 2) L.go<OpCiSweep<T, TB, BLK, WY>>(PSOLVE_K_CI_SWEEP3, side, a, c + cb + c);
+        else L.go<OpCiSweep<T, TB, BLK, WY>>(PSOLVE_K_CI_SWEEP4, side, a, c + cb + c + c);
     }
 }
 
+template <class T, class TB, bool BLK>
+static void sweeps(Launcher &L, int d, int side, int brole, int final_role, int skip, bool exact_bounds)
+{
+    if (exact_bounds) sweeps_impl<T, TB, BLK, false>(L, d, side, brole, final_role, skip);
+    else sweeps_impl<T, TB, BLK, true>(L, d, side, brole, final_role, skip);
+}
+
 template <class T, bool BLK>
-static void iteration_cheb(Launcher &L, int d)
+static void iteration_cheb(Launcher &L, int d, bool eb)
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
@@ -196,7 +203,7 @@ static void iteration_cheb(Launcher &L, int d)
         const double rd = (L.iter == 1) ? 8.0 : 24.0;
         L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, rd + 8.0 + (MIX ? c : 0.0) + c);
     }
-    sweeps<T, TB, BLK>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP);
+    sweeps<T, TB, BLK>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP, eb);
     {
         KArgs a{};
         a.skip = SKIP_STOP;
@@ -211,7 +218,7 @@ static void iteration_cheb(Launcher &L, int d)
         a.out = (d <= 1) ? ROLE_RH : ROLE_YA;
         L.go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, 24.0 + (MIX ? c : 0.0) + c);
     }
-    sweeps<T, TB, BLK>(L, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF);
+    sweeps<T, TB, BLK>(L, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF, eb);
     {
         KArgs a{};
         a.skip = SKIP_STOP | SKIP_HALF;
@@ -269,16 +276,16 @@ void enqueue_iteration(Launcher &L, const Plan &plan)
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
     switch (plan.prec) {
     case PSOLVE_FP32:
-        if (blk) iteration_cheb<float, true>(L, plan.degree);
-        else iteration_cheb<float, false>(L, plan.degree);
+        if (blk) iteration_cheb<float, true>(L, plan.degree, plan.exact_bounds);
+        else iteration_cheb<float, false>(L, plan.degree, plan.exact_bounds);
         break;
     case PSOLVE_BF16:
-        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree);
-        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree);
+        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds);
+        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds);
         break;
     default:
-        if (blk) iteration_cheb<double, true>(L, plan.degree);
-        else iteration_cheb<double, false>(L, plan.degree);
+        if (blk) iteration_cheb<double, true>(L, plan.degree, plan.exact_bounds);
+        else iteration_cheb<double, false>(L, plan.degree, plan.exact_bounds);
         break;
     }
 }
@@ -320,7 +327,7 @@ void enqueue_dot(Launcher &L)
 // reads v through ROLE_R (the caller points ROLE_R at v and sets first = 1,
 // iter = 0), then the sweeps, then a widening copy of p^ into ROLE_V.
 template <class T, bool BLK>
-static void precond_cheb(Launcher &L, int d)
+static void precond_cheb(Launcher &L, int d, bool eb)
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
@@ -329,7 +336,7 @@ static void precond_cheb(Launcher &L, int d)
     a.in = ROLE_PCUR;
     a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
     L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
-    sweeps<T, TB, BLK>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0);
+    sweeps<T, TB, BLK>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, eb);
     KArgs w{};
     w.in = ROLE_PH;
     w.out = ROLE_V;
@@ -341,16 +348,16 @@ void enqueue_precond(Launcher &L, const Plan &plan)
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
     switch (plan.prec) {
     case PSOLVE_FP32:
-        if (blk) precond_cheb<float, true>(L, plan.degree);
-        else precond_cheb<float, false>(L, plan.degree);
+        if (blk) precond_cheb<float, true>(L, plan.degree, plan.exact_bounds);
+        else precond_cheb<float, false>(L, plan.degree, plan.exact_bounds);
         break;
     case PSOLVE_BF16:
-        if (blk) precond_cheb<__nv_bfloat16, true>(L, plan.degree);
-        else precond_cheb<__nv_bfloat16, false>(L, plan.degree);
+        if (blk) precond_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds);
+        else precond_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds);
         break;
     default:
-        if (blk) precond_cheb<double, true>(L, plan.degree);
-        else precond_cheb<double, false>(L, plan.degree);
+        if (blk) precond_cheb<double, true>(L, plan.degree, plan.exact_bounds);
+        else precond_cheb<double, false>(L, plan.degree, plan.exact_bounds);
         break;
     }
 }

@@ -44,9 +44,10 @@ struct Plan {
     int precond = PSOLVE_PC_NONE;
     int degree = 0;
     int prec = PSOLVE_FP64;
+    bool exact_bounds = false; // scales (1, 1): the sweeps' y coefficient is zero
     bool operator==(const Plan &o) const
     {
-        return precond == o.precond && degree == o.degree && prec == o.prec;
+        return precond == o.precond && degree == o.degree && prec == o.prec && exact_bounds == o.exact_bounds;
     }
 };
 

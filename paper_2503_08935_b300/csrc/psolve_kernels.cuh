@@ -34,6 +34,42 @@
 namespace psolve {
 
 // ------------------------------------------------------------------------
+// Exact conversions on the integer pipe.  B300 executes FP64 conversions on
+// its narrow FP64 pipe (2 instructions per clock per SM), where they compete
+// with the FP64 arithmetic of the outer iteration; these IEEE-754 bit
+// manipulations give the same results on the ALU pipe.  Zeros, subnormals,
+// infinities, NaNs and out-of-range values (rare) take the hardware path.
+// ------------------------------------------------------------------------
+// float -> double, exact: re-bias the exponent (1023 - 127 = 896) and move
+// the 23-bit mantissa to the top of the 52-bit field.
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    const uint32_t lo = u << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float, round to nearest even: keep 23 of the 52 mantissa bits,
+// round on the 29 dropped bits (ties to even); a carry out of the mantissa
+// moves into the exponent (and to infinity at the top), as IEEE-754 rounding
+// does.  Results that would be subnormal or overflow take the hardware path.
+__device__ __forceinline__ float d2f_rn(double d)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(d);
+    const uint32_t lo = (uint32_t)__double2loint(d);
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    if (e < 897u || e > 1150u) return __double2float_rn(d); // float exponent outside [1, 254]
+    const uint32_t m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rest = lo & 0x1fffffffu;
+    uint32_t r = (hi & 0x80000000u) | ((e - 896u) << 23) | m23;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) r += 1u;
+    return __uint_as_float(r);
+}
+
+// ------------------------------------------------------------------------
 // Storage types of the Chebyshev vectors and their arithmetic type.
 // ------------------------------------------------------------------------
 template <class T> struct Elem;
@@ -41,6 +77,8 @@ template <> struct Elem<double> {
     using C = double;
     static __device__ __forceinline__ double ld(const void *p, int i) { return __ldg((const double *)p + i); }
     static __device__ __forceinline__ double lds(const void *p, int i) { return ((const double *)p)[i]; }
+    static __device__ __forceinline__ double wide(const void *p, int i) { return ld(p, i); }
+    static __device__ __forceinline__ double wides(const void *p, int i) { return lds(p, i); }
     static __device__ __forceinline__ void st(void *p, int i, double v) { ((double *)p)[i] = v; }
     static __device__ __forceinline__ double round(double v) { return v; }
 };
@@ -48,8 +86,10 @@ template <> struct Elem<float> {
     using C = float;
     static __device__ __forceinline__ float ld(const void *p, int i) { return __ldg((const float *)p + i); }
     static __device__ __forceinline__ float lds(const void *p, int i) { return ((const float *)p)[i]; }
+    static __device__ __forceinline__ double wide(const void *p, int i) { return f2d_exact(ld(p, i)); }
+    static __device__ __forceinline__ double wides(const void *p, int i) { return f2d_exact(lds(p, i)); }
     static __device__ __forceinline__ void st(void *p, int i, float v) { ((float *)p)[i] = v; }
-    static __device__ __forceinline__ float round(double v) { return (float)v; }
+    static __device__ __forceinline__ float round(double v) { return d2f_rn(v); }
 };
 template <> struct Elem<__nv_bfloat16> {
     using C = float;
@@ -61,13 +101,15 @@ template <> struct Elem<__nv_bfloat16> {
     {
         return __bfloat162float(((const __nv_bfloat16 *)p)[i]);
     }
+    static __device__ __forceinline__ double wide(const void *p, int i) { return f2d_exact(ld(p, i)); }
+    static __device__ __forceinline__ double wides(const void *p, int i) { return f2d_exact(lds(p, i)); }
     static __device__ __forceinline__ void st(void *p, int i, float v)
     {
         ((__nv_bfloat16 *)p)[i] = __float2bfloat16_rn(v);
     }
     static __device__ __forceinline__ float round(double v)
     {
-        return __bfloat162float(__float2bfloat16_rn((float)v));
+        return __bfloat162float(__float2bfloat16_rn(d2f_rn(v)));
     }
 };
 
@@ -862,7 +904,7 @@ struct OpCiFirst {
 //   w = rho_k (2 sigma y + (2/delta)(b - A y) - rho_{k-1} z),
 // y = y_{k-1} (stencil input), z = y_{k-2} (z = b/theta when k = 2).
 // TB is the storage type of the CI right-hand side b.
-template <class T, class TB, bool BLK>
+template <class T, class TB, bool BLK, bool WITH_Y = true>
 struct OpCiSweep {
     using E = Elem<T>;
     using EB = Elem<TB>;
@@ -899,6 +941,9 @@ struct OpCiSweep {
         //   = rho_k (2 sigma - (2/delta) cc) y + rho_k (2/delta) b - rho_k rho_{k-1} z
         //     + rho_k (2/delta)(cx sx + cy sy + cz sz);  z = b/theta when k = 2
         const double rk = D.rho[a.k], rk1 = D.rho[a.k - 1], tod = D.two_over_delta;
+        // WITH_Y = false: exact closed-form bounds, where lambda_min + lambda_max = 2 cc
+        // (Eq. 9: sin^2 a + cos^2 a = 1 per axis, for the grid and for every block), so
+        // theta = cc and the y coefficient vanishes; the kernel then skips its multiply.
         c_y = (C)(rk * (D.two_sigma - tod * D.cc));
         c_b = (C)(a.k == 2 ? rk * tod - rk * rk1 * D.theta_inv : rk * tod);
         c_z = (C)(-rk * rk1);
@@ -927,7 +972,9 @@ struct OpCiSweep {
     template <int NA>
     __device__ __forceinline__ void emit(int idx, C yc, C sx, C sy, C sz, C, const PW &p, double (&)[NA]) const
     {
-        C v = fma(c_b, p.b, c_y * yc);
+        C v;
+        if constexpr (WITH_Y) v = fma(c_b, p.b, c_y * yc);
+        else v = c_b * p.b;
         if (k >= 3) v = fma(c_z, p.z, v);
         E::st(out, idx, fma(c_zz, sz, fma(c_yy, sy, fma(c_x, sx, v))));
     }
@@ -944,7 +991,8 @@ struct OpStencilDot {
     using TH = T;
     using TP = double;
     static constexpr int NH = 1, NP = 1;
-    static constexpr bool XFORM = false;
+    // a narrower p^ is widened once per staged cell instead of at all 7 reads
+    static constexpr bool XFORM = !std::is_same<T, double>::value;
     int nh = 1, np = 1, hrole[NH], prole[NP];
     const void *ph;
     const double *rt;
@@ -959,11 +1007,8 @@ struct OpStencilDot {
         prole[0] = ROLE_RT;
         cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
     }
-    __device__ __forceinline__ double load(int idx) const { return (double)Elem<T>::ld(ph, idx); }
-    __device__ __forceinline__ double load_s(const void *const *h, int x) const
-    {
-        return (double)Elem<T>::lds(h[0], x);
-    }
+    __device__ __forceinline__ double load(int idx) const { return Elem<T>::wide(ph, idx); }
+    __device__ __forceinline__ double load_s(const void *const *h, int x) const { return Elem<T>::wides(h[0], x); }
     __device__ __forceinline__ double pw_s(const void *const *p, int x) const { return Elem<double>::lds(p[0], x); }
     __device__ __forceinline__ double sv(double u) const { return u; }
     __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? __ldg(rt + idx) : 0.0; }
@@ -988,7 +1033,7 @@ struct OpStencil2Dot {
     using TH = T;
     using TP = double;
     static constexpr int NH = 1, NP = 1;
-    static constexpr bool XFORM = false;
+    static constexpr bool XFORM = !std::is_same<T, double>::value;
     int nh = 1, np = 1, hrole[NH], prole[NP];
     const void *rh;
     const double *s;
@@ -1003,11 +1048,8 @@ struct OpStencil2Dot {
         prole[0] = ROLE_S;
         cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
     }
-    __device__ __forceinline__ double load(int idx) const { return (double)Elem<T>::ld(rh, idx); }
-    __device__ __forceinline__ double load_s(const void *const *h, int x) const
-    {
-        return (double)Elem<T>::lds(h[0], x);
-    }
+    __device__ __forceinline__ double load(int idx) const { return Elem<T>::wide(rh, idx); }
+    __device__ __forceinline__ double load_s(const void *const *h, int x) const { return Elem<T>::wides(h[0], x); }
     __device__ __forceinline__ double pw_s(const void *const *p, int x) const { return Elem<double>::lds(p[0], x); }
     __device__ __forceinline__ double sv(double u) const { return u; }
     __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? s[idx] : 0.0; }
@@ -1160,12 +1202,12 @@ struct OpUpdate {
     template <int NA>
     __device__ __forceinline__ void emit(int idx, double (&acc)[NA]) const
     {
-        const double pv = (double)Elem<T>::ld(ph, idx);
+        const double pv = Elem<T>::wide(ph, idx);
         if (half) {
             x[idx] = x[idx] + alpha * pv;
             return;
         }
-        const double rv = (double)Elem<T>::ld(rh, idx);
+        const double rv = Elem<T>::wide(rh, idx);
         const double sv = __ldg(s + idx), tv = __ldg(t + idx), rtv = __ldg(rt + idx);
         x[idx] = x[idx] + alpha * pv + omega * rv;
         const double rn = sv - omega * tv;
@@ -1260,7 +1302,7 @@ struct OpWiden {
     template <int NA>
     __device__ __forceinline__ void emit(int idx, double (&)[NA]) const
     {
-        out[idx] = (double)Elem<T>::ld(in, idx);
+        out[idx] = Elem<T>::wide(in, idx);
     }
 };
 

@@ -411,6 +411,7 @@ psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, i
     s->plan.precond = precond;
     s->plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
     s->plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : cheb_prec;
+    s->plan.exact_bounds = true; // requests use the exact closed-form bounds (checked at submit)
     s->budget = hbm_budget_bytes;
     s->pool_bytes = (size_t)hbm_budget_bytes;
     s->slots.resize(max_slots);
@@ -469,6 +470,10 @@ psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const doubl
     psolve_opts o;
     psolve_opts_default(&o);
     if (opts) o = *opts;
+    if (o.lmin_scale != 1.0 || o.lmax_scale != 1.0) {
+        set_error("served requests use the exact closed-form Chebyshev bounds (scales 1, 1)");
+        return PSOLVE_E_ARG;
+    }
     Request r;
     Problem &P = r.prob;
     for (int d = 0; d < 3; ++d) {

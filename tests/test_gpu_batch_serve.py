@@ -57,6 +57,9 @@ def test_server_admits_under_a_tight_budget_and_rejects_oversized():
         with pytest.raises(B.PsolveError) as e:
             srv.submit(big, big)
         assert e.value.status == B.REJECTED
+        with pytest.raises(B.PsolveError) as e:  # served requests share the exact bounds
+            srv.submit(bs[0], xs[0], lmin_scale=100.0, lmax_scale=1 - 1e-4)
+        assert e.value.status == B.E_ARG
         infos = [srv.wait(t) for t in tickets]
     for q, sh in enumerate(shapes):
         assert infos[q].status == B.OK

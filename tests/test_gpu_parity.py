@@ -58,6 +58,12 @@ def stencil_tol(h, u):
     return 1e-14 * 2 * cc * max(np.max(np.abs(u)), 1e-300)
 
 
+# ------------------------------------------------------------- conversions --
+@pytest.mark.parametrize("seed", [1, 2])
+def test_integer_pipe_conversions_match_hardware(seed):
+    assert B.selfcheck_conversions(seed=seed, count=1 << 27) == 0
+
+
 # ---------------------------------------------------------------- stencil --
 @pytest.mark.parametrize("engine", [0, 1])
 @pytest.mark.parametrize("shape", SHAPES)
@@ -422,3 +428,24 @@ def test_full_size_256_cheb8_fixed_iterations_and_residual():
         info = s.solve(bt, x, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8)
     assert info.status == B.OK
     assert info.rel_res_true <= 2e-10 and abs(info.rel_res_true - info.rel_res_recursive) <= 1e-11
+
+
+def test_full_size_256_cheb8_matches_stored_oracle_solve():
+    """The benchmark problem (256^3, G(CI) d=8, exact bounds, rtol 1e-10) against the
+    oracle's full solve stored by tests/golden/make_oracle_256.py: iteration count
+    within +-2, and the solution at 4096 seeded sample points within rel-L2 1e-8."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_256_cheb8.json")))
+    shape = (256, 256, 256)
+    b = dev(I.rhs_uniform(shape, seed=1))
+    x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, I.default_h(shape)) as s:
+        info = s.solve(b, x, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8)
+    assert info.status == B.OK and gold["status"] == O.OK
+    idx = torch.tensor(gold["sample_index"], dtype=torch.int64, device=DEV)
+    xs = x.reshape(-1)[idx].cpu().numpy()
+    ref = np.array(gold["sample_x"])
+    assert rel(xs, ref) <= 1e-8
+    assert abs(float(torch.linalg.vector_norm(x)) - gold["x_norm2"]) <= 1e-8 * gold["x_norm2"]
+    assert abs(info.iterations - gold["iterations"]) <= 2, (info.iterations, gold["iterations"])
