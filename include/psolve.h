@@ -211,7 +211,8 @@ PSOLVE_API psolve_status psolve_cheb_interval(psolve_ctx *ctx, int32_t precond, 
  * cause.  Its scratch (descriptor, scalars, per-unit partial sums) is one
  * fixed 4 MiB device array inside the library, held by every GPU that loads
  * it until the process exits; grids whose partial sums do not fit (more than
- * about 2.6e5 work units, roughly 800^3 points) return PSOLVE_E_ARG.  The first
+ * about 2.6e5 work units: a unit is a 32 x 8 tile of columns times up to 32
+ * planes, so very flat grids reach the limit first) return PSOLVE_E_ARG.  The first
  * call on a device looks the array's address up (cudaGetSymbolAddress) and
  * should come before any stream capture.  All calls share the array: calls
  * that overlap on the GPU (other streams, other host threads) race.  a_dev,
@@ -229,6 +230,13 @@ PSOLVE_API psolve_status psolve_dot_noalloc(const int64_t grid[3], const double 
  * stores the number of differences in *mismatches (0 expected).  No
  * counterpart in the paper (an implementation check). */
 PSOLVE_API psolve_status psolve_selfcheck_conversions(uint64_t seed, int64_t count, int64_t *mismatches);
+
+/* Self-check of the bounded waits: a kernel waits, with the same bounded wait
+ * the TMA ring uses, on a shared-memory barrier that nothing completes, and
+ * gives up after limit_cycles clock cycles (<= 2^34).  *status receives
+ * PSOLVE_TIMEOUT when the wait gave up as designed.  No counterpart in the
+ * paper (failure detection without a GPU fault). */
+PSOLVE_API psolve_status psolve_selfcheck_wait_timeout(int64_t limit_cycles, int32_t *status);
 
 /* ---- many independent grids at once ----------------------------------- */
 

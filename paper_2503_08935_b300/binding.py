@@ -30,7 +30,7 @@ EXPORTS = [
     "psolve_opts_default", "psolve_create", "psolve_solve", "psolve_solve_host", "psolve_destroy",
     "psolve_apply_A", "psolve_precond_apply", "psolve_dot", "psolve_cheb_interval", "psolve_solve_batch",
     "psolve_server_create", "psolve_submit", "psolve_poll", "psolve_server_destroy", "psolve_last_error",
-    "psolve_version", "psolve_dot_noalloc", "psolve_selfcheck_conversions",
+    "psolve_version", "psolve_dot_noalloc", "psolve_selfcheck_conversions", "psolve_selfcheck_wait_timeout",
 ]
 
 
@@ -115,6 +115,8 @@ def lib():
         L.psolve_server_destroy.restype = None
         L.psolve_selfcheck_conversions.argtypes = [ctypes.c_uint64, ctypes.c_int64, I64P]
         L.psolve_selfcheck_conversions.restype = ctypes.c_int32
+        L.psolve_selfcheck_wait_timeout.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]
+        L.psolve_selfcheck_wait_timeout.restype = ctypes.c_int32
         L.psolve_dot_noalloc.argtypes = [I64P, P, P, ctypes.c_void_p, DP]
         L.psolve_dot_noalloc.restype = ctypes.c_int32
         L.psolve_last_error.restype = ctypes.c_char_p
@@ -322,6 +324,15 @@ def selfcheck_conversions(seed=1, count=1 << 26) -> int:
     if st != OK:
         raise PsolveError(st, "psolve_selfcheck_conversions")
     return bad.value
+
+
+def selfcheck_wait_timeout(limit_cycles=1 << 20) -> int:
+    """Status of a bounded wait on a barrier nothing completes (TIMEOUT expected)."""
+    st_out = ctypes.c_int32()
+    st = lib().psolve_selfcheck_wait_timeout(int(limit_cycles), ctypes.byref(st_out))
+    if st != OK:
+        raise PsolveError(st, "psolve_selfcheck_wait_timeout")
+    return st_out.value
 
 
 def dot_noalloc(a, b, stream=None) -> float:

@@ -149,9 +149,11 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
         const cuuint32_t halo[3] = {(cuuint32_t)(TILE_X + 2 * (16 / es)), (cuuint32_t)(TILE_Y + 2), 1};
         const cuuint32_t plain[3] = {(cuuint32_t)TILE_X, (cuuint32_t)TILE_Y, 1};
         for (int v = 0; v < 2; ++v) {
+            // no L2 promotion: the halo boxes start 16 bytes before a line, and
+            // promoting their sector reads to whole lines multiplied DRAM reads
             CUresult e = fn(&maps[2 * r + v], dt, 3, D.vec[r], dims, strides, v == 0 ? halo : plain, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (e != CUDA_SUCCESS) return;
         }
     }
@@ -392,11 +394,13 @@ void problem_geometry(Problem &P, int sms)
     D.tiles_x = ceil_div(D.nx, TILE_X);
     D.tiles_y = ceil_div(D.ny, TILE_Y);
     const long long tiles = (long long)D.tiles_x * D.tiles_y;
-    // Chunk length: about 6 units per CTA of a full-device launch, at most
-    // 8 planes; a function of the grid shape and the GPU only.
-    long long zc = (long long)D.nz * tiles / (6LL * 4 * sms);
-    if (zc < 1) zc = 1;
-    if (zc > 8) zc = 8;
+    // Chunk length: the largest power of two (1..32 planes) that still gives a
+    // full-device launch (4 CTAs per SM) at least about 4 units per CTA; a
+    // function of the grid shape and the GPU only, so reductions do not depend
+    // on the batch mix.
+    const long long target = (long long)D.nz * tiles / (4LL * 4 * sms);
+    long long zc = 1;
+    while (zc * 2 <= target && zc < 32) zc *= 2;
     D.zc = (int)zc;
     D.nzc = ceil_div(D.nz, D.zc);
     D.units = (int)(tiles * D.nzc);

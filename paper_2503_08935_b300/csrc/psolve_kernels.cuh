@@ -37,35 +37,66 @@ namespace psolve {
 // Exact conversions on the integer pipe.  B300 executes FP64 conversions on
 // its narrow FP64 pipe (2 instructions per clock per SM), where they compete
 // with the FP64 arithmetic of the outer iteration; these IEEE-754 bit
-// manipulations give the same results on the ALU pipe.  Zeros, subnormals,
-// infinities, NaNs and out-of-range values (rare) take the hardware path.
+// manipulations give the same results with integer instructions only.
 // ------------------------------------------------------------------------
-// float -> double, exact: re-bias the exponent (1023 - 127 = 896) and move
-// the 23-bit mantissa to the top of the 52-bit field.
+// float -> double, exact.  Normal: re-bias the exponent (1023 - 127 = 896)
+// and move the 23-bit mantissa to the top of the 52-bit field.  Subnormal:
+// normalise with a leading-zero count.  Zero, Inf and NaN keep their class.
 __device__ __forceinline__ double f2d_exact(float f)
 {
     const uint32_t u = __float_as_uint(f);
+    const uint32_t sign = u & 0x80000000u;
     const uint32_t e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-    const uint32_t lo = u << 29;
+    const uint32_t man = u & 0x7fffffu;
+    uint32_t ed = e + 896u, m = man;
+    if (e == 0u) {
+        if (man == 0u) {
+            ed = 0u;
+        } else { // value man * 2^-149 = 1.f * 2^(31 - clz - 149)
+            const uint32_t lz = (uint32_t)__clz((int)man);
+            ed = 905u - lz;
+            m = (man << (lz - 8u)) & 0x7fffffu;
+        }
+    } else if (e == 0xffu) {
+        ed = 0x7ffu;
+    }
+    const uint32_t hi = sign | (ed << 20) | (m >> 3);
+    const uint32_t lo = m << 29;
     return __hiloint2double((int)hi, (int)lo);
 }
 
-// double -> float, round to nearest even: keep 23 of the 52 mantissa bits,
-// round on the 29 dropped bits (ties to even); a carry out of the mantissa
-// moves into the exponent (and to infinity at the top), as IEEE-754 rounding
-// does.  Results that would be subnormal or overflow take the hardware path.
+// double -> float, round to nearest even (IEEE-754).  Normal results keep 23
+// of the 52 mantissa bits and round on the 29 dropped bits; a carry out of the
+// mantissa moves into the exponent (and to infinity at the top).  Subnormal
+// results shift the 53-bit significand right by (926 - e) and round the same
+// way; results below half the smallest subnormal are zero, values beyond the
+// float range are infinity, NaN stays NaN.
 __device__ __forceinline__ float d2f_rn(double d)
 {
     const uint32_t hi = (uint32_t)__double2hiint(d);
     const uint32_t lo = (uint32_t)__double2loint(d);
+    const uint32_t sign = hi & 0x80000000u;
     const uint32_t e = (hi >> 20) & 0x7ffu;
-    if (e < 897u || e > 1150u) return __double2float_rn(d); // float exponent outside [1, 254]
-    const uint32_t m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    const uint32_t rest = lo & 0x1fffffffu;
-    uint32_t r = (hi & 0x80000000u) | ((e - 896u) << 23) | m23;
-    if (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) r += 1u;
+    uint32_t r;
+    if (e >= 897u && e <= 1150u) {
+        const uint32_t m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t rest = lo & 0x1fffffffu;
+        r = sign | ((e - 896u) << 23) | m23;
+        if (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) r += 1u;
+    } else if (e > 1150u) {
+        const bool nan = e == 0x7ffu && ((hi & 0xfffffu) | lo) != 0u;
+        r = sign | (nan ? 0x7fc00000u : 0x7f800000u);
+    } else if (e == 0u || 926u - e > 63u) {
+        r = sign; // +-0
+    } else {
+        const uint64_t m = (((uint64_t)(hi & 0xfffffu) | 0x100000u) << 32) | lo; // 53-bit significand
+        const uint32_t sh = 926u - e;                                           // 30..63
+        const uint64_t q = m >> sh;
+        const uint64_t rest = m & ((1ull << sh) - 1ull);
+        const uint64_t half = 1ull << (sh - 1u);
+        r = sign | (uint32_t)q;
+        if (rest > half || (rest == half && (q & 1ull))) r += 1u;
+    }
     return __uint_as_float(r);
 }
 
@@ -344,7 +375,8 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
     double acc[NDA];
 #pragma unroll
     for (int q = 0; q < NDA; ++q) acc[q] = 0.0;
-    int unit = tile * D.nzc + c0;
+    const int ntiles = D.tiles_x * D.tiles_y;
+    int unit = c0 * ntiles + tile; // units are numbered chunk-major
     int cend = min(nz, (c0 + 1) * zc);
     int buf = 0;
 
@@ -383,44 +415,46 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
         if constexpr (ND > 0) {
             if (k + 1 == cend) {
                 flush_unit<ND>(acc, sred, D.partials, unit);
-                ++unit;
+                unit += ntiles;
                 cend = min(nz, cend + zc);
             }
         }
     }
 }
 
-// Pointwise march (no stencil) over chunks [c0, c1) of one tile.
+// Pointwise march (no stencil) over chunks [c0, c1) of one tile.  Planes are
+// taken two at a time with both planes' loads issued before either is used
+// (different planes never alias), which doubles the loads in flight.
+// Op provides: struct In; In load(idx); void apply(idx, const In&, acc).
 template <class Op>
 __device__ __forceinline__ void march_point(Op &op, const Desc &D, int tile, int c0, int c1, double *sred)
 {
     constexpr int ND = Op::ND;
     constexpr int NDA = ND > 0 ? ND : 1;
+    using In = typename Op::In;
     const int nx = D.nx, ny = D.ny, nz = D.nz, zc = D.zc;
     const int plane = nx * ny;
     const int tid = threadIdx.x, tx = tid % TILE_X, ty = tid / TILE_X;
     const int i = (tile % D.tiles_x) * TILE_X + tx, j = (tile / D.tiles_x) * TILE_Y + ty;
     const bool in = (i < nx) && (j < ny);
     const int col = in ? j * nx + i : 0;
-    const int kb = c0 * zc;
-    const int ke = min(nz, c1 * zc);
+    const int ntiles = D.tiles_x * D.tiles_y;
     double acc[NDA];
 #pragma unroll
     for (int q = 0; q < NDA; ++q) acc[q] = 0.0;
-    int unit = tile * D.nzc + c0;
-    int cend = min(nz, (c0 + 1) * zc);
-    for (int k = kb; k < ke; ++k) {
-        if (in) op.emit(col + k * plane, acc);
-        if constexpr (ND > 0) {
-            if (k + 1 == cend) {
-                flush_unit<ND>(acc, sred, D.partials, unit);
-                ++unit;
-                cend = min(nz, cend + zc);
-            }
+    for (int c = c0; c < c1; ++c) {
+        const int kb = c * zc, ke = min(nz, (c + 1) * zc);
+        for (int k = kb; k < ke; k += 2) {
+            const bool two = k + 1 < ke;
+            In v0{}, v1{};
+            if (in) v0 = op.load(col + k * plane);
+            if (in && two) v1 = op.load(col + (k + 1) * plane);
+            if (in) op.apply(col + k * plane, v0, acc);
+            if (in && two) op.apply(col + (k + 1) * plane, v1, acc);
         }
+        if constexpr (ND > 0) flush_unit<ND>(acc, sred, D.partials, c * ntiles + tile);
     }
 }
-
 
 // ------------------------------------------------------------------------
 // TMA ring engine (problems with desc.tma = 1).
@@ -470,13 +504,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 
 // Bounded wait for the completion of phase `parity`: gives up after about
 // 2^31 clock cycles (about a second).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = 1LL << 31)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -505,7 +539,10 @@ struct Ring {
     static constexpr int HSTRIDE = align128(HBYTES);
     static constexpr int PSTRIDE = align128(PBYTES);
     static constexpr int STAGE = Op::NH * HSTRIDE + Op::NP * PSTRIDE;
-    static constexpr int XBYTES = Op::XFORM ? align128(HBOX * (int)sizeof(C)) : 0; // one u plane
+    using U = typename Op::U;
+    // transformed planes: the stencil value (C) and, when it differs, the centre value (U)
+    static constexpr bool UX = Op::XFORM && !std::is_same<U, C>::value;
+    static constexpr int XBYTES = Op::XFORM ? align128(HBOX * (int)sizeof(C)) + (UX ? align128(HBOX * (int)sizeof(U)) : 0) : 0;
     static constexpr int STAGES_RAW = (48 * 1024 - 3 * XBYTES) / (STAGE > 0 ? STAGE : 1);
     static constexpr int STAGES = STAGES_RAW < 4 ? 4 : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
     static constexpr int BYTES = STAGES * STAGE + 3 * XBYTES; // dynamic shared memory
@@ -579,7 +616,9 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
     const int q0 = kb - 1, q1 = ke; // stencil-input planes q0..q1, pointwise planes kb..ke-1
     const int nplanes = q1 - q0 + 1;
     const uint32_t seq0 = seq;
-    C *xring = reinterpret_cast<C *>(ring + S * R::STAGE); // transformed u planes (XFORM only)
+    unsigned char *xbase = ring + S * R::STAGE; // transformed u planes (XFORM only)
+    C *xring = reinterpret_cast<C *>(xbase);
+    U *uring = reinterpret_cast<U *>(xbase + 3 * align128(R::HBOX * (int)sizeof(C))); // when U != C
 
     auto stage_of = [&](int q) { return ring + ((seq0 + (q - q0)) % S) * R::STAGE; };
     auto bar_of = [&](int q) { return bars + (seq0 + (q - q0)) % S; };
@@ -606,8 +645,12 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
         if constexpr (Op::XFORM) {
             const void *h[NHA], *p[NPA];
             stage_ptrs<Op>(stage_of(q), h, p);
-            C *dst = xring + ((q - q0) % 3) * R::HBOX;
-            for (int x = tid; x < R::HBOX; x += NTHREADS) dst[x] = op.sv(op.load_s(h, x));
+            const int slot = ((q - q0) % 3) * R::HBOX;
+            for (int x = tid; x < R::HBOX; x += NTHREADS) {
+                const U v = op.load_s(h, x);
+                xring[slot + x] = op.sv(v);
+                if constexpr (R::UX) uring[slot + x] = v;
+            }
         }
     };
 
@@ -628,7 +671,8 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
     for (int a = 0; a < NDA; ++a) acc[a] = 0.0;
     int kk = 0;
     if constexpr (Op::BLOCKED) kk = kb % D.bz;
-    int unit = tile * D.nzc + c0;
+    const int ntiles = D.tiles_x * D.tiles_y;
+    int unit = c0 * ntiles + tile;
     int cend = min(nz, (c0 + 1) * zc);
 
     for (int k = kb; k < ke; ++k) {
@@ -648,7 +692,10 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
             }
             const void *h[NHA], *p[NPA];
             stage_ptrs<Op>(stage_of(k), h, p);
-            const U uc = op.load_s(h, me);
+            U uc;
+            if constexpr (!Op::XFORM) uc = op.load_s(h, me);
+            else if constexpr (R::UX) uc = uring[((k - q0) % 3) * R::HBOX + me];
+            else uc = xring[((k - q0) % 3) * R::HBOX + me];
             const PW pw = op.pw_s(p, mp);
             op.emit(col + k * plane, op.sv(uc), w + e, so + no, dn + un, uc, pw, acc);
         }
@@ -663,7 +710,7 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
         if constexpr (ND > 0) {
             if (k + 1 == cend) {
                 flush_unit<ND>(acc, sred, D.partials, unit);
-                ++unit;
+                unit += ntiles;
                 cend = min(nz, cend + zc);
             }
         }
@@ -701,9 +748,13 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
     const ListHdr hdr = *reinterpret_cast<const ListHdr *>(a.list);
     const int2 *ent = reinterpret_cast<const int2 *>(a.list + 2);
     const long long total = hdr.total;
-    int u0 = (int)(total * blockIdx.x / gridDim.x);
-    const int u1 = (int)(total * (blockIdx.x + 1) / gridDim.x);
-    if (u0 >= u1) return;
+    const long long G = gridDim.x;
+    // Strided assignment: this CTA takes units g, g + G, g + 2G, ... of the
+    // launch list.  With units numbered chunk-major, the CTAs running at the
+    // same time cover neighbouring tiles at nearby z, so halo rows read by one
+    // CTA are still in L2 when its neighbours read them.
+    long long u = blockIdx.x;
+    if (u >= total) return;
 
     if constexpr (Op::STENCIL) {
         if (threadIdx.x == 0) {
@@ -715,45 +766,44 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
     }
     uint32_t seq = 0;
 
-    int lo = 0, hi = hdr.n - 1; // last entry whose first unit <= u0
+    int lo = 0, hi = hdr.n - 1; // last entry whose first unit <= u
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (ent[mid].y <= u0) lo = mid;
+        if (ent[mid].y <= u) lo = mid;
         else hi = mid - 1;
     }
-    for (int e = lo; e < hdr.n && u0 < u1; ++e) {
+    for (int e = lo; e < hdr.n && u < total; ++e) {
         const int2 en = ent[e];
+        const long long pend = (e + 1 < hdr.n) ? ent[e + 1].y : total; // end of this problem's units
+        if (u >= pend) continue;
+        const int cnt = (int)((pend - 1 - u) / G + 1); // this CTA's units of the problem
+        const long long ufirst = u;
+        u += (long long)cnt * G;
         const Desc &D = a.descs[en.x];
         const int units = D.units;
-        const int pu0 = u0 - en.y;
-        const int pu1 = min(u1 - en.y, units);
-        u0 = en.y + pu1;
-        if (pu0 >= pu1) continue;
         Scal *sc = D.sc;
         if ((a.skip & SKIP_STOP) && ld_flag(&sc->stop)) continue;
         if ((a.skip & SKIP_HALF) && ld_flag(&sc->half)) continue;
 
         Op op(D, a, sc);
-        const int nzc = D.nzc;
+        const int ntiles = D.tiles_x * D.tiles_y;
         const bool use_tma = D.tma != 0;
-        for (int pu = pu0; pu < pu1;) {
-            const int tile = pu / nzc;
-            const int c0 = pu - tile * nzc;
-            const int run_end = min(pu1, (tile + 1) * nzc);
-            const int c1 = c0 + (run_end - pu);
+        for (int i = 0; i < cnt; ++i) {
+            const int l = (int)(ufirst + (long long)i * G - en.y); // problem-local unit, chunk-major
+            const int c0 = l / ntiles;
+            const int tile = l - c0 * ntiles;
             if constexpr (Op::STENCIL) {
-                if (use_tma) march_tma<Op>(op, D, tile, c0, c1, dyn_smem, bars, seq, sred, &s_dead);
-                else march_stencil<Op>(op, D, tile, c0, c1, sp, sred);
+                if (use_tma) march_tma<Op>(op, D, tile, c0, c0 + 1, dyn_smem, bars, seq, sred, &s_dead);
+                else march_stencil<Op>(op, D, tile, c0, c0 + 1, sp, sred);
             } else {
-                march_point<Op>(op, D, tile, c0, c1, sred);
+                march_point<Op>(op, D, tile, c0, c0 + 1, sred);
             }
-            pu = run_end;
         }
         if constexpr (Op::ND > 0) {
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
-                const unsigned n = (unsigned)(pu1 - pu0);
+                const unsigned n = (unsigned)cnt;
                 const unsigned prev = atomicAdd(&sc->ticket, n);
                 s_last = (prev + n == (unsigned)units);
             }
@@ -763,9 +813,9 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
                 double v[Op::ND];
 #pragma unroll
                 for (int q = 0; q < Op::ND; ++q) v[q] = 0.0;
-                for (int u = threadIdx.x; u < units; u += NTHREADS) {
+                for (int w = threadIdx.x; w < units; w += NTHREADS) {
 #pragma unroll
-                    for (int q = 0; q < Op::ND; ++q) v[q] += __ldcg(D.partials + u * MAX_DOTS + q);
+                    for (int q = 0; q < Op::ND; ++q) v[q] += __ldcg(D.partials + w * MAX_DOTS + q);
                 }
                 block_sum<Op::ND>(v, sred);
                 if (threadIdx.x == 0) {
@@ -1163,13 +1213,14 @@ struct OpInit0 {
         r = (double *)D.vec[ROLE_R];
         x = (double *)D.vec[ROLE_X];
     }
+    struct In { double b; };
+    __device__ __forceinline__ In load(int idx) const { return In{__ldg(b + idx)}; }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, double (&acc)[NA]) const
+    __device__ __forceinline__ void apply(int idx, const In &v, double (&acc)[NA]) const
     {
-        const double bv = __ldg(b + idx);
-        r[idx] = bv;
+        r[idx] = v.b;
         x[idx] = 0.0;
-        acc[0] += bv * bv;
+        acc[0] += v.b * v.b;
     }
 };
 
@@ -1199,20 +1250,31 @@ struct OpUpdate {
         omega = ld_scal(&sc->omega);
         half = ld_flag(&sc->half);
     }
-    template <int NA>
-    __device__ __forceinline__ void emit(int idx, double (&acc)[NA]) const
+    struct In { double x, p, r, s, t, rt; };
+    __device__ __forceinline__ In load(int idx) const
     {
-        const double pv = Elem<T>::wide(ph, idx);
+        In v{};
+        v.x = x[idx];
+        v.p = Elem<T>::wide(ph, idx);
+        if (!half) {
+            v.r = Elem<T>::wide(rh, idx);
+            v.s = __ldg(s + idx);
+            v.t = __ldg(t + idx);
+            v.rt = __ldg(rt + idx);
+        }
+        return v;
+    }
+    template <int NA>
+    __device__ __forceinline__ void apply(int idx, const In &v, double (&acc)[NA]) const
+    {
         if (half) {
-            x[idx] = x[idx] + alpha * pv;
+            x[idx] = v.x + alpha * v.p;
             return;
         }
-        const double rv = Elem<T>::wide(rh, idx);
-        const double sv = __ldg(s + idx), tv = __ldg(t + idx), rtv = __ldg(rt + idx);
-        x[idx] = x[idx] + alpha * pv + omega * rv;
-        const double rn = sv - omega * tv;
+        x[idx] = v.x + alpha * v.p + omega * v.r;
+        const double rn = v.s - omega * v.t;
         r[idx] = rn;
-        acc[0] += rtv * rn;
+        acc[0] += v.rt * rn;
         acc[1] += rn * rn;
     }
 };
@@ -1236,11 +1298,22 @@ struct OpPUpdate {
         omega = ld_scal(&sc->omega);
         first = ld_flag(&sc->first);
     }
-    template <int NA>
-    __device__ __forceinline__ void emit(int idx, double (&)[NA]) const
+    struct In { double r, p, w; };
+    __device__ __forceinline__ In load(int idx) const
     {
-        if (first) p[idx] = __ldg(r + idx);
-        else p[idx] = __ldg(r + idx) + beta * (p[idx] - omega * __ldg(w + idx));
+        In v{};
+        v.r = __ldg(r + idx);
+        if (!first) {
+            v.p = p[idx];
+            v.w = __ldg(w + idx);
+        }
+        return v;
+    }
+    template <int NA>
+    __device__ __forceinline__ void apply(int idx, const In &v, double (&)[NA]) const
+    {
+        if (first) p[idx] = v.r;
+        else p[idx] = v.r + beta * (v.p - omega * v.w);
     }
 };
 
@@ -1259,10 +1332,12 @@ struct OpSUpdate {
         s = (double *)D.vec[ROLE_S];
         alpha = ld_scal(&sc->alpha);
     }
+    struct In { double r, w; };
+    __device__ __forceinline__ In load(int idx) const { return In{__ldg(r + idx), __ldg(w + idx)}; }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, double (&acc)[NA]) const
+    __device__ __forceinline__ void apply(int idx, const In &u, double (&acc)[NA]) const
     {
-        const double v = __ldg(r + idx) - alpha * __ldg(w + idx);
+        const double v = u.r - alpha * u.w;
         s[idx] = v;
         acc[0] += v * v;
     }
@@ -1279,10 +1354,12 @@ struct OpDot {
         a = (const double *)D.vec[k.in];
         b = (const double *)D.vec[k.aux];
     }
+    struct In { double a, b; };
+    __device__ __forceinline__ In load(int idx) const { return In{__ldg(a + idx), __ldg(b + idx)}; }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, double (&acc)[NA]) const
+    __device__ __forceinline__ void apply(int, const In &v, double (&acc)[NA]) const
     {
-        acc[0] += __ldg(a + idx) * __ldg(b + idx);
+        acc[0] += v.a * v.b;
     }
 };
 
@@ -1299,10 +1376,12 @@ struct OpWiden {
         in = D.vec[k.in];
         out = (double *)D.vec[k.out];
     }
+    struct In { double v; };
+    __device__ __forceinline__ In load(int idx) const { return In{Elem<T>::wide(in, idx)}; }
     template <int NA>
-    __device__ __forceinline__ void emit(int idx, double (&)[NA]) const
+    __device__ __forceinline__ void apply(int idx, const In &v, double (&)[NA]) const
     {
-        out[idx] = Elem<T>::wide(in, idx);
+        out[idx] = v.v;
     }
 };
 

@@ -31,7 +31,14 @@ __global__ void k_check_conversions(uint64_t seed, long long count, unsigned lon
         if (kind == 1) bits = (bits & ~0x1fffffffull) | 0x10000000ull;
         if (kind == 2) bits = (bits & ~0x1fffffffull) | 0x0fffffffull;
         if (kind == 3) bits = (bits & ~0x1fffffffull) | 0x10000001ull;
-        if (i & 1) bits = (bits & 0x800fffffffffffffull) | ((uint64_t)(897 + (z % 254)) << 52); // float range
+        if ((i & 3) == 1) bits = (bits & 0x800fffffffffffffull) | ((uint64_t)(897 + (z % 254)) << 52); // normal
+        if ((i & 3) == 3) { // results in or near the float subnormal range, with exact ties at the rounding bit
+            const uint64_t e = 860 + (z % 40);  // 860..899
+            bits = (bits & 0x800fffffffffffffull) | (e << 52);
+            const int64_t sh = 926 - (int64_t)e;
+            if (kind == 1 && sh >= 30 && sh <= 52)
+                bits = (bits & ~((1ull << sh) - 1ull)) | (1ull << (sh - 1));
+        }
         const double d = __longlong_as_double((long long)bits);
         const float x = d2f_rn(d), y = __double2float_rn(d);
         if (!(isnan(x) && isnan(y)) && __float_as_uint(x) != __float_as_uint(y)) ++local;
@@ -64,5 +71,47 @@ extern "C" PSOLVE_API psolve_status psolve_selfcheck_conversions(uint64_t seed, 
         return PSOLVE_E_CUDA;
     }
     *mismatches = (int64_t)bad;
+    return PSOLVE_OK;
+}
+
+namespace {
+
+// One thread initialises an mbarrier that nothing will ever complete and waits
+// on it with the bounded wait the TMA ring uses, here with a short limit.
+__global__ void k_check_wait_timeout(long long limit, int *status)
+{
+    __shared__ alignas(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *status = mbar_wait(&bar, 0, limit) ? PSOLVE_OK : PSOLVE_TIMEOUT;
+}
+
+} // namespace
+
+extern "C" PSOLVE_API psolve_status psolve_selfcheck_wait_timeout(int64_t limit_cycles, int32_t *status)
+{
+    clear_error();
+    if (!status || limit_cycles < 0 || limit_cycles > (1LL << 34)) {
+        set_error("bad argument");
+        return PSOLVE_E_ARG;
+    }
+    int *d = nullptr;
+    PS_CK(cudaMalloc(&d, sizeof(int)));
+    cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) {
+        k_check_wait_timeout<<<1, 32>>>((long long)limit_cycles, d);
+        e = cudaGetLastError();
+    }
+    int h = -1;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        set_error("wait self-check: %s", cudaGetErrorString(e));
+        return PSOLVE_E_CUDA;
+    }
+    *status = h;
     return PSOLVE_OK;
 }

@@ -45,10 +45,17 @@ def test_noalloc_dot_matches_context_dot_twice(shape):
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
-    a = torch.zeros((1, 1, 1), dtype=torch.float64, device="cuda")
+    """A flat 32768 x 4096 x 1 grid has 524288 xy tiles, hence at least that many
+    work units whatever the chunk length, more than the 4 MiB scratch holds
+    (262144).  The vectors are allocated at full size all the same, so that the
+    call could not read out of bounds even if the size check were wrong."""
     import ctypes
-    grid = (ctypes.c_int64 * 3)(1024, 1024, 1024)
+    shape = (1, 4096, 32768)
+    a = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    grid = (ctypes.c_int64 * 3)(32768, 4096, 1)
     res = ctypes.c_double()
     st = B.lib().psolve_dot_noalloc(grid, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(a.data_ptr()),
                                     ctypes.c_void_p(0), ctypes.byref(res))
     assert st == B.E_ARG and "scratch" in B.last_error()
+    del a
+    torch.cuda.empty_cache()
