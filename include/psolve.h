@@ -101,12 +101,20 @@ typedef struct {
                                 (nx % 8 == 0, 16-byte aligned vectors), else
                                 the general engine; 1 = always the general
                                 engine (no tensor copies)                     */
-    int32_t reserved[4];
+    int32_t persistent;      /* 1: run the whole solve (r0, every outer
+                                iteration, the exit true residual) as ONE
+                                cooperative kernel launch whose phases are
+                                separated by grid barriers, captured in a
+                                CUDA graph when use_graph = 1.  Results are
+                                bitwise those of the per-kernel path.  Not
+                                with timing = 1.  A barrier wait that gives up
+                                (4 s) ends the solve with PSOLVE_TIMEOUT.     */
+    int32_t reserved[3];
 } psolve_opts;
 
 /* Fill *o with the defaults: scales 1, 1; blocks 1,1,1; FP64; half-step check
  * on; x0 = 0; poll auto; graphs on; timing off; true residual on; rr off;
- * engine auto. */
+ * engine auto; per-kernel launches (persistent off). */
 PSOLVE_API void psolve_opts_default(psolve_opts *o);
 
 /* Kernel classes reported by timing mode (psolve_result.kclass_*). */

@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
         ("true_residual", ctypes.c_int32),
         ("rr_every", ctypes.c_int32),
         ("engine", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("persistent", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

@@ -13,6 +13,7 @@
 #include <chrono>
 
 #include "psolve_engine.cuh"
+#include "psolve_persist.cuh"
 
 using namespace psolve;
 
@@ -182,6 +183,75 @@ int auto_poll(double bytes_per_iter, int kernels_per_iter)
     return std::max(1, std::min(8, k));
 }
 
+// A cached single-launch graph of the persistent solve.
+struct PersistEntry {
+    Plan plan;
+    int maxit = 0;
+    bool use_x0 = false, true_res = false;
+    cudaGraphExec_t exec = nullptr;
+};
+
+// The whole solve of a launch list as one persistent kernel launch (captured
+// into a CUDA graph when use_graph; cached in *cache when given).  Returns
+// once the launch is enqueued; d_gs->err tells afterwards whether a barrier
+// wait gave up.
+psolve_status run_persistent(cudaStream_t s, cudaStream_t cap, const Plan &plan, int sms, long long units,
+                             const Desc *d_desc, const int32_t *d_list, GridSync *d_gs, int maxit, bool use_x0,
+                             bool true_res, bool use_graph, std::vector<PersistEntry> *cache)
+{
+    int grid = 1;
+    psolve_status st = persist_configure(plan, sms, units, &grid);
+    if (st != PSOLVE_OK) return st;
+    PersistArgs a{};
+    a.descs = d_desc;
+    a.list = d_list;
+    a.gs = d_gs;
+    a.degree = plan.degree;
+    a.iters = maxit;
+    a.init = 1;
+    a.use_x0 = use_x0 ? 1 : 0;
+    a.true_res = true_res ? 1 : 0;
+    if (!use_graph) return persist_enqueue(s, plan, grid, a);
+    if (cache)
+        for (const PersistEntry &e : *cache)
+            if (e.plan == plan && e.maxit == maxit && e.use_x0 == use_x0 && e.true_res == true_res) {
+                PS_CK(cudaGraphLaunch(e.exec, s));
+                return PSOLVE_OK;
+            }
+    PS_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    st = persist_enqueue(cap, plan, grid, a);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (st != PSOLVE_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (st == PSOLVE_OK) set_error("capture of the persistent launch: %s", cudaGetErrorString(e));
+        return PSOLVE_E_CUDA;
+    }
+    PersistEntry ent;
+    ent.plan = plan;
+    ent.maxit = maxit;
+    ent.use_x0 = use_x0;
+    ent.true_res = true_res;
+    e = cudaGraphInstantiate(&ent.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        set_error("cudaGraphInstantiate (persistent): %s", cudaGetErrorString(e));
+        return PSOLVE_E_CUDA;
+    }
+    e = cudaGraphLaunch(ent.exec, s);
+    if (cache) cache->push_back(ent);
+    else {
+        // one-shot graph: destroyed once the launch has completed
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(ent.exec);
+    }
+    if (e != cudaSuccess) {
+        set_error("persistent graph launch: %s", cudaGetErrorString(e));
+        return PSOLVE_E_CUDA;
+    }
+    return PSOLVE_OK;
+}
+
 void fill_timing(const std::vector<LaunchRec> &recs, int final_iter, int half_exit, psolve_result *res)
 {
     for (const LaunchRec &r : recs) {
@@ -307,6 +377,8 @@ struct psolve_ctx {
     Scal *h_sc = nullptr; // 3 pinned slots: 2 for polling, 1 for set-up
     cudaEvent_t poll_ev[2] = {nullptr, nullptr};
     std::vector<GraphEntry> graphs;
+    std::vector<PersistEntry> pgraphs;    // single-launch graphs of the persistent solve
+    GridSync *d_gs = nullptr, *h_gs = nullptr; // its barrier state (device, pinned copy)
     std::vector<cudaEvent_t> events;
     double *d_hb = nullptr, *d_hx = nullptr; // device copies for psolve_solve_host
 };
@@ -341,6 +413,10 @@ void psolve_destroy(psolve_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (GraphEntry &g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (PersistEntry &g : c->pgraphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->d_gs) cudaFree(c->d_gs);
+    if (c->h_gs) cudaFreeHost(c->h_gs);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     for (cudaEvent_t e : c->poll_ev)
         if (e) cudaEventDestroy(e);
@@ -423,6 +499,8 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
     CREATE_CK(cudaMalloc(&c->d_list, 4 * sizeof(int32_t)));
     CREATE_CK(cudaHostAlloc(&c->h_desc, sizeof(Desc), cudaHostAllocDefault));
     CREATE_CK(cudaHostAlloc(&c->h_sc, 3 * sizeof(Scal), cudaHostAllocDefault));
+    CREATE_CK(cudaMalloc(&c->d_gs, sizeof(GridSync)));
+    CREATE_CK(cudaHostAlloc(&c->h_gs, sizeof(GridSync), cudaHostAllocDefault));
     CREATE_CK(cudaMalloc(&c->d_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM));
     CREATE_CK(cudaHostAlloc(&c->h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM, cudaHostAllocDefault));
     P.desc.tmap = c->d_tmap;
@@ -469,6 +547,10 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     psolve_status st = check_solve_args(rtol, maxit, precond, degree);
     if (st == PSOLVE_OK) st = check_blocks(c->P, precond);
     if (st != PSOLVE_OK) return st;
+    if (c->opts.persistent && c->opts.timing) {
+        set_error("timing mode times separate kernel launches; it cannot run with persistent = 1");
+        return PSOLVE_E_ARG;
+    }
     PS_CK(cudaSetDevice(c->di.dev));
     Problem &P = c->P;
     st = problem_set_cheb(P, precond, degree, c->opts.lmin_scale, c->opts.lmax_scale);
@@ -524,6 +606,41 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
         R.K = c->opts.poll_every > 0 ? c->opts.poll_every : auto_poll(b, (int)recs.size());
     }
 
+    const bool tr = c->opts.true_residual != 0;
+    if (c->opts.persistent) {
+        st = run_persistent(c->stream, c->cap, R.plan, R.sms, R.units, c->d_desc, c->d_list, c->d_gs, maxit, use_x0,
+                            tr, R.use_graph, &c->pgraphs);
+        if (st != PSOLVE_OK) return st;
+        R.launches += 1;
+        PS_CK(cudaMemcpyAsync(c->h_gs, c->d_gs, sizeof(GridSync), cudaMemcpyDeviceToHost, c->stream));
+        PS_CK(cudaMemcpyAsync(c->h_sc + 2, P.d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
+        PS_CK(cudaStreamSynchronize(c->stream));
+        if (c->h_gs->err) {
+            set_error("persistent solve: a %s wait gave up", c->h_gs->err == 1 ? "grid barrier" : "tensor copy");
+            return PSOLVE_TIMEOUT;
+        }
+        Scal s = c->h_sc[2];
+        if (s.zero_x) {
+            // b = 0 with an initial guess: x = 0, and the residual of the zeroed x
+            PS_CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)P.npts(), c->stream));
+            if (tr) {
+                Launcher T = R.launcher();
+                T.iter = -1;
+                enqueue_true_residual(T);
+                R.launches += T.launches;
+                PS_CK(T.err);
+            }
+            PS_CK(cudaMemcpyAsync(c->h_sc + 2, P.d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
+            PS_CK(cudaStreamSynchronize(c->stream));
+            s = c->h_sc[2];
+        }
+        psolve_result tmp;
+        std::memset(&tmp, 0, sizeof tmp);
+        fill_result(s, P, R.plan, use_x0, tr, t0, R.launches, &tmp);
+        if (res) *res = tmp;
+        return (psolve_status)s.status;
+    }
+
     Launcher L = R.launcher();
     L.iter = 0;
     enqueue_init(L, use_x0);
@@ -533,7 +650,6 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     if (st != PSOLVE_OK) return st;
     Scal s = R.h_sc[R.last_slot][0];
     if (s.zero_x) PS_CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)P.npts(), c->stream));
-    const bool tr = c->opts.true_residual != 0;
     if (tr) {
         Launcher T = R.launcher();
         T.iter = -1;
@@ -706,6 +822,10 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         set_error("unknown Chebyshev precision %d", o.cheb_prec);
         return PSOLVE_E_ARG;
     }
+    if (o.persistent && o.timing) {
+        set_error("timing mode times separate kernel launches; it cannot run with persistent = 1");
+        return PSOLVE_E_ARG;
+    }
     DevInfo di;
     st = device_info(&di);
     if (st != PSOLVE_OK) return st;
@@ -746,6 +866,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     CUtensorMap *d_tmap = nullptr, *h_tmap = nullptr;
     int32_t *d_list = nullptr, *h_list = nullptr;
     Scal *h_sc = nullptr;
+    GridSync *d_gs = nullptr, *h_gs = nullptr;
     cudaStream_t cap = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     std::vector<GraphEntry> graphs;
@@ -768,6 +889,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         if (h_tmap) cudaFreeHost(h_tmap);
         if (h_list) cudaFreeHost(h_list);
         if (h_sc) cudaFreeHost(h_sc);
+        if (d_gs) cudaFree(d_gs);
+        if (h_gs) cudaFreeHost(h_gs);
     };
 #define BATCH_CK(call)                                                                       \
     do {                                                                                     \
@@ -788,6 +911,10 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     BATCH_CK(cudaHostAlloc(&h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * count, cudaHostAllocDefault));
     BATCH_CK(cudaHostAlloc(&h_list, list_bytes, cudaHostAllocDefault));
     BATCH_CK(cudaHostAlloc(&h_sc, 2 * sizeof(Scal) * count, cudaHostAllocDefault));
+    if (o.persistent) {
+        BATCH_CK(cudaMalloc(&d_gs, sizeof(GridSync)));
+        BATCH_CK(cudaHostAlloc(&h_gs, sizeof(GridSync), cudaHostAllocDefault));
+    }
     BATCH_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     for (int k = 0; k < 2; ++k) BATCH_CK(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
     h_list[0] = count;
@@ -845,23 +972,41 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     R.poll_ev[1] = ev[1];
     R.K = o.poll_every > 0 ? o.poll_every : 4;
 
-    Launcher L = R.launcher();
-    L.iter = 0;
-    enqueue_init(L, false);
-    R.launches += L.launches;
-    BATCH_CK(L.err);
-    st = run_loop(R, maxit);
-    if (st != PSOLVE_OK) {
-        cleanup();
-        return st;
-    }
     const bool tr = o.true_residual != 0;
-    if (tr) {
-        Launcher T = R.launcher();
-        T.iter = -1;
-        enqueue_true_residual(T);
-        R.launches += T.launches;
-        BATCH_CK(T.err);
+    if (o.persistent) {
+        // every problem's whole solve in one cooperative launch
+        st = run_persistent(s, cap, R.plan, R.sms, R.units, d_desc, d_list, d_gs, maxit, false, tr, R.use_graph,
+                            nullptr);
+        if (st != PSOLVE_OK) {
+            cleanup();
+            return st;
+        }
+        R.launches += 1;
+        BATCH_CK(cudaMemcpyAsync(h_gs, d_gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+        BATCH_CK(cudaStreamSynchronize(s));
+        if (h_gs->err) {
+            set_error("persistent batch: a %s wait gave up", h_gs->err == 1 ? "grid barrier" : "tensor copy");
+            cleanup();
+            return PSOLVE_TIMEOUT;
+        }
+    } else {
+        Launcher L = R.launcher();
+        L.iter = 0;
+        enqueue_init(L, false);
+        R.launches += L.launches;
+        BATCH_CK(L.err);
+        st = run_loop(R, maxit);
+        if (st != PSOLVE_OK) {
+            cleanup();
+            return st;
+        }
+        if (tr) {
+            Launcher T = R.launcher();
+            T.iter = -1;
+            enqueue_true_residual(T);
+            R.launches += T.launches;
+            BATCH_CK(T.err);
+        }
     }
     BATCH_CK(cudaMemcpyAsync(h_sc, d_sc, sizeof(Scal) * count, cudaMemcpyDeviceToHost, s));
     BATCH_CK(cudaStreamSynchronize(s));

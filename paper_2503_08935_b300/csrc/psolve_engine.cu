@@ -161,118 +161,17 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
 }
 
 // --------------------------------------------------- per-iteration kernels --
-template <class T>
-static constexpr bool is_mixed() { return !std::is_same<T, double>::value; }
-
-// Chebyshev sweeps k = 2..d (Algorithm 2 loop).  y_k overwrites y_{k-2}'s
-// buffer (read only at the same point), and the last sweep writes `final_role`.
-template <class T, class TB, bool BLK, bool WY>
-static void sweeps_impl(Launcher &L, int d, int side, int brole, int final_role, int skip)
-{
-    const double c = sizeof(T), cb = sizeof(TB);
-    for (int k = 2; k <= d; ++k) {
-        KArgs a{};
-        a.k = k;
-        a.skip = skip;
-        a.in = (k % 2 == 0) ? ROLE_YA : ROLE_YB;
-        a.z = (k % 2 == 0) ? ROLE_YB : ROLE_YA;
-        a.out = (k == d) ? final_role : a.z;
-        a.b = brole;
-        if (k == 2) L.go<OpCiSweep<T, TB, BLK, WY>>(PSOLVE_K_CI_SWEEP3, side, a, c + cb + c);
-        else L.go<OpCiSweep<T, TB, BLK, WY>>(PSOLVE_K_CI_SWEEP4, side, a, c + cb + c + c);
-    }
-}
-
-template <class T, class TB, bool BLK>
-static void sweeps(Launcher &L, int d, int side, int brole, int final_role, int skip, bool exact_bounds)
-{
-    if (exact_bounds) sweeps_impl<T, TB, BLK, false>(L, d, side, brole, final_role, skip);
-    else sweeps_impl<T, TB, BLK, true>(L, d, side, brole, final_role, skip);
-}
-
 template <class T, bool BLK>
 static void iteration_cheb(Launcher &L, int d, bool eb)
 {
-    using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
-    constexpr bool MIX = is_mixed<T>();
-    const double c = sizeof(T);
-    // p side: p_{i-1} = r + beta (p_{i-2} - omega w) fused with CI sweep 1
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP;
-        a.in = ROLE_PCUR;
-        a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
-        const double rd = (L.iter == 1) ? 8.0 : 24.0;
-        L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, rd + 8.0 + (MIX ? c : 0.0) + c);
-    }
-    sweeps<T, TB, BLK>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP, eb);
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP;
-        a.in = ROLE_PH;
-        L.go<OpStencilDot<T>>(PSOLVE_K_STENCIL_DOT, 0, a, c + 16.0);
-    }
-    // s side: s = r - alpha w fused with CI sweep 1 and ||s||^2
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP;
-        a.in = ROLE_S;
-        a.out = (d <= 1) ? ROLE_RH : ROLE_YA;
-        L.go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, 24.0 + (MIX ? c : 0.0) + c);
-    }
-    sweeps<T, TB, BLK>(L, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF, eb);
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP | SKIP_HALF;
-        a.in = ROLE_RH;
-        L.go<OpStencil2Dot<T>>(PSOLVE_K_STENCIL_2DOT, 1, a, c + 16.0);
-    }
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP;
-        a.in = ROLE_PH;
-        a.aux = ROLE_RH;
-        L.go<OpUpdate<T>>(PSOLVE_K_UPDATE, 0, a, 48.0 + 2 * c, 16.0 + c, 1);
-    }
-}
-
-static void iteration_none(Launcher &L)
-{
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP;
-        L.go<OpPUpdate>(PSOLVE_K_OTHER, 0, a, L.iter == 1 ? 16.0 : 32.0);
-    }
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP;
-        a.in = ROLE_P;
-        L.go<OpStencilDot<double>>(PSOLVE_K_STENCIL_DOT, 0, a, 24.0);
-    }
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP;
-        L.go<OpSUpdate>(PSOLVE_K_OTHER, 0, a, 24.0);
-    }
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP | SKIP_HALF;
-        a.in = ROLE_S;
-        L.go<OpStencil2Dot<double>>(PSOLVE_K_STENCIL_2DOT, 1, a, 16.0);
-    }
-    {
-        KArgs a{};
-        a.skip = SKIP_STOP;
-        a.in = ROLE_P;
-        a.aux = ROLE_S;
-        L.go<OpUpdate<double>>(PSOLVE_K_UPDATE, 0, a, 56.0, 24.0, 1);
-    }
+    if (eb) prog_iteration_cheb<T, BLK, false>(L, d, L.iter);
+    else prog_iteration_cheb<T, BLK, true>(L, d, L.iter);
 }
 
 void enqueue_iteration(Launcher &L, const Plan &plan)
 {
     if (plan.precond == PSOLVE_PC_NONE) {
-        iteration_none(L);
+        prog_iteration_none(L, L.iter);
         return;
     }
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
@@ -292,20 +191,9 @@ void enqueue_iteration(Launcher &L, const Plan &plan)
     }
 }
 
-void enqueue_init(Launcher &L, bool use_x0)
-{
-    KArgs a{};
-    a.skip = 0;
-    if (use_x0) L.go<OpResidual<true>>(PSOLVE_K_INIT, 0, a, 32.0);
-    else L.go<OpInit0>(PSOLVE_K_INIT, 0, a, 24.0);
-}
+void enqueue_init(Launcher &L, bool use_x0) { prog_init(L, use_x0); }
 
-void enqueue_true_residual(Launcher &L)
-{
-    KArgs a{};
-    a.skip = 0;
-    L.go<OpResidual<false>>(PSOLVE_K_OTHER, 0, a, 16.0);
-}
+void enqueue_true_residual(Launcher &L) { prog_true_residual(L); }
 
 // Building blocks use the same kernels as the solve.
 void enqueue_apply_A(Launcher &L, bool blocked)
@@ -338,7 +226,8 @@ static void precond_cheb(Launcher &L, int d, bool eb)
     a.in = ROLE_PCUR;
     a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
     L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
-    sweeps<T, TB, BLK>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, eb);
+    if (eb) prog_sweeps<T, TB, BLK, false>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0);
+    else prog_sweeps<T, TB, BLK, true>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0);
     KArgs w{};
     w.in = ROLE_PH;
     w.out = ROLE_V;

@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "../../include/psolve.h"
-#include "psolve_kernels.cuh"
+#include "psolve_program.cuh"
 
 namespace psolve {
 

@@ -101,12 +101,25 @@ __device__ __forceinline__ float d2f_rn(double d)
 }
 
 // ------------------------------------------------------------------------
+// Global loads of solver vectors.  They go through L2 only (ld.global.cg):
+// the persistent kernel reads, after a grid barrier, vectors that other SMs
+// rewrote since this SM last read them, so neither the read-only path nor a
+// possibly stale L1 line may serve them.  Each vector element is read once
+// per kernel, so L1 would not help the streaming kernels either.
+// ------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T gld(const T *p)
+{
+    return __ldcg(p);
+}
+
+// ------------------------------------------------------------------------
 // Storage types of the Chebyshev vectors and their arithmetic type.
 // ------------------------------------------------------------------------
 template <class T> struct Elem;
 template <> struct Elem<double> {
     using C = double;
-    static __device__ __forceinline__ double ld(const void *p, int i) { return __ldg((const double *)p + i); }
+    static __device__ __forceinline__ double ld(const void *p, int i) { return gld((const double *)p + i); }
     static __device__ __forceinline__ double lds(const void *p, int i) { return ((const double *)p)[i]; }
     static __device__ __forceinline__ double wide(const void *p, int i) { return ld(p, i); }
     static __device__ __forceinline__ double wides(const void *p, int i) { return lds(p, i); }
@@ -115,7 +128,7 @@ template <> struct Elem<double> {
 };
 template <> struct Elem<float> {
     using C = float;
-    static __device__ __forceinline__ float ld(const void *p, int i) { return __ldg((const float *)p + i); }
+    static __device__ __forceinline__ float ld(const void *p, int i) { return gld((const float *)p + i); }
     static __device__ __forceinline__ float lds(const void *p, int i) { return ((const float *)p)[i]; }
     static __device__ __forceinline__ double wide(const void *p, int i) { return f2d_exact(ld(p, i)); }
     static __device__ __forceinline__ double wides(const void *p, int i) { return f2d_exact(lds(p, i)); }
@@ -126,7 +139,7 @@ template <> struct Elem<__nv_bfloat16> {
     using C = float;
     static __device__ __forceinline__ float ld(const void *p, int i)
     {
-        return __bfloat162float(__ldg((const __nv_bfloat16 *)p + i));
+        return __bfloat162float(gld((const __nv_bfloat16 *)p + i));
     }
     static __device__ __forceinline__ float lds(const void *p, int i)
     {
@@ -203,15 +216,19 @@ enum Epi {
 
 constexpr int ST_OK = 0, ST_NOT_CONVERGED = 4, ST_BREAKDOWN = 5, ST_NONFINITE = 6;
 
-__device__ __forceinline__ void stop_with(Scal *sc, int status)
+__device__ __forceinline__ void stop_with(volatile Scal *sc, int status)
 {
     sc->status = status;
     sc->stop = 1;
 }
 
+// Runs in one thread of the CTA that finished a reduction last.  The scalar
+// block is accessed through volatile (L2) loads and stores: in the persistent
+// kernel another SM may have rewritten it since this SM's L1 last held it.
 template <int EPI, int ND>
-__device__ void epilogue(const Desc &D, Scal *sc, const double (&v)[ND])
+__device__ void epilogue(const Desc &D, Scal *sc_mem, const double (&v)[ND])
 {
+    volatile Scal *sc = sc_mem;
     if constexpr (EPI == EPI_INIT0 || EPI == EPI_INITX0) {
         const double nb2 = v[0];
         const double rr = (EPI == EPI_INITX0) ? v[ND - 1] : v[0];
@@ -225,7 +242,9 @@ __device__ void epilogue(const Desc &D, Scal *sc, const double (&v)[ND])
         sc->half_exit = 0;
         sc->zero_x = 0;
         sc->maxit = D.maxit;
-        sc->alpha = sc->omega = sc->beta = 0.0;
+        sc->alpha = 0.0;
+        sc->omega = 0.0;
+        sc->beta = 0.0;
         sc->ss = 0.0;
         sc->stop = 0;
         sc->status = ST_NOT_CONVERGED;
@@ -262,7 +281,7 @@ __device__ void epilogue(const Desc &D, Scal *sc, const double (&v)[ND])
             if (om == 0.0) stop_with(sc, ST_BREAKDOWN);
         }
     } else if constexpr (EPI == EPI_UPDATE) {
-        sc->iter += 1;
+        sc->iter = sc->iter + 1;
         if (sc->half) { // x += alpha p^ was the whole update
             sc->rr = sc->ss;
             sc->half_exit = 1;
@@ -544,7 +563,7 @@ struct Ring {
     static constexpr bool UX = Op::XFORM && !std::is_same<U, C>::value;
     static constexpr int XBYTES = Op::XFORM ? align128(HBOX * (int)sizeof(C)) + (UX ? align128(HBOX * (int)sizeof(U)) : 0) : 0;
     static constexpr int STAGES_RAW = (48 * 1024 - 3 * XBYTES) / (STAGE > 0 ? STAGE : 1);
-    static constexpr int STAGES = STAGES_RAW < 4 ? 4 : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+    static constexpr int STAGES = STAGES_RAW < 4 ? 4 : (STAGES_RAW > 8 ? 8 : STAGES_RAW); // <= MAX_STAGES
     static constexpr int BYTES = STAGES * STAGE + 3 * XBYTES; // dynamic shared memory
 };
 
@@ -723,27 +742,23 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
 // ------------------------------------------------------------------------
 // The generic kernel: walk this CTA's unit range over the launch list.
 // ------------------------------------------------------------------------
-template <class Op>
-constexpr int ring_stages()
-{
-    if constexpr (Op::STENCIL) return Ring<Op>::STAGES;
-    else return 1;
-}
+// Shared-memory state of a CTA, reused by every phase a CTA runs.
+struct EngineShared {
+    double *sred;          // block-reduction scratch
+    uint64_t *bars;        // TMA ring mbarriers (MAX_STAGES)
+    int *s_last, *s_dead;
+    unsigned char *dyn;    // TMA ring / general-engine planes
+    uint32_t seq;          // planes this CTA has staged so far (all threads agree)
+};
 
+constexpr int MAX_STAGES = 8;
+
+// One phase: this CTA's strided share of every unit of the launch list.
 template <class Op>
-__global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
+__device__ __forceinline__ void engine_body(const KArgs &a, EngineShared &sh)
 {
     using C = typename Op::C;
-    constexpr int SPL = (TILE_X + 2) * (TILE_Y + 2);
-    constexpr int NB = ring_stages<Op>();
-    __shared__ double sred[(NTHREADS / 32) * MAX_DOTS];
-    __shared__ alignas(8) uint64_t bars[NB];
-    __shared__ int s_last, s_dead;
-    // the TMA ring, or the general engine's double-buffered plane: a CTA runs
-    // one engine at a time, and each march starts with a barrier
-    extern __shared__ __align__(128) unsigned char dyn_smem[];
-    C *sp = reinterpret_cast<C *>(dyn_smem);
-    (void)SPL;
+    C *sp = reinterpret_cast<C *>(sh.dyn);
 
     const ListHdr hdr = *reinterpret_cast<const ListHdr *>(a.list);
     const int2 *ent = reinterpret_cast<const int2 *>(a.list + 2);
@@ -755,16 +770,6 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
     // CTA are still in L2 when its neighbours read them.
     long long u = blockIdx.x;
     if (u >= total) return;
-
-    if constexpr (Op::STENCIL) {
-        if (threadIdx.x == 0) {
-            for (int b = 0; b < NB; ++b) mbar_init(&bars[b], 1);
-            mbar_init_fence();
-            s_dead = 0;
-        }
-        __syncthreads();
-    }
-    uint32_t seq = 0;
 
     int lo = 0, hi = hdr.n - 1; // last entry whose first unit <= u
     while (lo < hi) {
@@ -793,10 +798,10 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
             const int c0 = l / ntiles;
             const int tile = l - c0 * ntiles;
             if constexpr (Op::STENCIL) {
-                if (use_tma) march_tma<Op>(op, D, tile, c0, c0 + 1, dyn_smem, bars, seq, sred, &s_dead);
-                else march_stencil<Op>(op, D, tile, c0, c0 + 1, sp, sred);
+                if (use_tma) march_tma<Op>(op, D, tile, c0, c0 + 1, sh.dyn, sh.bars, sh.seq, sh.sred, sh.s_dead);
+                else march_stencil<Op>(op, D, tile, c0, c0 + 1, sp, sh.sred);
             } else {
-                march_point<Op>(op, D, tile, c0, c0 + 1, sred);
+                march_point<Op>(op, D, tile, c0, c0 + 1, sh.sred);
             }
         }
         if constexpr (Op::ND > 0) {
@@ -805,10 +810,10 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
                 __threadfence();
                 const unsigned n = (unsigned)cnt;
                 const unsigned prev = atomicAdd(&sc->ticket, n);
-                s_last = (prev + n == (unsigned)units);
+                *sh.s_last = (prev + n == (unsigned)units);
             }
             __syncthreads();
-            if (s_last) {
+            if (*sh.s_last) {
                 __threadfence();
                 double v[Op::ND];
 #pragma unroll
@@ -817,15 +822,49 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
 #pragma unroll
                     for (int q = 0; q < Op::ND; ++q) v[q] += __ldcg(D.partials + w * MAX_DOTS + q);
                 }
-                block_sum<Op::ND>(v, sred);
+                block_sum<Op::ND>(v, sh.sred);
                 if (threadIdx.x == 0) {
                     epilogue<Op::EPI, Op::ND>(D, sc, v);
                     sc->ticket = 0;
                     __threadfence();
                 }
             }
+            __syncthreads(); // s_last is reused by the next problem
         }
     }
+}
+
+// Initialise the CTA's shared state (mbarriers of the TMA ring).
+__device__ __forceinline__ void engine_setup(EngineShared &sh, double *sred, uint64_t *bars, int *s_last,
+                                             int *s_dead, unsigned char *dyn)
+{
+    sh.sred = sred;
+    sh.bars = bars;
+    sh.s_last = s_last;
+    sh.s_dead = s_dead;
+    sh.dyn = dyn;
+    sh.seq = 0;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < MAX_STAGES; ++b) mbar_init(&bars[b], 1);
+        mbar_init_fence();
+        *s_dead = 0;
+    }
+    __syncthreads();
+}
+
+template <class Op>
+__global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
+{
+    __shared__ double sred[(NTHREADS / 32) * MAX_DOTS];
+    __shared__ alignas(8) uint64_t bars[MAX_STAGES];
+    __shared__ int s_last, s_dead;
+    // the TMA ring, or the general engine's double-buffered plane: a CTA runs
+    // one engine at a time, and each march starts with a barrier
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    if ((long long)blockIdx.x >= reinterpret_cast<const ListHdr *>(a.list)->total) return;
+    EngineShared sh;
+    engine_setup(sh, sred, bars, &s_last, &s_dead, dyn_smem);
+    engine_body<Op>(a, sh);
 }
 
 // Dynamic shared memory a launch of k_engine<Op> needs.
@@ -919,10 +958,10 @@ struct OpCiFirst {
     __device__ __forceinline__ double load(int idx) const
     {
         if constexpr (SIDE == SIDE_S) {
-            return r[idx] - alpha * w[idx];
+            return gld(r + idx) - alpha * gld(w + idx);
         } else {
-            if (first) return r[idx];
-            return r[idx] + beta * (pold[idx] - omega * w[idx]);
+            if (first) return gld(r + idx);
+            return gld(r + idx) + beta * (gld(pold + idx) - omega * gld(w + idx));
         }
     }
     __device__ __forceinline__ double load_s(const void *const *h, int x) const
@@ -1061,7 +1100,7 @@ struct OpStencilDot {
     __device__ __forceinline__ double load_s(const void *const *h, int x) const { return Elem<T>::wides(h[0], x); }
     __device__ __forceinline__ double pw_s(const void *const *p, int x) const { return Elem<double>::lds(p[0], x); }
     __device__ __forceinline__ double sv(double u) const { return u; }
-    __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? __ldg(rt + idx) : 0.0; }
+    __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? gld(rt + idx) : 0.0; }
     template <int NA>
     __device__ __forceinline__ void emit(int idx, double u, double sx, double sy, double sz, double, double rtv,
                                          double (&acc)[NA]) const
@@ -1102,7 +1141,7 @@ struct OpStencil2Dot {
     __device__ __forceinline__ double load_s(const void *const *h, int x) const { return Elem<T>::wides(h[0], x); }
     __device__ __forceinline__ double pw_s(const void *const *p, int x) const { return Elem<double>::lds(p[0], x); }
     __device__ __forceinline__ double sv(double u) const { return u; }
-    __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? s[idx] : 0.0; }
+    __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? gld(s + idx) : 0.0; }
     template <int NA>
     __device__ __forceinline__ void emit(int idx, double u, double sx, double sy, double sz, double, double sv_,
                                          double (&acc)[NA]) const
@@ -1138,7 +1177,7 @@ struct OpApplyA {
         prole[0] = 0;
         cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
     }
-    __device__ __forceinline__ double load(int idx) const { return __ldg(u + idx); }
+    __device__ __forceinline__ double load(int idx) const { return gld(u + idx); }
     __device__ __forceinline__ double load_s(const void *const *h, int x) const { return Elem<double>::lds(h[0], x); }
     __device__ __forceinline__ double sv(double x) const { return x; }
     __device__ __forceinline__ PW pw(bool, int) const { return PW{}; }
@@ -1179,11 +1218,11 @@ struct OpResidual {
         prole[0] = ROLE_B;
         cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
     }
-    __device__ __forceinline__ double load(int idx) const { return x[idx]; }
+    __device__ __forceinline__ double load(int idx) const { return gld(x + idx); }
     __device__ __forceinline__ double load_s(const void *const *h, int x_) const { return Elem<double>::lds(h[0], x_); }
     __device__ __forceinline__ double pw_s(const void *const *p, int x_) const { return Elem<double>::lds(p[0], x_); }
     __device__ __forceinline__ double sv(double u) const { return u; }
-    __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? __ldg(b + idx) : 0.0; }
+    __device__ __forceinline__ double pw(bool valid, int idx) const { return valid ? gld(b + idx) : 0.0; }
     template <int NA>
     __device__ __forceinline__ void emit(int idx, double u, double sx, double sy, double sz, double, double bv,
                                          double (&acc)[NA]) const
@@ -1214,7 +1253,7 @@ struct OpInit0 {
         x = (double *)D.vec[ROLE_X];
     }
     struct In { double b; };
-    __device__ __forceinline__ In load(int idx) const { return In{__ldg(b + idx)}; }
+    __device__ __forceinline__ In load(int idx) const { return In{gld(b + idx)}; }
     template <int NA>
     __device__ __forceinline__ void apply(int idx, const In &v, double (&acc)[NA]) const
     {
@@ -1254,13 +1293,13 @@ struct OpUpdate {
     __device__ __forceinline__ In load(int idx) const
     {
         In v{};
-        v.x = x[idx];
+        v.x = gld(x + idx);
         v.p = Elem<T>::wide(ph, idx);
         if (!half) {
             v.r = Elem<T>::wide(rh, idx);
-            v.s = __ldg(s + idx);
-            v.t = __ldg(t + idx);
-            v.rt = __ldg(rt + idx);
+            v.s = gld(s + idx);
+            v.t = gld(t + idx);
+            v.rt = gld(rt + idx);
         }
         return v;
     }
@@ -1302,10 +1341,10 @@ struct OpPUpdate {
     __device__ __forceinline__ In load(int idx) const
     {
         In v{};
-        v.r = __ldg(r + idx);
+        v.r = gld(r + idx);
         if (!first) {
-            v.p = p[idx];
-            v.w = __ldg(w + idx);
+            v.p = gld(p + idx);
+            v.w = gld(w + idx);
         }
         return v;
     }
@@ -1333,7 +1372,7 @@ struct OpSUpdate {
         alpha = ld_scal(&sc->alpha);
     }
     struct In { double r, w; };
-    __device__ __forceinline__ In load(int idx) const { return In{__ldg(r + idx), __ldg(w + idx)}; }
+    __device__ __forceinline__ In load(int idx) const { return In{gld(r + idx), gld(w + idx)}; }
     template <int NA>
     __device__ __forceinline__ void apply(int idx, const In &u, double (&acc)[NA]) const
     {
@@ -1355,7 +1394,7 @@ struct OpDot {
         b = (const double *)D.vec[k.aux];
     }
     struct In { double a, b; };
-    __device__ __forceinline__ In load(int idx) const { return In{__ldg(a + idx), __ldg(b + idx)}; }
+    __device__ __forceinline__ In load(int idx) const { return In{gld(a + idx), gld(b + idx)}; }
     template <int NA>
     __device__ __forceinline__ void apply(int, const In &v, double (&acc)[NA]) const
     {

@@ -1,0 +1,152 @@
+// psolve_program.cuh -- the ordered phases of one outer Bi-CGSTAB iteration
+// (Algorithm 1, preconditioned by the Chebyshev iteration of Algorithm 2),
+// written once and run two ways:
+//   * on the host, V = Launcher: each phase becomes one kernel launch (plain
+//     or captured into a CUDA graph);
+//   * on the device, V = the persistent kernel's phase runner: each phase is
+//     run by every CTA of one cooperative launch, followed by a grid barrier.
+// V::go<Op>(cls, side, args, bytes_per_point, half_bytes_per_point, is_update)
+// runs one phase; the byte figures feed the host's traffic model and are
+// ignored on the device.  `iter` (1-based) only selects the first-iteration
+// byte figure.
+#pragma once
+#include <type_traits>
+
+#include "psolve_kernels.cuh"
+
+namespace psolve {
+
+template <class T>
+__host__ __device__ constexpr bool is_mixed()
+{
+    return !std::is_same<T, double>::value;
+}
+
+// Chebyshev sweeps k = 2..d (Algorithm 2 loop).  y_k overwrites y_{k-2}'s
+// buffer (read only at the same point), and the last sweep writes `final_role`.
+#pragma nv_exec_check_disable
+template <class T, class TB, bool BLK, bool WY, class V>
+__host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final_role, int skip)
+{
+    const double c = sizeof(T), cb = sizeof(TB);
+    for (int k = 2; k <= d; ++k) {
+        KArgs a{};
+        a.k = k;
+        a.skip = skip;
+        a.in = (k % 2 == 0) ? ROLE_YA : ROLE_YB;
+        a.z = (k % 2 == 0) ? ROLE_YB : ROLE_YA;
+        a.out = (k == d) ? final_role : a.z;
+        a.b = brole;
+        if (k == 2) v.template go<OpCiSweep<T, TB, BLK, WY>>(PSOLVE_K_CI_SWEEP3, side, a, c + cb + c);
+        else v.template go<OpCiSweep<T, TB, BLK, WY>>(PSOLVE_K_CI_SWEEP4, side, a, c + cb + c + c);
+    }
+}
+
+// One preconditioned outer iteration: direction update + M^-1 p, w = A p^
+// with r~.w (alpha), s = r - alpha w + M^-1 s with ||s||^2 (half-step test),
+// t = A r^ with t.s, t.t (omega), then x, r with r~.r, r.r (beta, stop test).
+#pragma nv_exec_check_disable
+template <class T, bool BLK, bool WY, class V>
+__host__ __device__ void prog_iteration_cheb(V &v, int d, int iter)
+{
+    using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
+    constexpr bool MIX = is_mixed<T>();
+    const double c = sizeof(T);
+    {
+        // p side: p_{i-1} = r + beta (p_{i-2} - omega w) fused with CI sweep 1
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_PCUR;
+        a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
+        const double rd = (iter == 1) ? 8.0 : 24.0;
+        v.template go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, rd + 8.0 + (MIX ? c : 0.0) + c);
+    }
+    prog_sweeps<T, TB, BLK, WY>(v, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP);
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_PH;
+        v.template go<OpStencilDot<T>>(PSOLVE_K_STENCIL_DOT, 0, a, c + 16.0);
+    }
+    {
+        // s side: s = r - alpha w fused with CI sweep 1 and ||s||^2
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_S;
+        a.out = (d <= 1) ? ROLE_RH : ROLE_YA;
+        v.template go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, 24.0 + (MIX ? c : 0.0) + c);
+    }
+    prog_sweeps<T, TB, BLK, WY>(v, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF);
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP | SKIP_HALF;
+        a.in = ROLE_RH;
+        v.template go<OpStencil2Dot<T>>(PSOLVE_K_STENCIL_2DOT, 1, a, c + 16.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_PH;
+        a.aux = ROLE_RH;
+        v.template go<OpUpdate<T>>(PSOLVE_K_UPDATE, 0, a, 48.0 + 2 * c, 16.0 + c, 1);
+    }
+}
+
+// One unpreconditioned outer iteration (M = I).
+#pragma nv_exec_check_disable
+template <class V>
+__host__ __device__ void prog_iteration_none(V &v, int iter)
+{
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        v.template go<OpPUpdate>(PSOLVE_K_OTHER, 0, a, iter == 1 ? 16.0 : 32.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_P;
+        v.template go<OpStencilDot<double>>(PSOLVE_K_STENCIL_DOT, 0, a, 24.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        v.template go<OpSUpdate>(PSOLVE_K_OTHER, 0, a, 24.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP | SKIP_HALF;
+        a.in = ROLE_S;
+        v.template go<OpStencil2Dot<double>>(PSOLVE_K_STENCIL_2DOT, 1, a, 16.0);
+    }
+    {
+        KArgs a{};
+        a.skip = SKIP_STOP;
+        a.in = ROLE_P;
+        a.aux = ROLE_S;
+        v.template go<OpUpdate<double>>(PSOLVE_K_UPDATE, 0, a, 56.0, 24.0, 1);
+    }
+}
+
+// r0 = b - A x0 (or r0 = b for x0 = 0) with ||b||^2 and ||r0||^2.
+#pragma nv_exec_check_disable
+template <class V>
+__host__ __device__ void prog_init(V &v, bool use_x0)
+{
+    KArgs a{};
+    a.skip = 0;
+    if (use_x0) v.template go<OpResidual<true>>(PSOLVE_K_INIT, 0, a, 32.0);
+    else v.template go<OpInit0>(PSOLVE_K_INIT, 0, a, 24.0);
+}
+
+// ||b - A x||^2 at exit.
+#pragma nv_exec_check_disable
+template <class V>
+__host__ __device__ void prog_true_residual(V &v)
+{
+    KArgs a{};
+    a.skip = 0;
+    v.template go<OpResidual<false>>(PSOLVE_K_OTHER, 0, a, 16.0);
+}
+
+} // namespace psolve
