@@ -13,8 +13,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpsolve.so")
-SOURCES = ["psolve_engine.cu", "psolve_api.cu", "psolve_persist.cu", "psolve_server.cu", "psolve_noalloc.cu",
-           "psolve_selfcheck.cu"]
+SOURCES = ["psolve_persist_f64.cu", "psolve_persist_f32.cu", "psolve_persist_bf16.cu", "psolve_engine.cu",
+           "psolve_api.cu", "psolve_persist.cu", "psolve_server.cu", "psolve_noalloc.cu", "psolve_selfcheck.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -192,25 +192,31 @@ struct PersistEntry {
 };
 
 // The whole solve of a launch list as one persistent kernel launch (captured
-// into a CUDA graph when use_graph; cached in *cache when given).  Returns
-// once the launch is enqueued; d_gs->err tells afterwards whether a barrier
-// wait gave up.
+// into a CUDA graph when use_graph; cached in *cache when given).  Uploads the
+// phase table from h_st (pinned; must stay untouched until the stream has
+// passed the launch), then enqueues the launch; d_st->gs.err tells afterwards
+// whether a barrier wait gave up.
 psolve_status run_persistent(cudaStream_t s, cudaStream_t cap, const Plan &plan, int sms, long long units,
-                             const Desc *d_desc, const int32_t *d_list, GridSync *d_gs, int maxit, bool use_x0,
-                             bool true_res, bool use_graph, std::vector<PersistEntry> *cache)
+                             const Desc *d_desc, const int32_t *d_list, PersistState *d_st, PersistState *h_st,
+                             int maxit, bool use_x0, bool true_res, bool use_graph, std::vector<PersistEntry> *cache)
 {
     int grid = 1;
     psolve_status st = persist_configure(plan, sms, units, &grid);
     if (st != PSOLVE_OK) return st;
+    persist_table(plan, use_x0, true_res, h_st);
+    const size_t off = offsetof(PersistState, n_init);
+    const size_t bytes = offsetof(PersistState, ph) - off +
+                         sizeof(PhaseRec) * (size_t)(h_st->n_init + h_st->n_iter + h_st->n_tail);
+    PS_CK(cudaMemcpyAsync(reinterpret_cast<char *>(d_st) + off, reinterpret_cast<char *>(h_st) + off, bytes,
+                          cudaMemcpyHostToDevice, s));
     PersistArgs a{};
     a.descs = d_desc;
     a.list = d_list;
-    a.gs = d_gs;
-    a.degree = plan.degree;
+    a.st = d_st;
     a.iters = maxit;
-    a.init = 1;
-    a.use_x0 = use_x0 ? 1 : 0;
-    a.true_res = true_res ? 1 : 0;
+    a.n_init = h_st->n_init;
+    a.n_iter = h_st->n_iter;
+    a.n_tail = h_st->n_tail;
     if (!use_graph) return persist_enqueue(s, plan, grid, a);
     if (cache)
         for (const PersistEntry &e : *cache)
@@ -378,7 +384,7 @@ struct psolve_ctx {
     cudaEvent_t poll_ev[2] = {nullptr, nullptr};
     std::vector<GraphEntry> graphs;
     std::vector<PersistEntry> pgraphs;    // single-launch graphs of the persistent solve
-    GridSync *d_gs = nullptr, *h_gs = nullptr; // its barrier state (device, pinned copy)
+    PersistState *d_ps = nullptr, *h_ps = nullptr; // its barrier words and phase table (device, pinned)
     std::vector<cudaEvent_t> events;
     double *d_hb = nullptr, *d_hx = nullptr; // device copies for psolve_solve_host
 };
@@ -415,8 +421,8 @@ void psolve_destroy(psolve_ctx *c)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     for (PersistEntry &g : c->pgraphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
-    if (c->d_gs) cudaFree(c->d_gs);
-    if (c->h_gs) cudaFreeHost(c->h_gs);
+    if (c->d_ps) cudaFree(c->d_ps);
+    if (c->h_ps) cudaFreeHost(c->h_ps);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     for (cudaEvent_t e : c->poll_ev)
         if (e) cudaEventDestroy(e);
@@ -499,8 +505,8 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
     CREATE_CK(cudaMalloc(&c->d_list, 4 * sizeof(int32_t)));
     CREATE_CK(cudaHostAlloc(&c->h_desc, sizeof(Desc), cudaHostAllocDefault));
     CREATE_CK(cudaHostAlloc(&c->h_sc, 3 * sizeof(Scal), cudaHostAllocDefault));
-    CREATE_CK(cudaMalloc(&c->d_gs, sizeof(GridSync)));
-    CREATE_CK(cudaHostAlloc(&c->h_gs, sizeof(GridSync), cudaHostAllocDefault));
+    CREATE_CK(cudaMalloc(&c->d_ps, sizeof(PersistState)));
+    CREATE_CK(cudaHostAlloc(&c->h_ps, sizeof(PersistState), cudaHostAllocDefault));
     CREATE_CK(cudaMalloc(&c->d_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM));
     CREATE_CK(cudaHostAlloc(&c->h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM, cudaHostAllocDefault));
     P.desc.tmap = c->d_tmap;
@@ -608,15 +614,15 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
 
     const bool tr = c->opts.true_residual != 0;
     if (c->opts.persistent) {
-        st = run_persistent(c->stream, c->cap, R.plan, R.sms, R.units, c->d_desc, c->d_list, c->d_gs, maxit, use_x0,
-                            tr, R.use_graph, &c->pgraphs);
+        st = run_persistent(c->stream, c->cap, R.plan, R.sms, R.units, c->d_desc, c->d_list, c->d_ps, c->h_ps,
+                            maxit, use_x0, tr, R.use_graph, &c->pgraphs);
         if (st != PSOLVE_OK) return st;
         R.launches += 1;
-        PS_CK(cudaMemcpyAsync(c->h_gs, c->d_gs, sizeof(GridSync), cudaMemcpyDeviceToHost, c->stream));
+        PS_CK(cudaMemcpyAsync(&c->h_ps->gs, &c->d_ps->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, c->stream));
         PS_CK(cudaMemcpyAsync(c->h_sc + 2, P.d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
         PS_CK(cudaStreamSynchronize(c->stream));
-        if (c->h_gs->err) {
-            set_error("persistent solve: a %s wait gave up", c->h_gs->err == 1 ? "grid barrier" : "tensor copy");
+        if (c->h_ps->gs.err) {
+            set_error("persistent solve: a %s wait gave up", c->h_ps->gs.err == 1 ? "grid barrier" : "tensor copy");
             return PSOLVE_TIMEOUT;
         }
         Scal s = c->h_sc[2];
@@ -866,7 +872,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     CUtensorMap *d_tmap = nullptr, *h_tmap = nullptr;
     int32_t *d_list = nullptr, *h_list = nullptr;
     Scal *h_sc = nullptr;
-    GridSync *d_gs = nullptr, *h_gs = nullptr;
+    PersistState *d_ps = nullptr, *h_ps = nullptr;
     cudaStream_t cap = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     std::vector<GraphEntry> graphs;
@@ -889,8 +895,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         if (h_tmap) cudaFreeHost(h_tmap);
         if (h_list) cudaFreeHost(h_list);
         if (h_sc) cudaFreeHost(h_sc);
-        if (d_gs) cudaFree(d_gs);
-        if (h_gs) cudaFreeHost(h_gs);
+        if (d_ps) cudaFree(d_ps);
+        if (h_ps) cudaFreeHost(h_ps);
     };
 #define BATCH_CK(call)                                                                       \
     do {                                                                                     \
@@ -912,8 +918,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     BATCH_CK(cudaHostAlloc(&h_list, list_bytes, cudaHostAllocDefault));
     BATCH_CK(cudaHostAlloc(&h_sc, 2 * sizeof(Scal) * count, cudaHostAllocDefault));
     if (o.persistent) {
-        BATCH_CK(cudaMalloc(&d_gs, sizeof(GridSync)));
-        BATCH_CK(cudaHostAlloc(&h_gs, sizeof(GridSync), cudaHostAllocDefault));
+        BATCH_CK(cudaMalloc(&d_ps, sizeof(PersistState)));
+        BATCH_CK(cudaHostAlloc(&h_ps, sizeof(PersistState), cudaHostAllocDefault));
     }
     BATCH_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     for (int k = 0; k < 2; ++k) BATCH_CK(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
@@ -975,17 +981,17 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     const bool tr = o.true_residual != 0;
     if (o.persistent) {
         // every problem's whole solve in one cooperative launch
-        st = run_persistent(s, cap, R.plan, R.sms, R.units, d_desc, d_list, d_gs, maxit, false, tr, R.use_graph,
-                            nullptr);
+        st = run_persistent(s, cap, R.plan, R.sms, R.units, d_desc, d_list, d_ps, h_ps, maxit, false, tr,
+                            R.use_graph, nullptr);
         if (st != PSOLVE_OK) {
             cleanup();
             return st;
         }
         R.launches += 1;
-        BATCH_CK(cudaMemcpyAsync(h_gs, d_gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+        BATCH_CK(cudaMemcpyAsync(&h_ps->gs, &d_ps->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
         BATCH_CK(cudaStreamSynchronize(s));
-        if (h_gs->err) {
-            set_error("persistent batch: a %s wait gave up", h_gs->err == 1 ? "grid barrier" : "tensor copy");
+        if (h_ps->gs.err) {
+            set_error("persistent batch: a %s wait gave up", h_ps->gs.err == 1 ? "grid barrier" : "tensor copy");
             cleanup();
             return PSOLVE_TIMEOUT;
         }

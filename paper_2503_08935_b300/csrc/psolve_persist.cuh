@@ -12,24 +12,44 @@ struct GridSync {
     int32_t pad_[2];
 };
 
+// One phase of the persistent kernel: which operation of the kernel's list
+// runs, with which arguments (descs/list are filled in on the device).
+struct PhaseRec {
+    int32_t kind;
+    int32_t pad_;
+    KArgs a;
+};
+
+// r0 + one outer iteration at the largest degree + the true residual.
+constexpr int MAX_PHASES = 2 * MAX_DEGREE + 8;
+
+// Device state of the persistent solve of one context or batch: the barrier
+// words and the phase table.  The table is uploaded before each launch, the
+// barrier words are reset by the launch's own memset node.
+struct PersistState {
+    GridSync gs;
+    int32_t n_init, n_iter, n_tail, pad_;
+    PhaseRec ph[MAX_PHASES];
+};
+
 struct PersistArgs {
     const Desc *descs;
     const int32_t *list; // launch list (ListHdr + entries)
-    GridSync *gs;
-    int32_t degree;      // Chebyshev degree d
+    PersistState *st;    // device
     int32_t iters;       // outer iterations at most (each problem also stops at its maxit)
-    int32_t init;        // 1: compute r0 and the norms first
-    int32_t use_x0;      // init from x0 (r0 = b - A x0) instead of x0 = 0
-    int32_t true_res;    // 1: ||b - A x||^2 after the loop
-    int32_t pad_;
+    int32_t n_init, n_iter, n_tail; // phases: [0, n_init) once, the next n_iter per iteration, then n_tail
 };
 
+// Fill st_host's phase table for `plan` (r0 from x0 or x0 = 0, the outer
+// iteration, the exit true residual when true_res).
+void persist_table(const Plan &plan, bool use_x0, bool true_res, PersistState *st_host);
 // Set the persistent kernel of `plan` up (shared memory, occupancy) and return
 // its grid size: resident CTAs per SM x SMs, at most the list's units.  Call
 // outside stream capture.
 psolve_status persist_configure(const Plan &plan, int sms, long long units, int *grid_out);
 // Enqueue the barrier reset and the cooperative launch on stream s
-// (capturable into a CUDA graph).
+// (capturable into a CUDA graph).  The phase table must already be on the
+// device.
 psolve_status persist_enqueue(cudaStream_t s, const Plan &plan, int grid, const PersistArgs &args);
 
 } // namespace psolve
