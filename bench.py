@@ -365,8 +365,9 @@ def run_gpu(args):
 def run_variants(args, b, x_ref, stream, B, torch):
     """The same 256^3 problem with the Chebyshev vectors in FP32 and in BF16
     (FP64 outer iteration), and with the rescaled bounds of the experimental
-    set-up (lambda_min x 100, lambda_max x (1 - 1e-4)), and the persistent
-    single-launch form of the solve; each reports time to
+    set-up (lambda_min x 100, lambda_max x (1 - 1e-4)), with residual
+    replacement every 5 iterations, and the persistent single-launch form of
+    the solve; each reports time to
     rtol 1e-10 (CUDA events, graph replay), iterations, the true residual and
     the relative L2 difference from the FP64 solution of the headline run."""
     out = {}
@@ -379,6 +380,8 @@ def run_variants(args, b, x_ref, stream, B, torch):
              ("fp64_gnocomm8_4x4x4", dict(blocks=(4, 4, 4)), B.PC_GNOCOMM_CHEB, 8),
              ("fp64_bj8_4x4x4", dict(blocks=(4, 4, 4)), B.PC_BJ_CHEB, 8),
              ("fp64_none", dict(), B.PC_NONE, 0),
+             ("fp32_cheb8_rr5", dict(cheb_prec=B.FP32, rr_every=5), B.PC_CHEB, 8),
+             ("bf16_cheb8_rr5", dict(cheb_prec=B.BF16, rr_every=5), B.PC_CHEB, 8),
              ("fp64_cheb8_persistent", dict(persistent=1), B.PC_CHEB, 8),
              ("fp32_cheb8_persistent", dict(cheb_prec=B.FP32, persistent=1), B.PC_CHEB, 8)]
     h = (1.0 / 257,) * 3

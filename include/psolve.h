@@ -95,8 +95,13 @@ typedef struct {
     int32_t timing;          /* 1: time each kernel class with CUDA events
                                 (plain launches); see psolve_result           */
     int32_t true_residual;   /* 1: recompute ||b - A x||/||b|| at exit        */
-    int32_t rr_every;        /* mixed precision: replace r by b - A x every
-                                rr_every iterations (0 = never)              */
+    int32_t rr_every;        /* residual replacement: after the update of
+                                every outer iteration that is a multiple of
+                                rr_every, replace the recursive r by the true
+                                b - A x, rescale beta and rho to it (rho =
+                                r~ . r) and take the stop test on its norm
+                                (0 = never).  Meant for the mixed-precision
+                                forms; not part of the paper's method.       */
     int32_t engine;          /* stencil kernels: 0 = TMA ring where possible
                                 (nx % 8 == 0, 16-byte aligned vectors), else
                                 the general engine; 1 = always the general

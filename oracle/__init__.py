@@ -76,6 +76,9 @@ def lib():
         L.oracle_precond_apply.argtypes = [I64, D, ctypes.POINTER(_PC), D, D]
         L.oracle_bicgstab.argtypes = [I64, D, D, D, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                       ctypes.POINTER(_PC), ctypes.c_int32, ctypes.POINTER(_Res), D, D]
+        L.oracle_bicgstab_rr.argtypes = [I64, D, D, D, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                         ctypes.POINTER(_PC), ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(_Res), D, D]
         _lib = L
     return _lib
 
@@ -182,17 +185,23 @@ class Result:
 
 
 def bicgstab(b, h, rtol=1e-10, maxit=2000, precond=PC_NONE, degree=0, blocks=(1, 1, 1),
-             lmin_scale=1.0, lmax_scale=1.0, x0=None, half_step_check=True):
-    """Algorithm 1.  Returns (x, Result).  ``x0`` None means x0 = 0."""
+             lmin_scale=1.0, lmax_scale=1.0, x0=None, half_step_check=True, rr_every=0):
+    """Algorithm 1.  Returns (x, Result).  ``x0`` None means x0 = 0.
+    ``rr_every`` > 0 adds residual replacement (not part of the paper's method)."""
     b = _vec(b)
     x = np.zeros_like(b) if x0 is None else _vec(x0).copy()
     hs = np.full(max(maxit, 1), np.nan)
     hr = np.full(max(maxit, 1), np.nan)
     pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale)
     r = _Res()
-    lib().oracle_bicgstab(_n(b.shape), _h(h), _dp(b), _dp(x), 1 if x0 is not None else 0, float(rtol),
-                          int(maxit), ctypes.byref(pc), 1 if half_step_check else 0, ctypes.byref(r),
-                          _dp(hs), _dp(hr))
+    if rr_every:
+        lib().oracle_bicgstab_rr(_n(b.shape), _h(h), _dp(b), _dp(x), 1 if x0 is not None else 0, float(rtol),
+                                 int(maxit), ctypes.byref(pc), 1 if half_step_check else 0, int(rr_every),
+                                 ctypes.byref(r), _dp(hs), _dp(hr))
+    else:
+        lib().oracle_bicgstab(_n(b.shape), _h(h), _dp(b), _dp(x), 1 if x0 is not None else 0, float(rtol),
+                              int(maxit), ctypes.byref(pc), 1 if half_step_check else 0, ctypes.byref(r),
+                              _dp(hs), _dp(hr))
     if r.status in (E_ARG, E_OOM):
         raise ValueError(f"oracle bicgstab failed with status {r.status}")
     it = r.iterations

@@ -247,7 +247,22 @@ int oracle_bicgstab(const int64_t n[3], const double h[3], const double *bvec,
                     const oracle_pc *pc, int32_t half_step_check,
                     oracle_result *res, double *hist_s, double *hist_r)
 {
+    return oracle_bicgstab_rr(n, h, bvec, x, use_x0, rtol, maxit, pc, half_step_check, 0,
+                              res, hist_s, hist_r);
+}
+
+/* rr_every > 0 adds residual replacement, which is not part of the paper's
+ * method: after the update of iteration i (a multiple of rr_every, i < maxit,
+ * not converged), r is recomputed as b - A x, its norm takes the stop test,
+ * and beta (proportional to rho_i) and rho_i are rescaled to rho = r~ . r of
+ * the new r.  rr_every = 0 is Algorithm 1 exactly. */
+int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec,
+                       double *x, int32_t use_x0, double rtol, int32_t maxit,
+                       const oracle_pc *pc, int32_t half_step_check, int32_t rr_every,
+                       oracle_result *res, double *hist_s, double *hist_r)
+{
     memset(res, 0, sizeof(*res));
+    if (rr_every < 0) return res->status = ORACLE_E_ARG;
     for (int d = 0; d < 3; ++d)
         if (n[d] < 1 || !(h[d] > 0.0)) return res->status = ORACLE_E_ARG;
     if (maxit < 0 || !(rtol >= 0.0) || !pc || pc->degree < 0) return res->status = ORACLE_E_ARG;
@@ -324,9 +339,24 @@ int oracle_bicgstab(const int64_t n[3], const double h[3], const double *bvec,
         if (hist_r) hist_r[i - 1] = rnorm / nb;
         if (!finite(rnorm)) { st = ORACLE_NONFINITE; break; }
         if (rnorm / nb <= rtol) { st = ORACLE_OK; break; }
-        const double rho_new = oracle_dot(N, rt, r);
+        double rho_new = oracle_dot(N, rt, r);
         if (rho_new == 0.0) { st = ORACLE_BREAKDOWN; break; }
-        const double beta = (rho_new / rho) * (alpha / omega);
+        double beta = (rho_new / rho) * (alpha / omega);
+        if (rr_every > 0 && i % rr_every == 0 && i < maxit) {
+            /* residual replacement (see above) */
+            e = oracle_apply_A(n, h, NULL, x, t);
+            if (e) { st = e; break; }
+            for (int64_t q = 0; q < N; ++q) r[q] = bvec[q] - t[q];
+            rnorm = sqrt(oracle_dot(N, r, r));
+            const double rho_true = oracle_dot(N, rt, r);
+            res->rel_res_recursive = rnorm / nb;
+            if (hist_r) hist_r[i - 1] = rnorm / nb;
+            if (!finite(rnorm) || !finite(rho_true)) { st = ORACLE_NONFINITE; break; }
+            if (rnorm / nb <= rtol) { st = ORACLE_OK; break; }
+            if (rho_true == 0.0) { st = ORACLE_BREAKDOWN; break; }
+            beta = beta * (rho_true / rho_new);
+            rho_new = rho_true;
+        }
         rho = rho_new;
         for (int64_t q = 0; q < N; ++q) p[q] = r[q] + beta * (p[q] - omega * w[q]);
     }

@@ -64,6 +64,12 @@ int oracle_bicgstab(const int64_t n[3], const double h[3], const double *b,
                     double *x, int32_t use_x0, double rtol, int32_t maxit,
                     const oracle_pc *pc, int32_t half_step_check,
                     oracle_result *res, double *hist_s, double *hist_r);
+/* oracle_bicgstab with residual replacement every rr_every iterations
+ * (0 = none; an addition to the paper's method, see psolve_oracle.c). */
+int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *b,
+                       double *x, int32_t use_x0, double rtol, int32_t maxit,
+                       const oracle_pc *pc, int32_t half_step_check, int32_t rr_every,
+                       oracle_result *res, double *hist_s, double *hist_r);
 
 #ifdef __cplusplus
 }

@@ -294,6 +294,15 @@ psolve_status check_grid(const int64_t g[3])
     return PSOLVE_OK;
 }
 
+psolve_status check_rr(int rr_every)
+{
+    if (rr_every < 0) {
+        set_error("rr_every must be >= 0");
+        return PSOLVE_E_ARG;
+    }
+    return PSOLVE_OK;
+}
+
 psolve_status check_solve_args(double rtol, int maxit, int precond, int degree)
 {
     if (!(rtol >= 0.0) || !std::isfinite(rtol)) {
@@ -557,6 +566,8 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
         set_error("timing mode times separate kernel launches; it cannot run with persistent = 1");
         return PSOLVE_E_ARG;
     }
+    st = check_rr(c->opts.rr_every);
+    if (st != PSOLVE_OK) return st;
     PS_CK(cudaSetDevice(c->di.dev));
     Problem &P = c->P;
     st = problem_set_cheb(P, precond, degree, c->opts.lmin_scale, c->opts.lmax_scale);
@@ -566,6 +577,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     D.rtol = rtol;
     D.maxit = maxit;
     D.half_check = c->opts.half_step_check ? 1 : 0;
+    D.rr_every = c->opts.rr_every;
     D.vec[ROLE_B] = (void *)rhs;
     D.vec[ROLE_X] = x;
     D.vec[ROLE_RT] = use_x0 ? P.desc.vec[ROLE_RT] : (void *)rhs;
@@ -588,6 +600,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     R.plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
     R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : P.prec;
     R.plan.exact_bounds = c->opts.lmin_scale == 1.0 && c->opts.lmax_scale == 1.0;
+    R.plan.rr_every = c->opts.rr_every;
     R.use_graph = c->opts.use_graph != 0;
     R.timing = c->opts.timing != 0;
     R.npts = (double)P.npts();
@@ -832,6 +845,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         set_error("timing mode times separate kernel launches; it cannot run with persistent = 1");
         return PSOLVE_E_ARG;
     }
+    st = check_rr(o.rr_every);
+    if (st != PSOLVE_OK) return st;
     DevInfo di;
     st = device_info(&di);
     if (st != PSOLVE_OK) return st;
@@ -938,6 +953,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         P.desc.rtol = rtol;
         P.desc.maxit = maxit;
         P.desc.half_check = o.half_step_check ? 1 : 0;
+        P.desc.rr_every = o.rr_every;
         P.desc.vec[ROLE_B] = (void *)rhs[q];
         P.desc.vec[ROLE_X] = x[q];
         P.desc.vec[ROLE_RT] = (void *)rhs[q];
@@ -964,6 +980,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     R.plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
     R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : o.cheb_prec;
     R.plan.exact_bounds = o.lmin_scale == 1.0 && o.lmax_scale == 1.0;
+    R.plan.rr_every = o.rr_every;
     R.use_graph = o.use_graph != 0;
     R.timing = o.timing != 0;
     R.npts = 0;

@@ -72,6 +72,7 @@ void Launcher::go(int cls, int side, KArgs a, double bytes_per_pt, double half_b
     rec.side = side;
     rec.iter = iter;
     rec.is_update = is_update;
+    rec.rr_every = rr_every;
     rec.bytes = bytes_per_pt * npts;
     rec.bytes_half = half_bytes_per_pt * npts;
     if (dry) {
@@ -162,31 +163,33 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
 
 // --------------------------------------------------- per-iteration kernels --
 template <class T, bool BLK>
-static void iteration_cheb(Launcher &L, int d, bool eb)
+static void iteration_cheb(Launcher &L, int d, bool eb, bool rr)
 {
-    if (eb) prog_iteration_cheb<T, BLK, false>(L, d, L.iter);
-    else prog_iteration_cheb<T, BLK, true>(L, d, L.iter);
+    if (eb) prog_iteration_cheb<T, BLK, false>(L, d, L.iter, rr);
+    else prog_iteration_cheb<T, BLK, true>(L, d, L.iter, rr);
 }
 
 void enqueue_iteration(Launcher &L, const Plan &plan)
 {
+    const bool rr = plan.rr_every > 0;
+    L.rr_every = plan.rr_every;
     if (plan.precond == PSOLVE_PC_NONE) {
-        prog_iteration_none(L, L.iter);
+        prog_iteration_none(L, L.iter, rr);
         return;
     }
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
     switch (plan.prec) {
     case PSOLVE_FP32:
-        if (blk) iteration_cheb<float, true>(L, plan.degree, plan.exact_bounds);
-        else iteration_cheb<float, false>(L, plan.degree, plan.exact_bounds);
+        if (blk) iteration_cheb<float, true>(L, plan.degree, plan.exact_bounds, rr);
+        else iteration_cheb<float, false>(L, plan.degree, plan.exact_bounds, rr);
         break;
     case PSOLVE_BF16:
-        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds);
-        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds);
+        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, rr);
+        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, rr);
         break;
     default:
-        if (blk) iteration_cheb<double, true>(L, plan.degree, plan.exact_bounds);
-        else iteration_cheb<double, false>(L, plan.degree, plan.exact_bounds);
+        if (blk) iteration_cheb<double, true>(L, plan.degree, plan.exact_bounds, rr);
+        else iteration_cheb<double, false>(L, plan.degree, plan.exact_bounds, rr);
         break;
     }
 }
@@ -255,6 +258,8 @@ void enqueue_precond(Launcher &L, const Plan &plan)
 
 bool launch_did_work(const LaunchRec &r, int final_iter, int half_exit)
 {
+    if (r.side == 2) // replacement: counted on the multiples of rr_every before the exit iteration
+        return r.rr_every > 0 && r.iter > 0 && r.iter % r.rr_every == 0 && r.iter < final_iter;
     if (r.iter > final_iter) return false;
     if (r.iter == final_iter && half_exit && r.side == 1) return false;
     return true;

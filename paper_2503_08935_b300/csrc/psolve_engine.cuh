@@ -45,9 +45,11 @@ struct Plan {
     int degree = 0;
     int prec = PSOLVE_FP64;
     bool exact_bounds = false; // scales (1, 1): the sweeps' y coefficient is zero
+    int rr_every = 0;          // residual replacement period (0: none)
     bool operator==(const Plan &o) const
     {
-        return precond == o.precond && degree == o.degree && prec == o.prec && exact_bounds == o.exact_bounds;
+        return precond == o.precond && degree == o.degree && prec == o.prec && exact_bounds == o.exact_bounds &&
+               rr_every == o.rr_every;
     }
 };
 
@@ -56,9 +58,11 @@ inline size_t ci_elem_bytes(int prec) { return prec == PSOLVE_FP64 ? 8 : (prec =
 // One kernel launch as the host sees it (for timing and byte accounting).
 struct LaunchRec {
     int cls;
-    int side;          // 0: always runs; 1: skipped after a passed half-step test
+    int side;          // 0: always runs; 1: skipped after a passed half-step test;
+                       // 2: runs on iterations that are multiples of rr_every
     int iter;          // outer iteration (1-based); 0 = set-up, -1 = after the loop
     int is_update;
+    int rr_every;
     double bytes;      // algorithmic bytes if the kernel does its full work
     double bytes_half; // update kernel after a passed half-step test
     cudaEvent_t ev0, ev1;
@@ -75,6 +79,7 @@ struct Launcher {
     bool dry = false;
     bool timing = false;
     int iter = 0;       // outer iteration being issued (byte model only)
+    int rr_every = 0;   // residual replacement period (byte model only)
     int64_t launches = 0;
     double npts = 0;    // points per problem for the byte model
     std::vector<LaunchRec> *recs = nullptr;

@@ -211,7 +211,8 @@ enum Epi {
     EPI_OMEGA,   // v0 = t . s, v1 = t . t -> omega = v0 / v1       (Alg. 1)
     EPI_UPDATE,  // v0 = r~ . r, v1 = ||r||^2 -> test, beta, rho     (Alg. 1)
     EPI_TRUE,    // v0 = ||b - A x||^2
-    EPI_RAW      // store v in red[]
+    EPI_RAW,     // store v in red[]
+    EPI_REPLACE  // v0 = r~ . r, v1 = ||r||^2 of r = b - A x -> rescale beta, rho; test
 };
 
 constexpr int ST_OK = 0, ST_NOT_CONVERGED = 4, ST_BREAKDOWN = 5, ST_NONFINITE = 6;
@@ -299,6 +300,18 @@ __device__ void epilogue(const Desc &D, Scal *sc_mem, const double (&v)[ND])
                 sc->first = 0;
                 if (sc->iter >= sc->maxit) stop_with(sc, ST_NOT_CONVERGED);
             }
+        }
+    } else if constexpr (EPI == EPI_REPLACE) {
+        // beta = (rho_i / rho_{i-1})(alpha / omega) is proportional to rho_i:
+        // rescale it to rho_i = r~ . r of the replaced residual
+        const double rho_new = v[0], rr = v[1];
+        sc->rr = rr;
+        if (!isfinite(rr) || !isfinite(rho_new)) stop_with(sc, ST_NONFINITE);
+        else if (rr <= sc->thr2) stop_with(sc, ST_OK);
+        else if (rho_new == 0.0) stop_with(sc, ST_BREAKDOWN);
+        else {
+            sc->beta = sc->beta * (rho_new / sc->rho);
+            sc->rho = rho_new;
         }
     } else if constexpr (EPI == EPI_TRUE) {
         sc->true_rr = v[0];
@@ -789,6 +802,7 @@ __device__ __forceinline__ void engine_body(const KArgs &a, EngineShared &sh)
         Scal *sc = D.sc;
         if ((a.skip & SKIP_STOP) && ld_flag(&sc->stop)) continue;
         if ((a.skip & SKIP_HALF) && ld_flag(&sc->half)) continue;
+        if ((a.skip & SKIP_NOT_RR) && (D.rr_every <= 0 || ld_flag(&sc->iter) % D.rr_every != 0)) continue;
 
         Op op(D, a, sc);
         const int ntiles = D.tiles_x * D.tiles_y;
@@ -1236,6 +1250,58 @@ struct OpResidual {
         } else {
             acc[0] += rv * rv;
         }
+    }
+};
+
+// Residual replacement: r = b - A x replaces the recursive residual, with
+// r~.r and ||r||^2 (the epilogue rescales beta and rho to the new r).  Runs
+// after the update of outer iterations that are multiples of rr_every.
+struct OpReplace {
+    using C = double;
+    using U = double;
+    struct PW {
+        double b, rt;
+    };
+    static constexpr int ND = 2, EPI = EPI_REPLACE;
+    static constexpr bool STENCIL = true, BLOCKED = false;
+    using TH = double;
+    using TP = double;
+    static constexpr int NH = 1, NP = 2;
+    static constexpr bool XFORM = false;
+    int nh = 1, np = 2, hrole[NH], prole[NP];
+    const double *x, *b, *rt;
+    double *r;
+    double cc, cx, cy, cz;
+    __device__ OpReplace(const Desc &D, const KArgs &, Scal *)
+    {
+        x = (const double *)D.vec[ROLE_X];
+        b = (const double *)D.vec[ROLE_B];
+        rt = (const double *)D.vec[ROLE_RT];
+        r = (double *)D.vec[ROLE_R];
+        hrole[0] = ROLE_X;
+        prole[0] = ROLE_B;
+        prole[1] = ROLE_RT;
+        cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
+    }
+    __device__ __forceinline__ double load(int idx) const { return gld(x + idx); }
+    __device__ __forceinline__ double load_s(const void *const *h, int x_) const { return Elem<double>::lds(h[0], x_); }
+    __device__ __forceinline__ PW pw_s(const void *const *p, int x_) const
+    {
+        return PW{Elem<double>::lds(p[0], x_), Elem<double>::lds(p[1], x_)};
+    }
+    __device__ __forceinline__ double sv(double u) const { return u; }
+    __device__ __forceinline__ PW pw(bool valid, int idx) const
+    {
+        return valid ? PW{gld(b + idx), gld(rt + idx)} : PW{0.0, 0.0};
+    }
+    template <int NA>
+    __device__ __forceinline__ void emit(int idx, double u, double sx, double sy, double sz, double, const PW &p,
+                                         double (&acc)[NA]) const
+    {
+        const double rv = p.b - apply_A_terms(cc, cx, cy, cz, u, sx, sy, sz);
+        r[idx] = rv;
+        acc[0] += p.rt * rv;
+        acc[1] += rv * rv;
     }
 };
 

@@ -108,12 +108,12 @@ struct PersistOps { // Chebyshev-preconditioned iteration
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     using List = TypeList<OpInit0, OpResidual<true>, OpResidual<false>, OpCiFirst<T, BLK, SIDE_P>,
                           OpCiSweep<T, TB, BLK, WY>, OpStencilDot<T>, OpCiFirst<T, BLK, SIDE_S>, OpStencil2Dot<T>,
-                          OpUpdate<T>>;
+                          OpUpdate<T>, OpReplace>;
 };
 template <class T, bool BLK, bool WY>
 struct PersistOps<0, T, BLK, WY> { // unpreconditioned iteration
     using List = TypeList<OpInit0, OpResidual<true>, OpResidual<false>, OpPUpdate, OpStencilDot<double>, OpSUpdate,
-                          OpStencil2Dot<double>, OpUpdate<double>>;
+                          OpStencil2Dot<double>, OpUpdate<double>, OpReplace>;
 };
 
 // Runs operation number `kind` of the list.  The phase's arguments come from
@@ -238,8 +238,8 @@ void table_of(const Plan &plan, bool use_x0, bool true_res, PersistState *st)
     TableBuilder<L> tb{st->ph};
     prog_init(tb, use_x0);
     st->n_init = tb.n;
-    if constexpr (KIND == 0) prog_iteration_none(tb, 2);
-    else prog_iteration_cheb<T, BLK, WY>(tb, plan.degree, 2);
+    if constexpr (KIND == 0) prog_iteration_none(tb, 2, plan.rr_every > 0);
+    else prog_iteration_cheb<T, BLK, WY>(tb, plan.degree, 2, plan.rr_every > 0);
     st->n_iter = tb.n - st->n_init;
     if (true_res) prog_true_residual(tb);
     st->n_tail = tb.n - st->n_init - st->n_iter;
@@ -257,8 +257,8 @@ PersistKernel kernel_of()
     SmemMax m;
     prog_init(m, false);
     prog_init(m, true);
-    if constexpr (KIND == 0) prog_iteration_none(m, 1);
-    else prog_iteration_cheb<T, BLK, WY>(m, 3, 1);
+    if constexpr (KIND == 0) prog_iteration_none(m, 1, true);
+    else prog_iteration_cheb<T, BLK, WY>(m, 3, 1, true);
     prog_true_residual(m);
     return PersistKernel{k_persist<KIND, T, BLK, WY>, m.bytes, table_of<KIND, T, BLK, WY>};
 }

@@ -3,11 +3,11 @@
 // written once and run two ways:
 //   * on the host, V = Launcher: each phase becomes one kernel launch (plain
 //     or captured into a CUDA graph);
-//   * on the device, V = the persistent kernel's phase runner: each phase is
-//     run by every CTA of one cooperative launch, followed by a grid barrier.
+//   * on the host, V = the persistent kernel's table builder: the phases are
+//     recorded as (operation, arguments), and one cooperative launch runs
+//     them on every CTA with a grid barrier after each.
 // V::go<Op>(cls, side, args, bytes_per_point, half_bytes_per_point, is_update)
-// runs one phase; the byte figures feed the host's traffic model and are
-// ignored on the device.  `iter` (1-based) only selects the first-iteration
+// takes one phase; the byte figures feed the host's traffic model.  `iter` (1-based) only selects the first-iteration
 // byte figure.
 #pragma once
 #include <type_traits>
@@ -20,6 +20,18 @@ template <class T>
 __host__ __device__ constexpr bool is_mixed()
 {
     return !std::is_same<T, double>::value;
+}
+
+// Residual replacement after the update: r = b - A x for the problems whose
+// outer iteration count is a multiple of their rr_every (side 2: the byte
+// model counts it only on those iterations).
+#pragma nv_exec_check_disable
+template <class V>
+__host__ __device__ void prog_replace(V &v)
+{
+    KArgs a{};
+    a.skip = SKIP_STOP | SKIP_NOT_RR;
+    v.template go<OpReplace>(PSOLVE_K_OTHER, 2, a, 32.0);
 }
 
 // Chebyshev sweeps k = 2..d (Algorithm 2 loop).  y_k overwrites y_{k-2}'s
@@ -44,10 +56,11 @@ __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final
 
 // One preconditioned outer iteration: direction update + M^-1 p, w = A p^
 // with r~.w (alpha), s = r - alpha w + M^-1 s with ||s||^2 (half-step test),
-// t = A r^ with t.s, t.t (omega), then x, r with r~.r, r.r (beta, stop test).
+// t = A r^ with t.s, t.t (omega), then x, r with r~.r, r.r (beta, stop test),
+// then, when rr, the residual replacement.
 #pragma nv_exec_check_disable
 template <class T, bool BLK, bool WY, class V>
-__host__ __device__ void prog_iteration_cheb(V &v, int d, int iter)
+__host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr)
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
@@ -90,12 +103,13 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter)
         a.aux = ROLE_RH;
         v.template go<OpUpdate<T>>(PSOLVE_K_UPDATE, 0, a, 48.0 + 2 * c, 16.0 + c, 1);
     }
+    if (rr) prog_replace(v);
 }
 
 // One unpreconditioned outer iteration (M = I).
 #pragma nv_exec_check_disable
 template <class V>
-__host__ __device__ void prog_iteration_none(V &v, int iter)
+__host__ __device__ void prog_iteration_none(V &v, int iter, bool rr)
 {
     {
         KArgs a{};
@@ -126,6 +140,7 @@ __host__ __device__ void prog_iteration_none(V &v, int iter)
         a.aux = ROLE_S;
         v.template go<OpUpdate<double>>(PSOLVE_K_UPDATE, 0, a, 56.0, 24.0, 1);
     }
+    if (rr) prog_replace(v);
 }
 
 // r0 = b - A x0 (or r0 = b for x0 = 0) with ||b||^2 and ||r0||^2.

@@ -97,7 +97,7 @@ struct Desc {
     // tensor copies (nx % 8 == 0, 16-byte aligned vectors); tmap[2*role] is the
     // role's halo-box map, tmap[2*role + 1] its plain-box map.
     int32_t tma;
-    int32_t pad_;
+    int32_t rr_every;   // residual replacement every rr_every outer iterations (0: never)
     const CUtensorMap *tmap;
 };
 
@@ -122,5 +122,6 @@ constexpr int ST_TIMEOUT = 7; // a bounded wait of the TMA ring gave up
 
 constexpr int SKIP_STOP = 1; // skip problems whose `stop` is set
 constexpr int SKIP_HALF = 2; // skip problems whose `half` is set
+constexpr int SKIP_NOT_RR = 4; // skip problems whose iteration count is not a multiple of rr_every
 
 } // namespace psolve

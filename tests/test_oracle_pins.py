@@ -382,3 +382,52 @@ def test_rescaled_interval_inverted_is_rejected():
     """lambda_min x 100 exceeds lambda_max on a tiny grid: the interval is empty."""
     with pytest.raises(ValueError):
         O.cheb_interval((4, 4, 4), I.default_h((4, 4, 4)), O.PC_CHEB, (1, 1, 1), 100.0, 1 - 1e-4)
+
+
+# ------------------------------------------- residual replacement (added form) --
+# Not part of the paper's method: every rr_every iterations r is recomputed as
+# b - A x and beta, rho are rescaled to it.  In exact arithmetic the recursive
+# and the true residual coincide, so the iteration is unchanged.
+@pytest.mark.parametrize("shape", [(4, 4, 4), (6, 5, 4)])
+@pytest.mark.parametrize("rr", [1, 2])
+def test_residual_replacement_matches_dense_solve(shape, rr):
+    h = I.default_h(shape)
+    P = dense_P(shape, h)
+    b = I.rhs_uniform(shape, seed=23)
+    x, res = O.bicgstab(b, h, rtol=1e-13, maxit=1000, precond=O.PC_CHEB, degree=3, rr_every=rr)
+    assert res.status == O.OK
+    xs = np.linalg.solve(P, b.ravel())
+    assert rel(x, xs) <= 10 * np.linalg.cond(P) * 1e-13
+    assert res.rel_res_true <= 1e-12
+
+
+def test_residual_replacement_that_never_triggers_is_algorithm_1():
+    shape = (12, 10, 9)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=24)
+    x0, r0 = O.bicgstab(b, h, rtol=1e-10, maxit=500, precond=O.PC_CHEB, degree=4)
+    x1, r1 = O.bicgstab(b, h, rtol=1e-10, maxit=500, precond=O.PC_CHEB, degree=4, rr_every=r0.iterations + 1)
+    assert r1.iterations == r0.iterations and np.array_equal(x0, x1)
+
+
+@pytest.mark.parametrize("pc", PCS[:2])
+def test_residual_replacement_every_iteration_closes_the_residual_gap(pc):
+    """With rr_every = 1 the recursive residual at exit is one update away from a
+    true one, so it agrees with the recomputed true residual far below rtol, and the
+    iteration count stays within a few of Algorithm 1's."""
+    shape = (16, 16, 16)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=42)
+    rtol = 1e-10
+    xa, ra = O.bicgstab(b, h, rtol=rtol, maxit=2000, precond=pc[0], degree=pc[1] + 2)
+    x, res = O.bicgstab(b, h, rtol=rtol, maxit=2000, precond=pc[0], degree=pc[1] + 2, rr_every=1)
+    assert res.status == O.OK and res.rel_res_recursive <= rtol
+    assert abs(res.rel_res_true - res.rel_res_recursive) <= 1e-3 * rtol
+    assert abs(res.iterations - ra.iterations) <= 2
+    assert rel(x, xa) <= 1e-8
+
+
+def test_residual_replacement_rejects_negative_period():
+    b = I.rhs_uniform((4, 4, 4), seed=1)
+    with pytest.raises(ValueError):
+        O.bicgstab(b, I.default_h((4, 4, 4)), rr_every=-1)
