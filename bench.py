@@ -471,6 +471,17 @@ def extra_batch(B, I, torch, stream, count=64):
     run_p()
     ms_p, infos_p = _timed_cuda(run_p, stream, torch, 2)
     same_p = all(bool(torch.equal(a, c)) for a, c in zip(xs, xg))
+    # with the slab depth and engine of each grid shape picked by the autotuner
+    # (the first call tunes and is not timed)
+    tuned = {}
+    for name, kw in (("graph", {}), ("persistent", {"persistent": 1})):
+        run_t = lambda: B.solve_batch(bs, xs, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8, stream=stream,
+                                      autotune=1, **kw)
+        run_t()
+        ms_t, infos_t = _timed_cuda(run_t, stream, torch, 2)
+        tuned[name] = {"ms": ms_t, "solves_per_s": count * 1e3 / ms_t, "all_ok": all(i.status == B.OK for i in infos_t),
+                       "max_iterations": max(i.iterations for i in infos_t)}
+    tuned["slab_planes"] = sorted({(i.slab_planes, i.engine) for i in infos_t})
     solvers = [B.Solver(sh, stream=stream) for sh in shapes]
 
     def seq():
@@ -487,6 +498,7 @@ def extra_batch(B, I, torch, stream, count=64):
             "points_total": npts, "batched_ms": ms_b, "batched_solves_per_s": count * 1e3 / ms_b,
             "persistent_ms": ms_p, "persistent_solves_per_s": count * 1e3 / ms_p,
             "persistent_launches": infos_p[0].kernel_launches, "persistent_bitwise_equal_to_graph": same_p,
+            "autotuned": tuned,
             "sequential_ms": ms_s, "sequential_solves_per_s": count * 1e3 / ms_s, "speedup": ms_s / ms_b,
             "all_ok": all(i.status == B.OK for i in infos), "iterations_equal_to_solo": same,
             "max_iterations": max(i.iterations for i in infos)}

@@ -114,12 +114,20 @@ typedef struct {
                                 bitwise those of the per-kernel path.  Not
                                 with timing = 1.  A barrier wait that gives up
                                 (4 s) ends the solve with PSOLVE_TIMEOUT.     */
-    int32_t reserved[3];
+    int32_t autotune;        /* 1: pick the slab depth (z planes per work
+                                unit) and the stencil engine of each grid
+                                shape by timing candidates on the GPU (at
+                                psolve_create, or per shape in a batch);
+                                decisions are cached per process and, when
+                                the environment variable PSOLVE_TUNE_CACHE
+                                names a file, in that file across processes.
+                                0: built-in rule.                            */
+    int32_t reserved[2];
 } psolve_opts;
 
 /* Fill *o with the defaults: scales 1, 1; blocks 1,1,1; FP64; half-step check
  * on; x0 = 0; poll auto; graphs on; timing off; true residual on; rr off;
- * engine auto; per-kernel launches (persistent off). */
+ * engine auto; per-kernel launches (persistent off); autotune off. */
 PSOLVE_API void psolve_opts_default(psolve_opts *o);
 
 /* Kernel classes reported by timing mode (psolve_result.kclass_*). */
@@ -141,6 +149,9 @@ typedef struct {
     int32_t iterations;        /* outer index i at exit (0 if r0 passes)       */
     int32_t half_step_exit;    /* 1 if the exit was the ||s|| half-step test   */
     int32_t engine;            /* stencil engine used: 1 TMA ring, 0 general   */
+    int32_t slab_planes;       /* z planes per work unit of the grid          */
+    int32_t tuned;             /* 1: slab and engine chosen by the autotuner,
+                                  2: taken from its on-disk cache, 0: rule    */
     double rel_res_recursive;  /* ||r||/||b|| of the recursive residual        */
     double rel_res_true;       /* ||b - A x||/||b|| at exit (if enabled)       */
     double seconds;            /* wall time of the call                        */

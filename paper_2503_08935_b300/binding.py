@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
         ("rr_every", ctypes.c_int32),
         ("engine", ctypes.c_int32),
         ("persistent", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("autotune", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -59,6 +60,8 @@ class Result(ctypes.Structure):
         ("iterations", ctypes.c_int32),
         ("half_step_exit", ctypes.c_int32),
         ("engine", ctypes.c_int32),
+        ("slab_planes", ctypes.c_int32),
+        ("tuned", ctypes.c_int32),
         ("rel_res_recursive", ctypes.c_double),
         ("rel_res_true", ctypes.c_double),
         ("seconds", ctypes.c_double),
@@ -184,6 +187,8 @@ class SolveInfo:
     kernel_launches: int
     kclass: dict
     engine: int = 0
+    slab_planes: int = 0
+    tuned: int = 0
 
     @property
     def status_name(self):
@@ -193,7 +198,7 @@ class SolveInfo:
 def _info(r: Result) -> SolveInfo:
     d = r.as_dict()
     return SolveInfo(r.status, r.iterations, bool(r.half_step_exit), r.rel_res_recursive, r.rel_res_true,
-                     r.seconds, r.model_bytes, r.kernel_launches, d["kclass"], r.engine)
+                     r.seconds, r.model_bytes, r.kernel_launches, d["kclass"], r.engine, r.slab_planes, r.tuned)
 
 
 class Solver:

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpsolve.so")
 SOURCES = ["psolve_persist_f64.cu", "psolve_persist_f32.cu", "psolve_persist_bf16.cu", "psolve_engine.cu",
-           "psolve_api.cu", "psolve_persist.cu", "psolve_server.cu", "psolve_noalloc.cu", "psolve_selfcheck.cu"]
+           "psolve_api.cu", "psolve_persist.cu", "psolve_server.cu", "psolve_noalloc.cu", "psolve_selfcheck.cu",
+           "psolve_tune.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
@@ -40,16 +41,22 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     objs = []
     build_dir = os.path.join(HERE, "_build")
     os.makedirs(build_dir, exist_ok=True)
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    headers.append(os.path.join(HERE, "..", "include", "psolve.h"))
+    t_headers = max(os.path.getmtime(f) for f in headers)
     procs = []
-    for src in SOURCES:  # one nvcc per source, all at once
+    for src in SOURCES:  # one nvcc per out-of-date source, all at once
         obj = os.path.join(build_dir, src.replace(".cu", ".o"))
+        objs.append(obj)
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) > max(
+                t_headers, os.path.getmtime(os.path.join(CSRC, src))):
+            continue
         cmd = [NVCC, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if ptxas_v:
             cmd += ["-Xptxas", "-v"]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((cmd, subprocess.Popen(cmd)))
-        objs.append(obj)
     failed = [cmd for cmd, p in procs if p.wait() != 0]
     if failed:
         raise subprocess.CalledProcessError(1, failed[0])

@@ -14,6 +14,7 @@
 
 #include "psolve_engine.cuh"
 #include "psolve_persist.cuh"
+#include "psolve_tune.cuh"
 
 using namespace psolve;
 
@@ -344,6 +345,8 @@ void fill_result(const Scal &s, const Problem &P, const Plan &plan, bool use_x0,
     r.iterations = s.iter;
     r.half_step_exit = s.half_exit;
     r.engine = P.desc.tma;
+    r.slab_planes = P.desc.zc;
+    r.tuned = P.tuned;
     r.rel_res_recursive = s.nb2 > 0 ? std::sqrt(s.rr / s.nb2) : 0.0;
     r.rel_res_true = !true_res ? -1.0 : (s.nb2 > 0 ? std::sqrt(s.true_rr / s.nb2) : 0.0);
     r.seconds = now_s() - t0;
@@ -396,6 +399,7 @@ struct psolve_ctx {
     PersistState *d_ps = nullptr, *h_ps = nullptr; // its barrier words and phase table (device, pinned)
     std::vector<cudaEvent_t> events;
     double *d_hb = nullptr, *d_hx = nullptr; // device copies for psolve_solve_host
+    bool tma_ok = true; // false: the autotuner chose the general engine
 };
 
 extern "C" {
@@ -509,6 +513,17 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
     } while (0)
     CREATE_CK(cudaMalloc(&P.mem, P.mem_bytes));
     problem_bind(P, P.mem);
+    if (o.autotune) {
+        TuneChoice tc;
+        st = tune_problem(P, c->di.sms, c->stream, &tc);
+        if (st != PSOLVE_OK) {
+            psolve_destroy(c);
+            return st;
+        }
+        problem_geometry(P, c->di.sms, tc.zc);
+        c->tma_ok = tc.engine == 1;
+        P.tuned = tc.from_cache ? 2 : 1;
+    }
     CREATE_CK(cudaMemset(P.d_sc, 0, sizeof(Scal)));
     CREATE_CK(cudaMalloc(&c->d_desc, sizeof(Desc)));
     CREATE_CK(cudaMalloc(&c->d_list, 4 * sizeof(int32_t)));
@@ -530,7 +545,7 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
 
 static psolve_status upload_desc(psolve_ctx *c)
 {
-    problem_encode_tmaps(c->P, c->h_tmap, c->opts.engine != 1);
+    problem_encode_tmaps(c->P, c->h_tmap, c->opts.engine != 1 && c->tma_ok);
     *c->h_desc = c->P.desc;
     if (c->P.desc.tma)
         PS_CK(cudaMemcpyAsync(c->d_tmap, c->h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM,
@@ -939,11 +954,23 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     BATCH_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     for (int k = 0; k < 2; ++k) BATCH_CK(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
     h_list[0] = count;
-    h_list[1] = (int32_t)total_units;
     int32_t ub = 0;
     for (int q = 0; q < count; ++q) {
         Problem &P = probs[q];
         problem_bind(P, mem + offs[q]);
+        bool tma_ok = true;
+        if (o.autotune) {
+            // per grid shape (cached), so a grid decomposes as it does alone
+            TuneChoice tc;
+            st = tune_problem(P, di.sms, s, &tc);
+            if (st != PSOLVE_OK) {
+                cleanup();
+                return st;
+            }
+            problem_geometry(P, di.sms, tc.zc);
+            tma_ok = tc.engine == 1;
+            P.tuned = tc.from_cache ? 2 : 1;
+        }
         P.desc.sc = d_sc + q;
         st = problem_set_cheb(P, precond, degree, o.lmin_scale, o.lmax_scale);
         if (st != PSOLVE_OK) {
@@ -958,12 +985,19 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         P.desc.vec[ROLE_X] = x[q];
         P.desc.vec[ROLE_RT] = (void *)rhs[q];
         P.desc.tmap = d_tmap + (size_t)TMAPS_PER_PROBLEM * q;
-        problem_encode_tmaps(P, h_tmap + (size_t)TMAPS_PER_PROBLEM * q, o.engine != 1);
+        problem_encode_tmaps(P, h_tmap + (size_t)TMAPS_PER_PROBLEM * q, o.engine != 1 && tma_ok);
         h_desc[q] = P.desc;
         h_list[2 + 2 * q] = q;
         h_list[3 + 2 * q] = ub;
+        if ((long long)ub + P.desc.units >= (1LL << 31)) {
+            set_error("batch too large");
+            cleanup();
+            return PSOLVE_E_ARG;
+        }
         ub += P.desc.units;
     }
+    total_units = ub;
+    h_list[1] = ub;
     BATCH_CK(cudaMemcpyAsync(d_tmap, h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * count,
                              cudaMemcpyHostToDevice, s));
     BATCH_CK(cudaMemcpyAsync(d_desc, h_desc, sizeof(Desc) * count, cudaMemcpyHostToDevice, s));

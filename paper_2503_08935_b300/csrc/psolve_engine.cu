@@ -256,6 +256,37 @@ void enqueue_precond(Launcher &L, const Plan &plan)
     }
 }
 
+// The autotuner's probe: one Chebyshev sweep (k >= 3 form), one stencil with
+// two dots and one update, with every role on workspace vectors and no skips.
+template <class T, bool BLK>
+static void tune_probe(Launcher &L)
+{
+    using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
+    KArgs s{};
+    s.k = 3;
+    s.in = ROLE_YA;
+    s.z = ROLE_YB;
+    s.b = is_mixed<T>() ? ROLE_BC : ROLE_PH;
+    s.out = ROLE_RH;
+    L.go<OpCiSweep<T, TB, BLK, false>>(PSOLVE_K_CI_SWEEP4, 0, s, 0.0);
+    KArgs t{};
+    t.in = ROLE_RH;
+    L.go<OpStencil2Dot<T>>(PSOLVE_K_STENCIL_2DOT, 0, t, 0.0);
+    KArgs u{};
+    u.in = ROLE_PH;
+    u.aux = ROLE_RH;
+    L.go<OpUpdate<T>>(PSOLVE_K_UPDATE, 0, u, 0.0);
+}
+
+void enqueue_tune_probe(Launcher &L, int prec, bool blk)
+{
+    switch (prec) {
+    case PSOLVE_FP32: blk ? tune_probe<float, true>(L) : tune_probe<float, false>(L); break;
+    case PSOLVE_BF16: blk ? tune_probe<__nv_bfloat16, true>(L) : tune_probe<__nv_bfloat16, false>(L); break;
+    default: blk ? tune_probe<double, true>(L) : tune_probe<double, false>(L); break;
+    }
+}
+
 bool launch_did_work(const LaunchRec &r, int final_iter, int half_exit)
 {
     if (r.side == 2) // replacement: counted on the multiples of rr_every before the exit iteration
@@ -279,7 +310,7 @@ double model_bytes_for(const std::vector<LaunchRec> &recs, int final_iter, int h
 // ------------------------------------------------------------- workspace --
 static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-void problem_geometry(Problem &P, int sms)
+void problem_geometry(Problem &P, int sms, int zc_choice)
 {
     Desc &D = P.desc;
     D.nx = (int)P.n[0];
@@ -295,6 +326,7 @@ void problem_geometry(Problem &P, int sms)
     const long long target = (long long)D.nz * tiles / (4LL * 4 * sms);
     long long zc = 1;
     while (zc * 2 <= target && zc < 32) zc *= 2;
+    if (zc_choice > 0) zc = zc_choice < D.nz ? zc_choice : D.nz; // a tuned slab depth
     D.zc = (int)zc;
     D.nzc = ceil_div(D.nz, D.zc);
     D.units = (int)(tiles * D.nzc);
@@ -312,15 +344,11 @@ void problem_geometry(Problem &P, int sms)
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-static int units_for(const int64_t n[3], int sms)
+// Units of the finest decomposition (one plane per unit): the partial-sum
+// buffer is sized for it, so any slab depth fits the same workspace.
+static long long units_max(const int64_t n[3])
 {
-    Problem tmp;
-    for (int d = 0; d < 3; ++d) {
-        tmp.n[d] = n[d];
-        tmp.h[d] = 1.0;
-    }
-    problem_geometry(tmp, sms);
-    return tmp.desc.units;
+    return (long long)((n[0] + TILE_X - 1) / TILE_X) * ((n[1] + TILE_Y - 1) / TILE_Y) * n[2];
 }
 
 size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms)
@@ -328,7 +356,8 @@ size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms)
     const size_t N = (size_t)(n[0] * n[1] * n[2]);
     const size_t v64 = align_up(N * 8), vci = align_up(N * ci_elem_bytes(prec));
     size_t b = v64 * (6 + (with_rt ? 1 : 0)) + vci * (4 + (prec != PSOLVE_FP64 ? 1 : 0));
-    b += align_up(sizeof(Scal)) + align_up((size_t)units_for(n, sms) * MAX_DOTS * sizeof(double));
+    (void)sms;
+    b += align_up(sizeof(Scal)) + align_up((size_t)units_max(n) * MAX_DOTS * sizeof(double));
     return b;
 }
 

@@ -100,6 +100,7 @@ struct Problem {
     int blocks[3] = {1, 1, 1};
     int prec = PSOLVE_FP64;
     bool have_rt = false;  // r~ buffer allocated (x0 != 0 support)
+    int tuned = 0;         // slab/engine from the autotuner: 1 measured, 2 cached, 0 rule
     Desc desc{};           // host copy (vec[] of b, x filled per solve)
     char *mem = nullptr;   // one device allocation for all workspace vectors
     size_t mem_bytes = 0;
@@ -110,8 +111,10 @@ struct Problem {
 
 // Bytes one problem's workspace needs (vectors + partials + scalars).
 size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms);
-// Fill the geometry fields of P.desc from P.n, P.h, P.blocks.
-void problem_geometry(Problem &P, int sms);
+// Fill the geometry fields of P.desc from P.n, P.h, P.blocks.  The slab depth
+// (planes per unit) is zc_choice when > 0 (a tuned value, at most nz), else
+// the built-in rule.
+void problem_geometry(Problem &P, int sms, int zc_choice = 0);
 // Lay out P's workspace inside `base` (device, problem_bytes long).
 void problem_bind(Problem &P, char *base);
 // Chebyshev interval [a, b] (Eq. 9-11 times the scales) for precond.
@@ -128,6 +131,9 @@ void enqueue_true_residual(Launcher &L);
 void enqueue_apply_A(Launcher &L, bool blocked);
 void enqueue_dot(Launcher &L);
 void enqueue_precond(Launcher &L, const Plan &plan);
+// The autotuner's probe kernels (a sweep, a stencil with two dots, an update)
+// for Chebyshev vectors of precision `prec`; needs every role bound.
+void enqueue_tune_probe(Launcher &L, int prec, bool blk);
 
 // Encode the tensor maps of every bound vector of P into maps[0..2*NROLES)
 // and set P.desc.tma (1 when the TMA engine can run this problem: nx % 8 == 0,

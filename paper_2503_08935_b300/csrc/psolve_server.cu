@@ -209,6 +209,7 @@ void finish(psolve_server *s, const Request &r, const Scal &sc, double t)
     res.iterations = sc.iter;
     res.half_step_exit = sc.half_exit;
     res.engine = r.prob.desc.tma;
+    res.slab_planes = r.prob.desc.zc;
     res.rel_res_recursive = sc.nb2 > 0 ? std::sqrt(sc.rr / sc.nb2) : 0.0;
     res.rel_res_true = sc.nb2 > 0 ? std::sqrt(sc.true_rr / sc.nb2) : 0.0;
     res.seconds = t - r.t_submit; // latency: submit -> result ready

@@ -46,16 +46,17 @@ def test_struct_layout_matches_c(tmp_path):
     src = tmp_path / "probe.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "psolve.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(psolve_opts), sizeof(psolve_result),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(psolve_opts), sizeof(psolve_result),"
         " offsetof(psolve_result, kernel_launches), offsetof(psolve_result, kclass_bytes),"
-        " offsetof(psolve_opts, engine)); return 0;}\n")
+        " offsetof(psolve_opts, engine), offsetof(psolve_opts, autotune), offsetof(psolve_result, tuned));"
+        " return 0;}\n")
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
-    so, sr, okl, okb, orr = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
-                                                    check=True).stdout.split())
+    so, sr, okl, okb, orr, oat, otu = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                                              check=True).stdout.split())
     assert so == ctypes.sizeof(B.Opts) and sr == ctypes.sizeof(B.Result)
     assert okl == B.Result.kernel_launches.offset and okb == B.Result.kclass_bytes.offset
-    assert orr == B.Opts.engine.offset
+    assert orr == B.Opts.engine.offset and oat == B.Opts.autotune.offset and otu == B.Result.tuned.offset
 
 
 def test_default_opts(L):
