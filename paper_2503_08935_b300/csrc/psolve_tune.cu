@@ -4,18 +4,19 @@
 // For every candidate (slab depth 1, 2, 4, 8, 16, 32 planes, at most nz;
 // TMA ring when the grid allows it, and the general engine) it times a probe
 // of the solve's kernel kinds on the problem's own workspace: one Chebyshev
-// sweep, one stencil with two dots and one update (one warm-up, then three
-// timed repetitions, CUDA events on the caller's stream), and keeps the
-// fastest.  The choice depends on the grid shape, the Chebyshev precision and
+// sweep, one stencil with two dots and one update (a timed warm-up sizes the
+// measurement to about 300 us of work, at least 3 repetitions; the best of two
+// trials, CUDA events on the caller's stream), and keeps the fastest.  The choice depends on the grid shape, the Chebyshev precision and
 // the GPU's SM count only, so a grid gets the same decomposition (hence the
 // same reduction order and bitwise the same result) alone, in a batch or in
 // a later process.
 //
 // Cache: every decision is kept for the life of the process and, when the
 // environment variable PSOLVE_TUNE_CACHE names a file, appended to it as one
-// text line "psolve-tune-1 sms nx ny nz prec zc engine us" and read back at
-// the first tuning request of a later process (the first line for a key
-// wins).  Lines that do not parse are ignored.
+// text line "psolve-tune-1 sms nx ny nz prec zc engine us" (preceded by one
+// "# candidate ..." comment line per measured candidate) and read back at the
+// first tuning request of a later process (the first line for a key wins).
+// Lines that do not parse are ignored.
 #include <cstdlib>
 #include <map>
 #include <mutex>
@@ -67,12 +68,20 @@ void load_locked()
     std::fclose(f);
 }
 
-void append_locked(const TuneKey &k, const TuneChoice &c)
+struct Candidate {
+    int zc, engine;
+    double us;
+};
+
+void append_locked(const TuneKey &k, const TuneChoice &c, const std::vector<Candidate> &all)
 {
     const char *path = cache_path();
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
+    for (const Candidate &m : all) // every measurement, as comments
+        std::fprintf(f, "# candidate %d %d %d %d %d %d %d %.3f\n", k.sms, k.nx, k.ny, k.nz, k.prec, m.zc, m.engine,
+                     m.us);
     std::fprintf(f, "psolve-tune-1 %d %d %d %d %d %d %d %.3f\n", k.sms, k.nx, k.ny, k.nz, k.prec, c.zc, c.engine,
                  c.us);
     std::fclose(f);
@@ -109,15 +118,29 @@ psolve_status time_candidate(Problem &P, int sms, int zc, bool tma, cudaStream_t
     L.units = D.units;
     L.d_desc = d_desc;
     L.d_list = d_list;
-    enqueue_tune_probe(L, P.prec, false); // warm-up
+    // warm-up, timed once to size the measurement: enough repetitions for
+    // about 300 us of work, and the best of two trials
     PS_CK(cudaEventRecord(ev[0], s));
-    for (int rep = 0; rep < 3; ++rep) enqueue_tune_probe(L, P.prec, false);
+    enqueue_tune_probe(L, P.prec, false);
     PS_CK(cudaEventRecord(ev[1], s));
     PS_CK(L.err);
     PS_CK(cudaEventSynchronize(ev[1]));
     float ms = 0.f;
     PS_CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-    *us = 1e3 * ms / 3.0;
+    int reps = ms > 0.f ? (int)(0.3f / ms) + 1 : 3;
+    reps = reps < 3 ? 3 : (reps > 64 ? 64 : reps);
+    double best = -1.0;
+    for (int trial = 0; trial < 2; ++trial) {
+        PS_CK(cudaEventRecord(ev[0], s));
+        for (int rep = 0; rep < reps; ++rep) enqueue_tune_probe(L, P.prec, false);
+        PS_CK(cudaEventRecord(ev[1], s));
+        PS_CK(L.err);
+        PS_CK(cudaEventSynchronize(ev[1]));
+        PS_CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        const double t = 1e3 * ms / reps;
+        if (best < 0.0 || t < best) best = t;
+    }
+    *us = best;
     return PSOLVE_OK;
 }
 
@@ -142,6 +165,7 @@ psolve_status tune_problem(const Problem &P0, int sms, cudaStream_t s, TuneChoic
     psolve_status st = PSOLVE_OK;
     TuneChoice best;
     best.us = -1.0;
+    std::vector<Candidate> all;
     auto ck = [&](cudaError_t e) {
         if (e != cudaSuccess && st == PSOLVE_OK) {
             set_error("autotuner: %s", cudaGetErrorString(e));
@@ -156,6 +180,7 @@ psolve_status tune_problem(const Problem &P0, int sms, cudaStream_t s, TuneChoic
             for (int zc = 1; zc <= 32 && zc <= P.n[2] && st == PSOLVE_OK; zc *= 2) {
                 double us = -1.0;
                 st = time_candidate(P, sms, zc, engine == 1, s, d_desc, d_list, d_tmap, h_tmap.data(), ev, &us);
+                if (st == PSOLVE_OK && us >= 0.0) all.push_back(Candidate{zc, engine, us});
                 if (st == PSOLVE_OK && us >= 0.0 && (best.us < 0.0 || us < best.us)) {
                     best.zc = zc;
                     best.engine = engine;
@@ -172,7 +197,7 @@ psolve_status tune_problem(const Problem &P0, int sms, cudaStream_t s, TuneChoic
     if (st != PSOLVE_OK) return st;
     best.from_cache = 0;
     g_cache.emplace(key, best);
-    append_locked(key, best);
+    append_locked(key, best, all);
     *out = best;
     return PSOLVE_OK;
 }

@@ -99,8 +99,13 @@ def test_tune_cache_file_is_written_and_obeyed(tmp_path):
     fresh = tmp_path / "fresh.txt"
     r = _child(fresh)
     assert r["status"] == B.OK and r["tuned"] == 1
-    line = fresh.read_text().split()
-    assert line[0] == "psolve-tune-1" and list(map(int, line[1:8])) == [sms, 40, 32, 24, 0, r["zc"], r["engine"]]
+    lines = fresh.read_text().splitlines()
+    decisions = [ln.split() for ln in lines if ln.startswith("psolve-tune-1")]
+    assert len(decisions) == 1 and list(map(int, decisions[0][1:8])) == [sms, 40, 32, 24, 0, r["zc"], r["engine"]]
+    # every measured candidate is recorded as a comment line before it
+    cands = [ln.split() for ln in lines if ln.startswith("# candidate")]
+    assert len(cands) >= 6 and all(list(map(int, c[2:7])) == [sms, 40, 32, 24, 0] for c in cands)
+    assert min(float(c[9]) for c in cands) == pytest.approx(float(decisions[0][8]), rel=1e-3)
     # a planted entry: the child takes it without measuring
     planted = tmp_path / "planted.txt"
     planted.write_text(f"garbage line\npsolve-tune-1 {sms} 40 32 24 0 2 0 1.0\npsolve-tune-1 {sms} 40 32 24 0 8 1 0.5\n")
