@@ -526,7 +526,7 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
     }
     CREATE_CK(cudaMemset(P.d_sc, 0, sizeof(Scal)));
     CREATE_CK(cudaMalloc(&c->d_desc, sizeof(Desc)));
-    CREATE_CK(cudaMalloc(&c->d_list, 4 * sizeof(int32_t)));
+    CREATE_CK(cudaMalloc(&c->d_list, (LIST_HDR_INTS + 2) * sizeof(int32_t)));
     CREATE_CK(cudaHostAlloc(&c->h_desc, sizeof(Desc), cudaHostAllocDefault));
     CREATE_CK(cudaHostAlloc(&c->h_sc, 3 * sizeof(Scal), cudaHostAllocDefault));
     CREATE_CK(cudaMalloc(&c->d_ps, sizeof(PersistState)));
@@ -534,7 +534,7 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
     CREATE_CK(cudaMalloc(&c->d_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM));
     CREATE_CK(cudaHostAlloc(&c->h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM, cudaHostAllocDefault));
     P.desc.tmap = c->d_tmap;
-    const int32_t list[4] = {1, P.desc.units, 0, 0};
+    const int32_t list[LIST_HDR_INTS + 2] = {1, P.desc.units, 0, 0, 0, 0};
     CREATE_CK(cudaMemcpy(c->d_list, list, sizeof list, cudaMemcpyHostToDevice));
     CREATE_CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     for (int s = 0; s < 2; ++s) CREATE_CK(cudaEventCreateWithFlags(&c->poll_ev[s], cudaEventDisableTiming));
@@ -907,7 +907,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     cudaEvent_t ev[2] = {nullptr, nullptr};
     std::vector<GraphEntry> graphs;
     std::vector<cudaEvent_t> events;
-    const size_t list_bytes = sizeof(int32_t) * (2 + 2 * (size_t)count);
+    const size_t list_bytes = sizeof(int32_t) * (LIST_HDR_INTS + 2 * (size_t)count);
     auto cleanup = [&]() {
         if (s) cudaStreamSynchronize(s);
         for (GraphEntry &g : graphs)
@@ -954,6 +954,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     BATCH_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     for (int k = 0; k < 2; ++k) BATCH_CK(cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming));
     h_list[0] = count;
+    h_list[2] = h_list[3] = 0; // the list's work counters start at zero
     int32_t ub = 0;
     for (int q = 0; q < count; ++q) {
         Problem &P = probs[q];
@@ -987,8 +988,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         P.desc.tmap = d_tmap + (size_t)TMAPS_PER_PROBLEM * q;
         problem_encode_tmaps(P, h_tmap + (size_t)TMAPS_PER_PROBLEM * q, o.engine != 1 && tma_ok);
         h_desc[q] = P.desc;
-        h_list[2 + 2 * q] = q;
-        h_list[3 + 2 * q] = ub;
+        h_list[LIST_HDR_INTS + 2 * q] = q;
+        h_list[LIST_HDR_INTS + 1 + 2 * q] = ub;
         if ((long long)ub + P.desc.units >= (1LL << 31)) {
             set_error("batch too large");
             cleanup();

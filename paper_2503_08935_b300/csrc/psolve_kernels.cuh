@@ -753,20 +753,30 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
 }
 
 // ------------------------------------------------------------------------
-// The generic kernel: walk this CTA's unit range over the launch list.
+// The generic kernel: take units from the launch list until it is exhausted.
 // ------------------------------------------------------------------------
 // Shared-memory state of a CTA, reused by every phase a CTA runs.
 struct EngineShared {
     double *sred;          // block-reduction scratch
     uint64_t *bars;        // TMA ring mbarriers (MAX_STAGES)
     int *s_last, *s_dead;
+    int *s_unit;           // the unit thread 0 took
     unsigned char *dyn;    // TMA ring / general-engine planes
     uint32_t seq;          // planes this CTA has staged so far (all threads agree)
 };
 
 constexpr int MAX_STAGES = 8;
 
-// One phase: this CTA's strided share of every unit of the launch list.
+// One phase.  Each CTA starts with the unit of its own index and then takes
+// units one at a time from the list's counter, so a unit goes to whichever
+// CTA is free first and no SM idles while another still holds a queue of
+// units; units are handed out in increasing order,
+// chunk-major within a problem, so the CTAs running at one time cover
+// neighbouring tiles at nearby z and the halo rows one CTA reads are still
+// in L2 when its neighbours read them.  A problem's dot products are summed
+// per unit, and the CTA that completes its last unit (atomic ticket) reduces
+// the per-unit partials in unit order, so results do not depend on which CTA
+// took which unit.
 template <class Op>
 __device__ __forceinline__ void engine_body(const KArgs &a, EngineShared &sh)
 {
@@ -774,88 +784,97 @@ __device__ __forceinline__ void engine_body(const KArgs &a, EngineShared &sh)
     C *sp = reinterpret_cast<C *>(sh.dyn);
 
     const ListHdr hdr = *reinterpret_cast<const ListHdr *>(a.list);
-    const int2 *ent = reinterpret_cast<const int2 *>(a.list + 2);
-    const long long total = hdr.total;
-    const long long G = gridDim.x;
-    // Strided assignment: this CTA takes units g, g + G, g + 2G, ... of the
-    // launch list.  With units numbered chunk-major, the CTAs running at the
-    // same time cover neighbouring tiles at nearby z, so halo rows read by one
-    // CTA are still in L2 when its neighbours read them.
-    long long u = blockIdx.x;
-    if (u >= total) return;
-
-    int lo = 0, hi = hdr.n - 1; // last entry whose first unit <= u
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (ent[mid].y <= u) lo = mid;
-        else hi = mid - 1;
-    }
-    for (int e = lo; e < hdr.n && u < total; ++e) {
+    const int2 *ent = reinterpret_cast<const int2 *>(a.list + LIST_HDR_INTS);
+    uint32_t *sched = reinterpret_cast<uint32_t *>(const_cast<int32_t *>(a.list)) + 2; // next, done
+    const int G = gridDim.x;
+    // the first unit of a CTA is its index; the rest come from the counter
+    // (never touched when the list has no more units than the launch has CTAs)
+    const bool dynamic = hdr.total > G;
+    int u = blockIdx.x;
+    int e = 0; // list entry of the last unit taken
+    while (u < hdr.total) {
+        if (e + 1 < hdr.n && ent[e + 1].y <= u) { // the last entry whose first unit <= u
+            int lo = e + 1, hi = hdr.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ent[mid].y <= u) lo = mid;
+                else hi = mid - 1;
+            }
+            e = lo;
+        }
         const int2 en = ent[e];
-        const long long pend = (e + 1 < hdr.n) ? ent[e + 1].y : total; // end of this problem's units
-        if (u >= pend) continue;
-        const int cnt = (int)((pend - 1 - u) / G + 1); // this CTA's units of the problem
-        const long long ufirst = u;
-        u += (long long)cnt * G;
         const Desc &D = a.descs[en.x];
-        const int units = D.units;
         Scal *sc = D.sc;
-        if ((a.skip & SKIP_STOP) && ld_flag(&sc->stop)) continue;
-        if ((a.skip & SKIP_HALF) && ld_flag(&sc->half)) continue;
-        if ((a.skip & SKIP_NOT_RR) && (D.rr_every <= 0 || ld_flag(&sc->iter) % D.rr_every != 0)) continue;
-
-        Op op(D, a, sc);
-        const int ntiles = D.tiles_x * D.tiles_y;
-        const bool use_tma = D.tma != 0;
-        for (int i = 0; i < cnt; ++i) {
-            const int l = (int)(ufirst + (long long)i * G - en.y); // problem-local unit, chunk-major
+        const bool skip = ((a.skip & SKIP_STOP) && ld_flag(&sc->stop)) ||
+                          ((a.skip & SKIP_HALF) && ld_flag(&sc->half)) ||
+                          ((a.skip & SKIP_NOT_RR) && (D.rr_every <= 0 || ld_flag(&sc->iter) % D.rr_every != 0));
+        if (!skip) {
+            Op op(D, a, sc);
+            const int ntiles = D.tiles_x * D.tiles_y;
+            const int l = u - en.y; // problem-local unit, chunk-major
             const int c0 = l / ntiles;
             const int tile = l - c0 * ntiles;
             if constexpr (Op::STENCIL) {
-                if (use_tma) march_tma<Op>(op, D, tile, c0, c0 + 1, sh.dyn, sh.bars, sh.seq, sh.sred, sh.s_dead);
+                if (D.tma) march_tma<Op>(op, D, tile, c0, c0 + 1, sh.dyn, sh.bars, sh.seq, sh.sred, sh.s_dead);
                 else march_stencil<Op>(op, D, tile, c0, c0 + 1, sp, sh.sred);
             } else {
                 march_point<Op>(op, D, tile, c0, c0 + 1, sh.sred);
             }
-        }
-        if constexpr (Op::ND > 0) {
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                const unsigned n = (unsigned)cnt;
-                const unsigned prev = atomicAdd(&sc->ticket, n);
-                *sh.s_last = (prev + n == (unsigned)units);
-            }
-            __syncthreads();
-            if (*sh.s_last) {
-                __threadfence();
-                double v[Op::ND];
-#pragma unroll
-                for (int q = 0; q < Op::ND; ++q) v[q] = 0.0;
-                for (int w = threadIdx.x; w < units; w += NTHREADS) {
-#pragma unroll
-                    for (int q = 0; q < Op::ND; ++q) v[q] += __ldcg(D.partials + w * MAX_DOTS + q);
-                }
-                block_sum<Op::ND>(v, sh.sred);
+            if constexpr (Op::ND > 0) {
+                const int units = D.units;
+                __syncthreads();
                 if (threadIdx.x == 0) {
-                    epilogue<Op::EPI, Op::ND>(D, sc, v);
-                    sc->ticket = 0;
                     __threadfence();
+                    const unsigned prev = atomicAdd(&sc->ticket, 1u);
+                    *sh.s_last = (prev + 1u == (unsigned)units);
                 }
+                __syncthreads();
+                if (*sh.s_last) {
+                    __threadfence();
+                    double v[Op::ND];
+#pragma unroll
+                    for (int q = 0; q < Op::ND; ++q) v[q] = 0.0;
+                    for (int w = threadIdx.x; w < units; w += NTHREADS) {
+#pragma unroll
+                        for (int q = 0; q < Op::ND; ++q) v[q] += __ldcg(D.partials + w * MAX_DOTS + q);
+                    }
+                    block_sum<Op::ND>(v, sh.sred);
+                    if (threadIdx.x == 0) {
+                        epilogue<Op::EPI, Op::ND>(D, sc, v);
+                        sc->ticket = 0;
+                        __threadfence();
+                    }
+                }
+                __syncthreads(); // s_last is reused by the next unit
             }
-            __syncthreads(); // s_last is reused by the next problem
+        }
+        if (!dynamic) break;
+        if (threadIdx.x == 0) *sh.s_unit = G + (int)atomicAdd(&sched[0], 1u);
+        __syncthreads();
+        u = *sh.s_unit;
+        __syncthreads(); // every thread has read s_unit before thread 0 takes the next unit
+    }
+    // The last CTA to finish resets the counters for the next launch on this
+    // list (no CTA of this launch touches them after its own last take).
+    if (dynamic && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&sched[1], 1u) == (unsigned)G - 1u) {
+            atomicExch(&sched[0], 0u);
+            atomicExch(&sched[1], 0u);
+            __threadfence();
         }
     }
 }
 
 // Initialise the CTA's shared state (mbarriers of the TMA ring).
 __device__ __forceinline__ void engine_setup(EngineShared &sh, double *sred, uint64_t *bars, int *s_last,
-                                             int *s_dead, unsigned char *dyn)
+                                             int *s_dead, int *s_unit, unsigned char *dyn)
 {
     sh.sred = sred;
     sh.bars = bars;
     sh.s_last = s_last;
     sh.s_dead = s_dead;
+    sh.s_unit = s_unit;
     sh.dyn = dyn;
     sh.seq = 0;
     if (threadIdx.x == 0) {
@@ -871,13 +890,12 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
 {
     __shared__ double sred[(NTHREADS / 32) * MAX_DOTS];
     __shared__ alignas(8) uint64_t bars[MAX_STAGES];
-    __shared__ int s_last, s_dead;
+    __shared__ int s_last, s_dead, s_unit;
     // the TMA ring, or the general engine's double-buffered plane: a CTA runs
     // one engine at a time, and each march starts with a barrier
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    if ((long long)blockIdx.x >= reinterpret_cast<const ListHdr *>(a.list)->total) return;
     EngineShared sh;
-    engine_setup(sh, sred, bars, &s_last, &s_dead, dyn_smem);
+    engine_setup(sh, sred, bars, &s_last, &s_dead, &s_unit, dyn_smem);
     engine_body<Op>(a, sh);
 }
 

@@ -39,7 +39,7 @@ constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // Scratch layout: [Desc][launch list][Scal][partials ...].
 constexpr size_t OFF_DESC = 0;
 constexpr size_t OFF_LIST = align256(sizeof(Desc));
-constexpr size_t OFF_SCAL = OFF_LIST + align256(4 * sizeof(int32_t));
+constexpr size_t OFF_SCAL = OFF_LIST + align256((LIST_HDR_INTS + 2) * sizeof(int32_t));
 constexpr size_t OFF_PART = OFF_SCAL + align256(sizeof(Scal));
 
 psolve_status scratch_for_device(int dev, unsigned char **out)
@@ -114,7 +114,7 @@ extern "C" PSOLVE_API psolve_status psolve_dot_noalloc(const int64_t grid[3], co
     D.partials = reinterpret_cast<double *>(base + OFF_PART);
     D.tma = 0;
     D.tmap = nullptr;
-    const int32_t list[4] = {1, D.units, 0, 0};
+    const int32_t list[LIST_HDR_INTS + 2] = {1, D.units, 0, 0, 0, 0};
     // host staging is pageable (stack) memory; the copies complete before the
     // calls return, so the stack buffers may go out of scope afterwards
     PS_CK(cudaMemcpyAsync(base + OFF_DESC, &D, sizeof(Desc), cudaMemcpyHostToDevice, s));

@@ -138,7 +138,7 @@ static __device__ bool list_all_stopped(const Desc *descs, const int32_t *list, 
     __syncthreads();
     if (threadIdx.x == 0) {
         const ListHdr hdr = *reinterpret_cast<const ListHdr *>(list);
-        const int2 *ent = reinterpret_cast<const int2 *>(list + 2);
+        const int2 *ent = reinterpret_cast<const int2 *>(list + LIST_HDR_INTS);
         int all = 1;
         for (int e = 0; e < hdr.n && all; ++e)
             if (!ld_flag(&descs[ent[e].x].sc->stop)) all = 0;
@@ -183,11 +183,11 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_persist(PersistArgs pa)
     using L = typename PersistOps<KIND, T, BLK, WY>::List;
     __shared__ double sred[(NTHREADS / 32) * MAX_DOTS];
     __shared__ alignas(8) uint64_t bars[MAX_STAGES];
-    __shared__ int s_last, s_dead, s_flag, s_all, s_kind;
+    __shared__ int s_last, s_dead, s_flag, s_all, s_kind, s_unit;
     __shared__ KArgs s_a;
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     EngineShared sh;
-    engine_setup(sh, sred, bars, &s_last, &s_dead, dyn_smem);
+    engine_setup(sh, sred, bars, &s_last, &s_dead, &s_unit, dyn_smem);
     uint32_t target = 0;
     bool ok = true;
     for (int i = 0; i < pa.n_init && ok; ++i)

@@ -144,19 +144,24 @@ struct psolve_server {
 
 namespace {
 
-// Lists are [n, total, (slot, first unit) x n]; capacity max_slots entries.
-int32_t *list_host(psolve_server *s, int which) { return s->h_lists + (size_t)which * (2 + 2 * s->max_slots); }
+// Lists are [n, total, next, done, (slot, first unit) x n]; capacity
+// max_slots entries.
+int32_t *list_host(psolve_server *s, int which)
+{
+    return s->h_lists + (size_t)which * (LIST_HDR_INTS + 2 * s->max_slots);
+}
 
-size_t list_bytes(int n) { return sizeof(int32_t) * (2 + 2 * (size_t)n); }
+size_t list_bytes(int n) { return sizeof(int32_t) * (LIST_HDR_INTS + 2 * (size_t)n); }
 
 cudaError_t upload_list(psolve_server *s, int which, const std::vector<int> &slots)
 {
     int32_t *h = list_host(s, which);
     h[0] = (int32_t)slots.size();
+    h[2] = h[3] = 0; // the list's work counters start at zero
     int32_t ub = 0;
     for (size_t q = 0; q < slots.size(); ++q) {
-        h[2 + 2 * q] = slots[q];
-        h[3 + 2 * q] = ub;
+        h[LIST_HDR_INTS + 2 * q] = slots[q];
+        h[LIST_HDR_INTS + 1 + 2 * q] = ub;
         ub += s->slots[slots[q]].req.prob.desc.units;
     }
     h[1] = ub;

@@ -109,7 +109,7 @@ psolve_status time_candidate(Problem &P, int sms, int zc, bool tma, cudaStream_t
     if (D.tma)
         PS_CK(cudaMemcpyAsync(d_tmap, h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM, cudaMemcpyHostToDevice, s));
     PS_CK(cudaMemcpyAsync(d_desc, &D, sizeof(Desc), cudaMemcpyHostToDevice, s));
-    const int32_t list[4] = {1, D.units, 0, 0};
+    const int32_t list[LIST_HDR_INTS + 2] = {1, D.units, 0, 0, 0, 0};
     PS_CK(cudaMemcpyAsync(d_list, list, sizeof list, cudaMemcpyHostToDevice, s));
     PS_CK(cudaMemsetAsync(P.d_sc, 0, sizeof(Scal), s));
     Launcher L;
@@ -173,7 +173,7 @@ psolve_status tune_problem(const Problem &P0, int sms, cudaStream_t s, TuneChoic
         }
         return st == PSOLVE_OK;
     };
-    if (ck(cudaMalloc(&d_desc, sizeof(Desc))) && ck(cudaMalloc(&d_list, 4 * sizeof(int32_t))) &&
+    if (ck(cudaMalloc(&d_desc, sizeof(Desc))) && ck(cudaMalloc(&d_list, (LIST_HDR_INTS + 2) * sizeof(int32_t))) &&
         ck(cudaMalloc(&d_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM)) && ck(cudaEventCreate(&ev[0])) &&
         ck(cudaEventCreate(&ev[1]))) {
         for (int engine = 1; engine >= 0 && st == PSOLVE_OK; --engine)

@@ -103,10 +103,17 @@ struct Desc {
 
 // Header of a device-side launch list: `n` entries of (problem, first unit)
 // follow it as int pairs; `total` is the sum of the listed problems' units.
+// `next` and `done` are the list's work counter and finished-CTA count: a
+// kernel's CTAs take units by incrementing `next`, and the last CTA to finish
+// sets both back to zero, so every launch on the list starts from zero (the
+// host writes them as zero).
 struct ListHdr {
     int32_t n;
     int32_t total;
+    uint32_t next;
+    uint32_t done;
 };
+constexpr int LIST_HDR_INTS = 4; // ints before the first (problem, first unit) entry
 
 // Arguments common to every kernel launch.
 struct KArgs {
