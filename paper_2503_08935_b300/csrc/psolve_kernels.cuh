@@ -610,6 +610,10 @@ __device__ __forceinline__ void stage_ptrs(unsigned char *stage, const void *(&h
 // Stencil march over chunks [c0, c1) of one tile, operands staged by TMA.
 // `seq` counts the planes this CTA has staged so far (all threads agree); plane
 // number n lives in stage n % STAGES and completes phase (n / STAGES) & 1.
+// The stages (and mbarrier parities) of planes k-1, k, k+1 are carried as
+// rolling indices, and each thread keeps the centre values of those three
+// planes in registers (a z-queue), so a point costs four in-plane neighbour
+// reads from shared memory plus one for the next plane's centre.
 template <class Op>
 __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c0, int c1,
                                           unsigned char *ring, uint64_t *bars, uint32_t &seq,
@@ -652,51 +656,74 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
     C *xring = reinterpret_cast<C *>(xbase);
     U *uring = reinterpret_cast<U *>(xbase + 3 * align128(R::HBOX * (int)sizeof(C))); // when U != C
 
-    auto stage_of = [&](int q) { return ring + ((seq0 + (q - q0)) % S) * R::STAGE; };
-    auto bar_of = [&](int q) { return bars + (seq0 + (q - q0)) % S; };
-    auto parity_of = [&](int q) { return (uint32_t)(((seq0 + (q - q0)) / S) & 1u); };
-    auto wait_plane = [&](int q) {
+    // rolling stage index and mbarrier parity of a plane, advanced plane by plane
+    struct Slot {
+        int st;
+        uint32_t par;
+        __device__ __forceinline__ void next()
+        {
+            if (++st == R::STAGES) {
+                st = 0;
+                par ^= 1u;
+            }
+        }
+    };
+    Slot sm{(int)(seq0 % S), (seq0 / S) & 1u}; // plane k-1 (starts at q0)
+    Slot sc = sm;
+    sc.next(); // plane k
+    Slot sn = sc;
+    sn.next(); // plane k+1
+    int xm = 0, xc = 1, xn = 2; // transformed-plane slots of k-1, k, k+1 (XFORM only)
+
+    auto stage = [&](int st) { return ring + st * R::STAGE; };
+    auto wait = [&](const Slot &sl) {
         if (*s_dead) return;
-        if (!mbar_wait(bar_of(q), parity_of(q))) {
+        if (!mbar_wait(bars + sl.st, sl.par)) {
             *s_dead = 1;
             D.sc->status = ST_TIMEOUT;
             D.sc->stop = 1;
         }
     };
-    // u of plane q at halo-box index x, from the staged arrays
-    auto u_at = [&](int q, int x) -> C {
-        if constexpr (Op::XFORM) {
-            return xring[((q - q0) % 3) * R::HBOX + x];
-        } else {
-            const void *h[NHA], *p[NPA];
-            stage_ptrs<Op>(stage_of(q), h, p);
-            return op.sv(op.load_s(h, x));
-        }
-    };
-    auto transform = [&](int q) {
+    auto transform = [&](int st, int slot) {
         if constexpr (Op::XFORM) {
             const void *h[NHA], *p[NPA];
-            stage_ptrs<Op>(stage_of(q), h, p);
-            const int slot = ((q - q0) % 3) * R::HBOX;
+            stage_ptrs<Op>(stage(st), h, p);
             for (int x = tid; x < R::HBOX; x += NTHREADS) {
                 const U v = op.load_s(h, x);
-                xring[slot + x] = op.sv(v);
-                if constexpr (R::UX) uring[slot + x] = v;
+                xring[slot * R::HBOX + x] = op.sv(v);
+                if constexpr (R::UX) uring[slot * R::HBOX + x] = v;
             }
+        }
+    };
+    // this thread's centre value of the plane in stage `st` / slot `slot`
+    auto centre = [&](int st, int slot) -> U {
+        if constexpr (!Op::XFORM) {
+            const void *h[NHA], *p[NPA];
+            stage_ptrs<Op>(stage(st), h, p);
+            return op.load_s(h, me);
+        } else if constexpr (R::UX) {
+            return uring[slot * R::HBOX + me];
+        } else {
+            return xring[slot * R::HBOX + me];
         }
     };
 
     __syncthreads(); // the previous run's readers of the ring are done
     if (tid == 0) {
+        Slot si = sm;
         for (int n = 0; n < S && n < nplanes; ++n) {
             const int q = q0 + n;
-            ring_issue<Op>(op, D, stage_of(q), bar_of(q), i0, j0, q, q >= kb && q < ke);
+            ring_issue<Op>(op, D, stage(si.st), bars + si.st, i0, j0, q, q >= kb && q < ke);
+            si.next();
         }
     }
-    wait_plane(q0);
-    wait_plane(kb);
-    transform(q0);
-    transform(kb);
+    wait(sm);
+    wait(sc);
+    transform(sm.st, xm);
+    transform(sc.st, xc);
+    if constexpr (Op::XFORM) __syncthreads();
+    U zdn = in ? centre(sm.st, xm) : U(0); // centre values of planes k-1 and k
+    U zc_ = in ? centre(sc.st, xc) : U(0);
 
     double acc[NDA];
 #pragma unroll
@@ -708,12 +735,24 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
     int cend = min(nz, (c0 + 1) * zc);
 
     for (int k = kb; k < ke; ++k) {
-        wait_plane(k + 1);
-        transform(k + 1);
+        wait(sn);
+        transform(sn.st, xn);
         if constexpr (Op::XFORM) __syncthreads();
-        if (in && !*s_dead) {
-            C w = u_at(k, me - 1), e = u_at(k, me + 1), so = u_at(k, me - W), no = u_at(k, me + W);
-            C dn = u_at(k - 1, me), un = u_at(k + 1, me);
+        const bool live = in && !*s_dead;
+        U zup = U(0);
+        if (live) {
+            zup = centre(sn.st, xn);
+            C w, e, so, no;
+            if constexpr (Op::XFORM) {
+                const C *xs = xring + xc * R::HBOX;
+                w = xs[me - 1], e = xs[me + 1], so = xs[me - W], no = xs[me + W];
+            } else {
+                const void *h[NHA], *p[NPA];
+                stage_ptrs<Op>(stage(sc.st), h, p);
+                w = op.sv(op.load_s(h, me - 1)), e = op.sv(op.load_s(h, me + 1));
+                so = op.sv(op.load_s(h, me - W)), no = op.sv(op.load_s(h, me + W));
+            }
+            C dn = op.sv(zdn), un = op.sv(zup);
             if constexpr (Op::BLOCKED) {
                 if (!okw) w = C(0);
                 if (!oke) e = C(0);
@@ -723,19 +762,25 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
                 if (kk == D.bz - 1) un = C(0);
             }
             const void *h[NHA], *p[NPA];
-            stage_ptrs<Op>(stage_of(k), h, p);
-            U uc;
-            if constexpr (!Op::XFORM) uc = op.load_s(h, me);
-            else if constexpr (R::UX) uc = uring[((k - q0) % 3) * R::HBOX + me];
-            else uc = xring[((k - q0) % 3) * R::HBOX + me];
+            stage_ptrs<Op>(stage(sc.st), h, p);
             const PW pw = op.pw_s(p, mp);
-            op.emit(col + k * plane, op.sv(uc), w + e, so + no, dn + un, uc, pw, acc);
+            op.emit(col + k * plane, op.sv(zc_), w + e, so + no, dn + un, zc_, pw, acc);
         }
-        __syncthreads(); // stage of plane k-1 (and its u plane) is free
+        __syncthreads(); // stage of plane k-1 (and its transformed plane) is free
         if (tid == 0 && k - 1 + S <= q1 && !*s_dead) {
             const int q = k - 1 + S;
-            ring_issue<Op>(op, D, stage_of(q), bar_of(q), i0, j0, q, q >= kb && q < ke);
+            ring_issue<Op>(op, D, stage(sm.st), bars + sm.st, i0, j0, q, q >= kb && q < ke);
         }
+        // rotate: plane k becomes k-1, k+1 becomes k
+        sm = sc;
+        sc = sn;
+        sn.next();
+        const int xt = xm;
+        xm = xc;
+        xc = xn;
+        xn = xt;
+        zdn = zc_;
+        zc_ = zup;
         if constexpr (Op::BLOCKED) {
             if (++kk == D.bz) kk = 0;
         }
@@ -747,8 +792,8 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
             }
         }
     }
-    // drain: planes issued but not consumed in this run (q1 is always waited
-    // above; planes beyond it are never issued), so nothing is left in flight.
+    // every issued plane was waited for (q1 in the last step; planes beyond q1
+    // are never issued), so nothing is left in flight
     seq = seq0 + nplanes;
 }
 
