@@ -545,6 +545,18 @@ def extra_serve(B, I, torch, stream, n_req, factors=(0.8,), budget=120e9, max_sl
                                      "mean_ms": float(lat.mean()),
                                      "all_ok": all(i.status == B.OK for i in infos),
                                      "max_true_residual": max(i.rel_res_true for i in infos)}
+    # the same requests solved one after another, each with its own context
+    # (create, solve, destroy: what a loop of plain solves does), same settings
+    ncal = min(200, n_req)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in range(ncal):
+        with B.Solver(tuple(bs[q].shape), cheb_prec=B.FP32, stream=stream) as s_:
+            s_.solve(bs[q], xs[q], rtol=1e-8, maxit=2000, precond=B.PC_CHEB, degree=8)
+    torch.cuda.synchronize()
+    seq = ncal / (time.perf_counter() - t0)
+    out["sequential_solves_per_s"] = seq
+    out["served_vs_sequential"] = out["calibrated_mu_solves_per_s"] / seq
     return out
 
 

@@ -262,6 +262,18 @@ PSOLVE_API psolve_status psolve_selfcheck_conversions(uint64_t seed, int64_t cou
  * paper (failure detection without a GPU fault). */
 PSOLVE_API psolve_status psolve_selfcheck_wait_timeout(int64_t limit_cycles, int32_t *status);
 
+/* Self-check of the persistent kernel's grid barrier: a cooperative launch of
+ * *ctas small CTAs meets once at the same bounded grid barrier the persistent
+ * solve uses, with a wait limit of limit_ns nanoseconds (1e3 .. 2e9), while
+ * CTA absent_cta never arrives (absent_cta < 0: every CTA arrives).  On
+ * return *passed CTAs got through, *gave_up CTAs timed out and *error_word
+ * is the barrier's error word (1 after a time-out).  Expected: absent_cta < 0
+ * gives passed = ctas, gave_up = 0, error_word = 0; absent_cta >= 0 gives
+ * passed = 0, gave_up = ctas - 1, error_word = 1, within about limit_ns.  No
+ * counterpart in the paper (failure detection without a GPU fault). */
+PSOLVE_API psolve_status psolve_selfcheck_grid_timeout(int64_t limit_ns, int32_t absent_cta, int32_t *ctas,
+                                                       int32_t *passed, int32_t *gave_up, int32_t *error_word);
+
 /* ---- many independent grids at once ----------------------------------- */
 
 /* Solve `count` independent problems of (possibly) different sizes together:

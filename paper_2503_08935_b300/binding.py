@@ -31,6 +31,7 @@ EXPORTS = [
     "psolve_apply_A", "psolve_precond_apply", "psolve_dot", "psolve_cheb_interval", "psolve_solve_batch",
     "psolve_server_create", "psolve_submit", "psolve_poll", "psolve_server_destroy", "psolve_last_error",
     "psolve_version", "psolve_dot_noalloc", "psolve_selfcheck_conversions", "psolve_selfcheck_wait_timeout",
+    "psolve_selfcheck_grid_timeout",
 ]
 
 
@@ -121,6 +122,9 @@ def lib():
         L.psolve_selfcheck_conversions.restype = ctypes.c_int32
         L.psolve_selfcheck_wait_timeout.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]
         L.psolve_selfcheck_wait_timeout.restype = ctypes.c_int32
+        I32P = ctypes.POINTER(ctypes.c_int32)
+        L.psolve_selfcheck_grid_timeout.argtypes = [ctypes.c_int64, ctypes.c_int32, I32P, I32P, I32P, I32P]
+        L.psolve_selfcheck_grid_timeout.restype = ctypes.c_int32
         L.psolve_dot_noalloc.argtypes = [I64P, P, P, ctypes.c_void_p, DP]
         L.psolve_dot_noalloc.restype = ctypes.c_int32
         L.psolve_last_error.restype = ctypes.c_char_p
@@ -339,6 +343,16 @@ def selfcheck_wait_timeout(limit_cycles=1 << 20) -> int:
     if st != OK:
         raise PsolveError(st, "psolve_selfcheck_wait_timeout")
     return st_out.value
+
+
+def selfcheck_grid_timeout(limit_ns=20_000_000, absent_cta=0) -> dict:
+    """One grid barrier of the persistent kernel with CTA `absent_cta` missing
+    (-1: none); returns the CTA counts and the barrier's error word."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    st = lib().psolve_selfcheck_grid_timeout(int(limit_ns), int(absent_cta), *[ctypes.byref(x) for x in v])
+    if st != OK:
+        raise PsolveError(st, "psolve_selfcheck_grid_timeout")
+    return dict(zip(("ctas", "passed", "gave_up", "error_word"), (x.value for x in v)))
 
 
 def dot_noalloc(a, b, stream=None) -> float:

@@ -55,7 +55,8 @@ __device__ __forceinline__ void fence_proxy_async_global()
 
 // All CTAs of the launch meet here.  Returns false when the launch is being
 // abandoned (this CTA or another gave up waiting).
-static __device__ bool grid_sync(GridSync *gs, uint32_t &target, int *s_flag)
+static __device__ bool grid_sync(GridSync *gs, uint32_t &target, int *s_flag,
+                                 unsigned long long limit_ns = GRID_WAIT_NS)
 {
     fence_proxy_async_global();
     __syncthreads();
@@ -71,7 +72,7 @@ static __device__ bool grid_sync(GridSync *gs, uint32_t &target, int *s_flag)
                 ok = 0;
                 break;
             }
-            if (globaltimer_ns() - t0 > GRID_WAIT_NS) {
+            if (globaltimer_ns() - t0 > limit_ns) {
                 atomicExch(&gs->err, 1);
                 ok = 0;
                 break;

@@ -1,7 +1,7 @@
 // psolve_selfcheck.cu -- psolve_selfcheck_conversions: compares the library's
 // integer-pipe conversions (f2d_exact, d2f_rn in psolve_kernels.cuh) bit for
 // bit with the GPU's own conversion instructions.
-#include "psolve_engine.cuh"
+#include "psolve_persist_kernel.cuh"
 
 using namespace psolve;
 
@@ -113,5 +113,73 @@ extern "C" PSOLVE_API psolve_status psolve_selfcheck_wait_timeout(int64_t limit_
         return PSOLVE_E_CUDA;
     }
     *status = h;
+    return PSOLVE_OK;
+}
+
+namespace {
+
+// Every CTA but `absent` meets at one grid barrier with a wait limit of
+// limit_ns; CTA `absent` (or none, when absent < 0) never arrives.
+__global__ void k_check_grid_timeout(GridSync *gs, int absent, unsigned long long limit_ns, int *passed,
+                                     int *gave_up)
+{
+    __shared__ int s_flag;
+    if ((int)blockIdx.x == absent) return;
+    uint32_t target = 0;
+    const bool ok = grid_sync(gs, target, &s_flag, limit_ns);
+    if (threadIdx.x == 0) atomicAdd(ok ? passed : gave_up, 1);
+}
+
+} // namespace
+
+extern "C" PSOLVE_API psolve_status psolve_selfcheck_grid_timeout(int64_t limit_ns, int32_t absent_cta,
+                                                                  int32_t *ctas, int32_t *passed,
+                                                                  int32_t *gave_up, int32_t *error_word)
+{
+    clear_error();
+    if (!ctas || !passed || !gave_up || !error_word || limit_ns < 1000 || limit_ns > 2000000000LL) {
+        set_error("bad argument");
+        return PSOLVE_E_ARG;
+    }
+    DevInfo di;
+    psolve_status st = device_info(&di);
+    if (st != PSOLVE_OK) return st;
+    const int grid = 2 * di.sms; // 2 small CTAs per SM: co-resident, and the launch is cooperative anyway
+    if (absent_cta >= grid) {
+        set_error("absent_cta %d outside the %d CTAs of the check", absent_cta, grid);
+        return PSOLVE_E_ARG;
+    }
+    GridSync *d_gs = nullptr;
+    int *d_cnt = nullptr;
+    PS_CK(cudaMalloc(&d_gs, sizeof(GridSync)));
+    cudaError_t e = cudaMalloc(&d_cnt, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d_gs, 0, sizeof(GridSync));
+    if (e == cudaSuccess) e = cudaMemset(d_cnt, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(32);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_check_grid_timeout, d_gs, (int)absent_cta, (unsigned long long)limit_ns,
+                               d_cnt, d_cnt + 1);
+    }
+    int h[2] = {0, 0};
+    GridSync g{};
+    if (e == cudaSuccess) e = cudaMemcpy(h, d_cnt, sizeof h, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&g, d_gs, sizeof g, cudaMemcpyDeviceToHost);
+    cudaFree(d_gs);
+    if (d_cnt) cudaFree(d_cnt);
+    if (e != cudaSuccess) {
+        set_error("grid barrier self-check: %s", cudaGetErrorString(e));
+        return PSOLVE_E_CUDA;
+    }
+    *ctas = grid;
+    *passed = h[0];
+    *gave_up = h[1];
+    *error_word = g.err;
     return PSOLVE_OK;
 }

@@ -150,3 +150,22 @@ def test_persistent_batch_mixed_stop_times():
         assert ip[q].status == ir[q].status and ip[q].iterations == ir[q].iterations
         assert np.array_equal(xp[q].cpu().numpy(), xr[q].cpu().numpy())
     assert ip[3].iterations == 0
+
+
+def test_grid_barrier_gives_up_when_a_cta_never_arrives():
+    """Failure detection without a GPU fault: one CTA of a cooperative launch
+    skips the persistent kernel's grid barrier; every other CTA gives up after
+    the (short) wait limit, raises the error word and returns."""
+    import time
+    ok = B.selfcheck_grid_timeout(limit_ns=20_000_000, absent_cta=-1)
+    assert ok["passed"] == ok["ctas"] and ok["gave_up"] == 0 and ok["error_word"] == 0
+    t0 = time.perf_counter()
+    bad = B.selfcheck_grid_timeout(limit_ns=20_000_000, absent_cta=0)
+    elapsed = time.perf_counter() - t0
+    assert bad["passed"] == 0 and bad["gave_up"] == bad["ctas"] - 1 and bad["error_word"] == 1
+    assert elapsed < 2.0
+    # the context is still usable afterwards
+    shape = (8, 8, 16)
+    b = torch.from_numpy(I.rhs_uniform(shape, seed=305)).to(DEV)
+    x, info = run(shape, b, B.PC_CHEB, 4, persistent=1)
+    assert info.status == B.OK
