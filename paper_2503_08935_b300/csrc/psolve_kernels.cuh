@@ -930,8 +930,20 @@ __device__ __forceinline__ void engine_setup(EngineShared &sh, double *sred, uin
     __syncthreads();
 }
 
+// Resident CTAs per SM a kernel is compiled for: 4 (64 registers a thread),
+// or the operation's MIN_BLOCKS when it fits in fewer registers without
+// spilling (more warps to hide the ring's latency).
+template <class Op, class = void>
+struct MinBlocks {
+    static constexpr int value = 4;
+};
 template <class Op>
-__global__ void __launch_bounds__(NTHREADS, 4) k_engine(KArgs a)
+struct MinBlocks<Op, std::void_t<decltype(Op::MIN_BLOCKS)>> {
+    static constexpr int value = Op::MIN_BLOCKS;
+};
+
+template <class Op>
+__global__ void __launch_bounds__(NTHREADS, MinBlocks<Op>::value) k_engine(KArgs a)
 {
     __shared__ double sred[(NTHREADS / 32) * MAX_DOTS];
     __shared__ alignas(8) uint64_t bars[MAX_STAGES];
@@ -1080,6 +1092,11 @@ struct OpCiSweep {
     static constexpr int ND = 0, EPI = EPI_NONE;
     static constexpr bool STENCIL = true, BLOCKED = BLK;
     static_assert(sizeof(TB) == sizeof(T), "CI right-hand side and iterates share one type");
+    // without block restriction the FP32/BF16 sweep fits 40 registers: 6 CTAs
+    // per SM hide more of the ring's latency (FP32 sweep 79 -> 71 us at 256^3);
+    // the FP64 sweep is bound by the FP64 pipe and measured slower at 5 (48
+    // registers), so it keeps 4
+    static constexpr int MIN_BLOCKS = (BLK || sizeof(T) == 8) ? 4 : 6;
     // staged form: halo box of y_{k-1}, plain boxes of b and y_{k-2}
     using TH = T;
     using TP = T;
