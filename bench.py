@@ -50,6 +50,21 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(ms, dist, device):
+    """The step time of the slowest rank (every rank gets it); ms itself on one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, ms_per_step):
+    """Whole-job solves/s: every rank solves one problem per step (replicas)."""
+    return world * 1e3 / ms_per_step
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -247,11 +262,7 @@ def run_gpu(args):
         infos = [fn() for _ in range(steps)]
         ev1.record(stream)
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
         return ms, infos
 
     def solve_dev():
@@ -276,7 +287,7 @@ def run_gpu(args):
     ms_e2e, infos_e2e = timed(solve_e2e, args.steps)
 
     per_step = ms / args.steps
-    value = world * 1e3 / per_step
+    value = aggregate_value(world, per_step)
     iters = infos[-1].iterations
     model_bytes = statistics.mean(i.model_bytes for i in infos)
     launches = sum(i.kernel_launches for i in infos)
@@ -337,7 +348,7 @@ def run_gpu(args):
         "model_bytes_per_solve": model_bytes,
         "rel_res_true": infos[-1].rel_res_true,
         "roofline": roof,
-        "e2e": {"value": world * 1e3 * args.steps / ms_e2e, "unit": "solves/s",
+        "e2e": {"value": aggregate_value(world, ms_e2e / args.steps), "unit": "solves/s",
                 "h2d_bytes_per_step": 8 * npts, "d2h_bytes_per_step": 8 * npts,
                 "ms_per_step": ms_e2e / args.steps},
         "gpu_launches": launches,
