@@ -40,6 +40,7 @@ class _PC(ctypes.Structure):
         ("blocks", ctypes.c_int32 * 3),
         ("lmin_scale", ctypes.c_double),
         ("lmax_scale", ctypes.c_double),
+        ("bc", ctypes.c_int32 * 6),
     ]
 
 
@@ -74,6 +75,11 @@ def lib():
         L.oracle_cheb_interval.argtypes = [I64, D, ctypes.c_int32, I32, ctypes.c_double,
                                            ctypes.c_double, D, D]
         L.oracle_precond_apply.argtypes = [I64, D, ctypes.POINTER(_PC), D, D]
+        L.oracle_apply_A_bc.argtypes = [I64, D, I32, I32, D, D]
+        L.oracle_eig_bounds_bc.argtypes = [I64, D, I32, D, D]
+        L.oracle_cheb_bc.argtypes = [I64, D, I32, I32, ctypes.c_double, ctypes.c_double, ctypes.c_int32, D, D]
+        L.oracle_cheb_interval_bc.argtypes = [I64, D, I32, ctypes.c_int32, I32, ctypes.c_double,
+                                              ctypes.c_double, D, D]
         L.oracle_bicgstab.argtypes = [I64, D, D, D, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                       ctypes.POINTER(_PC), ctypes.c_int32, ctypes.POINTER(_Res), D, D]
         L.oracle_bicgstab_rr.argtypes = [I64, D, D, D, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -102,6 +108,14 @@ def _blk(blocks):
     return (ctypes.c_int32 * 3)(*[int(v) for v in blocks])
 
 
+def _bc(bc):
+    """Face conditions x-, x+, y-, y+, z-, z+ (0 Dirichlet, 1 Neumann) or None."""
+    if bc is None:
+        return None
+    assert len(bc) == 6
+    return (ctypes.c_int32 * 6)(*[int(v) for v in bc])
+
+
 def _vec(a):
     a = np.ascontiguousarray(a, dtype=np.float64)
     assert a.ndim == 3
@@ -120,40 +134,58 @@ def dot(a, b) -> float:
     return lib().oracle_dot(a.size, _dp(a), _dp(b))
 
 
-def apply_A(u, h, blocks=None):
-    """out = A u (Eq. 6).  ``h`` = (hx, hy, hz); ``blocks`` = blocks per axis (x, y, z)."""
+def apply_A(u, h, blocks=None, bc=None):
+    """out = A u (Eq. 6).  ``h`` = (hx, hy, hz); ``blocks`` = blocks per axis (x, y, z);
+    ``bc`` = face conditions (x-, x+, y-, y+, z-, z+), 0 Dirichlet / 1 Neumann (Eq. 4 / Eq. 5)."""
     u = _vec(u)
     out = np.empty_like(u)
-    _check(lib().oracle_apply_A(_n(u.shape), _h(h), _blk(blocks), _dp(u), _dp(out)), "apply_A")
+    if bc is None:
+        st = lib().oracle_apply_A(_n(u.shape), _h(h), _blk(blocks), _dp(u), _dp(out))
+    else:
+        st = lib().oracle_apply_A_bc(_n(u.shape), _h(h), _bc(bc), _blk(blocks), _dp(u), _dp(out))
+    _check(st, "apply_A")
     return out
 
 
-def eig_bounds(n_xyz, h):
+def eig_bounds(n_xyz, h, bc=None):
     """(lambda_min, lambda_max) of the grid operator, Eq. 10 / Eq. 11."""
     lo, hi = ctypes.c_double(), ctypes.c_double()
     n = (ctypes.c_int64 * 3)(*[int(v) for v in n_xyz])
-    _check(lib().oracle_eig_bounds(n, _h(h), ctypes.byref(lo), ctypes.byref(hi)), "eig_bounds")
+    if bc is None:
+        st = lib().oracle_eig_bounds(n, _h(h), ctypes.byref(lo), ctypes.byref(hi))
+    else:
+        st = lib().oracle_eig_bounds_bc(n, _h(h), _bc(bc), ctypes.byref(lo), ctypes.byref(hi))
+    _check(st, "eig_bounds")
     return lo.value, hi.value
 
 
-def cheb_interval(shape, h, precond, blocks=(1, 1, 1), lmin_scale=1.0, lmax_scale=1.0):
+def cheb_interval(shape, h, precond, blocks=(1, 1, 1), lmin_scale=1.0, lmax_scale=1.0, bc=None):
     a, b = ctypes.c_double(), ctypes.c_double()
-    _check(lib().oracle_cheb_interval(_n(shape), _h(h), int(precond), _blk(blocks), float(lmin_scale),
-                                      float(lmax_scale), ctypes.byref(a), ctypes.byref(b)),
-           "cheb_interval")
+    if bc is None:
+        st = lib().oracle_cheb_interval(_n(shape), _h(h), int(precond), _blk(blocks), float(lmin_scale),
+                                        float(lmax_scale), ctypes.byref(a), ctypes.byref(b))
+    else:
+        st = lib().oracle_cheb_interval_bc(_n(shape), _h(h), _bc(bc), int(precond), _blk(blocks),
+                                           float(lmin_scale), float(lmax_scale), ctypes.byref(a), ctypes.byref(b))
+    _check(st, "cheb_interval")
     return a.value, b.value
 
 
-def cheb(rhs, h, a, b, degree, blocks=None):
+def cheb(rhs, h, a, b, degree, blocks=None, bc=None):
     """Algorithm 2 on [a, b] for ``degree`` iterations (x = z if 0, x = y if 1)."""
     rhs = _vec(rhs)
     x = np.empty_like(rhs)
-    _check(lib().oracle_cheb(_n(rhs.shape), _h(h), _blk(blocks), float(a), float(b), int(degree),
-                             _dp(rhs), _dp(x)), "cheb")
+    if bc is None:
+        st = lib().oracle_cheb(_n(rhs.shape), _h(h), _blk(blocks), float(a), float(b), int(degree),
+                               _dp(rhs), _dp(x))
+    else:
+        st = lib().oracle_cheb_bc(_n(rhs.shape), _h(h), _bc(bc), _blk(blocks), float(a), float(b), int(degree),
+                                  _dp(rhs), _dp(x))
+    _check(st, "cheb")
     return x
 
 
-def _pc(precond, degree, blocks, lmin_scale, lmax_scale):
+def _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc=None):
     pc = _PC()
     pc.type = int(precond)
     pc.degree = int(degree)
@@ -161,13 +193,15 @@ def _pc(precond, degree, blocks, lmin_scale, lmax_scale):
         pc.blocks[d] = int(blocks[d])
     pc.lmin_scale = float(lmin_scale)
     pc.lmax_scale = float(lmax_scale)
+    for f in range(6):
+        pc.bc[f] = int(bc[f]) if bc is not None else 0
     return pc
 
 
-def precond_apply(v, h, precond, degree, blocks=(1, 1, 1), lmin_scale=1.0, lmax_scale=1.0):
+def precond_apply(v, h, precond, degree, blocks=(1, 1, 1), lmin_scale=1.0, lmax_scale=1.0, bc=None):
     v = _vec(v)
     out = np.empty_like(v)
-    pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale)
+    pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc)
     _check(lib().oracle_precond_apply(_n(v.shape), _h(h), ctypes.byref(pc), _dp(v), _dp(out)),
            "precond_apply")
     return out
@@ -185,14 +219,15 @@ class Result:
 
 
 def bicgstab(b, h, rtol=1e-10, maxit=2000, precond=PC_NONE, degree=0, blocks=(1, 1, 1),
-             lmin_scale=1.0, lmax_scale=1.0, x0=None, half_step_check=True, rr_every=0):
+             lmin_scale=1.0, lmax_scale=1.0, x0=None, half_step_check=True, rr_every=0, bc=None):
     """Algorithm 1.  Returns (x, Result).  ``x0`` None means x0 = 0.
-    ``rr_every`` > 0 adds residual replacement (not part of the paper's method)."""
+    ``rr_every`` > 0 adds residual replacement (not part of the paper's method).
+    ``bc`` = face conditions of the operator (None: all zero Dirichlet)."""
     b = _vec(b)
     x = np.zeros_like(b) if x0 is None else _vec(x0).copy()
     hs = np.full(max(maxit, 1), np.nan)
     hr = np.full(max(maxit, 1), np.nan)
-    pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale)
+    pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc)
     r = _Res()
     if rr_every:
         lib().oracle_bicgstab_rr(_n(b.shape), _h(h), _dp(b), _dp(x), 1 if x0 is not None else 0, float(rtol),

@@ -10,11 +10,17 @@
  * Every routine is the textbook definition written out with plain loops in
  * the order the paper states it:
  *   - 7-point operator          : Eq. 3 (second-order difference) and Eq. 6
- *                                 (Kronecker sum of 1-D Dirichlet matrices D,
- *                                 Eq. 4); neighbours outside the grid are 0.
+ *                                 (Kronecker sum of 1-D matrices: Dirichlet D,
+ *                                 Eq. 4, where neighbours outside the grid are
+ *                                 0, or, on a face with a zero-flux Neumann
+ *                                 condition, N of Eq. 5, where the boundary
+ *                                 unknown's outside neighbour equals its
+ *                                 inside one).
  *   - Block restriction         : Eq. 12-14 (R_s A R_s^T, non-overlapping
  *                                 equal blocks; cross-block neighbours are 0).
- *   - Eigenvalue bounds         : Eq. 8-11 with the Dirichlet spectrum Eq. 9.
+ *   - Eigenvalue bounds         : Eq. 8-11 with the Dirichlet spectrum Eq. 9;
+ *                                 for N (Eq. 5) the closed form of its
+ *                                 spectrum (see mu_range_1d).
  *   - Chebyshev iteration       : Eq. 15 (theta, delta, sigma) and Algorithm 2.
  *   - Preconditioned Bi-CGSTAB  : Algorithm 1 (right-preconditioned form with
  *                                 the half-step exit), stopping on the
@@ -74,21 +80,48 @@ double oracle_dot(int64_t N, const double *a, const double *b)
 /* 7-point operator, Eq. 3 / Eq. 6.                                           */
 /* ------------------------------------------------------------------------ */
 
-/* Value of u at integer coordinates c (one of which may be out of range), or
- * 0 if c lies outside the grid (zero Dirichlet ghost, Eq. 4) or, when
- * bs != NULL, outside the block of size bs that contains `home`. */
-static double nb_value(const int64_t n[3], const int64_t *bs, const double *u,
-                       const int64_t home[3], const int64_t c[3])
+/* Value of u at integer coordinates c_in (one of which may be out of range).
+ * Outside the grid it is 0 (zero Dirichlet ghost, Eq. 4), except across a
+ * face with a zero-flux Neumann condition (bc[face] == 1, faces ordered x-,
+ * x+, y-, y+, z-, z+), where the outside neighbour of the boundary unknown
+ * equals its inside neighbour (matrix N, Eq. 5: its row reads
+ * 2 u_0 - 2 u_1).  When bs != NULL it is also 0 outside the block of size bs
+ * that contains `home` (Eq. 14). */
+static double nb_value(const int64_t n[3], const int64_t *bs, const int32_t *bc, const double *u,
+                       const int64_t home[3], const int64_t c_in[3])
 {
+    int64_t c[3] = {c_in[0], c_in[1], c_in[2]};
     for (int d = 0; d < 3; ++d) {
+        if (c[d] < 0 && bc && bc[2 * d] == 1) c[d] = home[d] + 1;
+        if (c[d] >= n[d] && bc && bc[2 * d + 1] == 1) c[d] = home[d] - 1;
         if (c[d] < 0 || c[d] >= n[d]) return 0.0;
         if (bs && (c[d] / bs[d]) != (home[d] / bs[d])) return 0.0;
     }
     return u[c[0] + n[0] * (c[1] + n[1] * c[2])];
 }
 
+/* Boundary conditions: NULL (all Dirichlet) or six codes 0 (Dirichlet) / 1
+ * (Neumann); a Neumann face needs at least 2 points (and 2 per block) on its
+ * axis. */
+static int check_bc(const int64_t n[3], const int64_t *bs, const int32_t *bc)
+{
+    if (!bc) return ORACLE_OK;
+    for (int f = 0; f < 6; ++f) {
+        if (bc[f] != 0 && bc[f] != 1) return ORACLE_E_ARG;
+        const int d = f / 2;
+        if (bc[f] == 1 && (n[d] < 2 || (bs && bs[d] < 2))) return ORACLE_E_ARG;
+    }
+    return ORACLE_OK;
+}
+
 int oracle_apply_A(const int64_t n[3], const double h[3], const int32_t blocks[3],
                    const double *u, double *out)
+{
+    return oracle_apply_A_bc(n, h, NULL, blocks, u, out);
+}
+
+int oracle_apply_A_bc(const int64_t n[3], const double h[3], const int32_t bc[6], const int32_t blocks[3],
+                      const double *u, double *out)
 {
     int64_t bs_store[3];
     const int64_t *bs = NULL;
@@ -101,6 +134,7 @@ int oracle_apply_A(const int64_t n[3], const double h[3], const int32_t blocks[3
         }
         bs = bs_store;
     }
+    if (check_bc(n, bs, bc)) return ORACLE_E_ARG;
     for (int64_t k = 0; k < n[2]; ++k)
         for (int64_t j = 0; j < n[1]; ++j)
             for (int64_t i = 0; i < n[0]; ++i) {
@@ -111,8 +145,8 @@ int oracle_apply_A(const int64_t n[3], const double h[3], const int32_t blocks[3
                     int64_t lo[3] = {i, j, k}, hi[3] = {i, j, k};
                     lo[d] -= 1;
                     hi[d] += 1;
-                    const double ul = nb_value(n, bs, u, home, lo);
-                    const double uh = nb_value(n, bs, u, home, hi);
+                    const double ul = nb_value(n, bs, bc, u, home, lo);
+                    const double uh = nb_value(n, bs, bc, u, home, hi);
                     /* (-u_{d-1} + 2 u_d - u_{d+1}) / h_d^2 , Eq. 3 */
                     acc += (-ul + 2.0 * uc - uh) / (h[d] * h[d]);
                 }
@@ -145,6 +179,49 @@ int oracle_eig_bounds(const int64_t n[3], const double h[3], double *lmin, doubl
     return ORACLE_OK;
 }
 
+/* Extreme eigenvalues of the 1-D operator of size m with face conditions fm
+ * (minus side) and fp (plus side), 0 = Dirichlet (D, Eq. 4), 1 = Neumann (N,
+ * Eq. 5).  D: Eq. 9.  One Neumann face: N is similar to a symmetric matrix
+ * with the eigenvectors cos((2i-1) pi j / (2m)), j counted from the Neumann
+ * end, so mu_i = 4 sin^2((2i-1) pi / (4m)), i = 1..m.  Neumann on both faces:
+ * eigenvectors cos(i pi j / (m-1)), mu_i = 4 sin^2(i pi / (2(m-1))),
+ * i = 0..m-1, so the range is [0, 4]. */
+static void mu_range_1d(int64_t m, int fm, int fp, double *mn, double *mx)
+{
+    const double pi = 3.14159265358979323846;
+    if (!fm && !fp) {
+        *mn = mu_dirichlet(1, m);
+        *mx = mu_dirichlet(m, m);
+    } else if (fm != fp) {
+        const double s1 = sin(pi / (4.0 * (double)m));
+        const double s2 = sin((2.0 * (double)m - 1.0) * pi / (4.0 * (double)m));
+        *mn = 4.0 * s1 * s1;
+        *mx = 4.0 * s2 * s2;
+    } else {
+        const double s2 = sin((double)(m - 1) * pi / (2.0 * (double)(m - 1)));
+        *mn = 0.0;
+        *mx = 4.0 * s2 * s2;
+    }
+}
+
+int oracle_eig_bounds_bc(const int64_t n[3], const double h[3], const int32_t bc[6], double *lmin,
+                         double *lmax)
+{
+    if (!bc) return oracle_eig_bounds(n, h, lmin, lmax);
+    if (check_bc(n, NULL, bc)) return ORACLE_E_ARG;
+    double lo = 0.0, hi = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] < 1 || !(h[d] > 0.0)) return ORACLE_E_ARG;
+        double mn, mx;
+        mu_range_1d(n[d], bc[2 * d], bc[2 * d + 1], &mn, &mx);
+        lo += mn / (h[d] * h[d]); /* Eq. 10 */
+        hi += mx / (h[d] * h[d]); /* Eq. 11 */
+    }
+    *lmin = lo;
+    *lmax = hi;
+    return ORACLE_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Chebyshev iteration, Eq. 15 and Algorithm 2.                               */
 /* The operator is the full grid operator (blocks == NULL) or its block-      */
@@ -152,6 +229,12 @@ int oracle_eig_bounds(const int64_t n[3], const double h[3], double *lmin, doubl
 /* ------------------------------------------------------------------------ */
 int oracle_cheb(const int64_t n[3], const double h[3], const int32_t blocks[3],
                 double a, double b, int32_t degree, const double *rhs, double *x)
+{
+    return oracle_cheb_bc(n, h, NULL, blocks, a, b, degree, rhs, x);
+}
+
+int oracle_cheb_bc(const int64_t n[3], const double h[3], const int32_t bc[6], const int32_t blocks[3],
+                   double a, double b, int32_t degree, const double *rhs, double *x)
 {
     if (degree < 0 || !(b > a) || !(a > 0.0)) return ORACLE_E_ARG;
     const int64_t N = n[0] * n[1] * n[2];
@@ -175,14 +258,14 @@ int oracle_cheb(const int64_t n[3], const double h[3], const int32_t blocks[3],
         memcpy(x, z, sizeof(double) * (size_t)N);
         goto done;
     }
-    st = oracle_apply_A(n, h, blocks, rhs, Av);
+    st = oracle_apply_A_bc(n, h, bc, blocks, rhs, Av);
     if (st) goto done;
     for (int64_t q = 0; q < N; ++q)
         y[q] = 2.0 * rho_cur / delta * (2.0 * rhs[q] - Av[q] / theta);
     for (int32_t it = 2; it <= degree; ++it) {
         rho_old = rho_cur;
         rho_cur = 1.0 / (2.0 * sigma - rho_old);
-        st = oracle_apply_A(n, h, blocks, y, Av);
+        st = oracle_apply_A_bc(n, h, bc, blocks, y, Av);
         if (st) goto done;
         for (int64_t q = 0; q < N; ++q)
             w[q] = rho_cur * (2.0 * sigma * y[q] + 2.0 / delta * (rhs[q] - Av[q]) - rho_old * z[q]);
@@ -206,6 +289,50 @@ int oracle_cheb_interval(const int64_t n[3], const double h[3], int32_t precond,
                          const int32_t blocks[3], double lmin_scale, double lmax_scale,
                          double *a, double *b)
 {
+    return oracle_cheb_interval_bc(n, h, NULL, precond, blocks, lmin_scale, lmax_scale, a, b);
+}
+
+/* With face conditions: G(CI) and GNoComm(CI) take the whole grid's bounds.
+ * BJ(CI) blocks differ in their outer faces (a block on a Neumann face has
+ * that face, the others have Dirichlet ghosts), so the interval covers every
+ * kind of block: per axis the smallest minimum and the largest maximum over
+ * the first, the interior and the last block. */
+int oracle_cheb_interval_bc(const int64_t n[3], const double h[3], const int32_t bc[6], int32_t precond,
+                            const int32_t blocks[3], double lmin_scale, double lmax_scale, double *a,
+                            double *b)
+{
+    if (bc && !(bc[0] == 0 && bc[1] == 0 && bc[2] == 0 && bc[3] == 0 && bc[4] == 0 && bc[5] == 0)) {
+        double lo = 0.0, hi = 0.0;
+        if (check_bc(n, NULL, bc)) return ORACLE_E_ARG;
+        for (int d = 0; d < 3; ++d) {
+            if (n[d] < 1 || !(h[d] > 0.0)) return ORACLE_E_ARG;
+            double mn, mx;
+            const int fm = bc[2 * d], fp = bc[2 * d + 1];
+            if (precond == ORACLE_PC_BJ_CHEB && blocks && blocks[d] > 1) {
+                if (n[d] % blocks[d]) return ORACLE_E_ARG;
+                const int64_t m = n[d] / blocks[d];
+                double mn2, mx2;
+                mu_range_1d(m, fm, 0, &mn, &mx);   /* first block */
+                mu_range_1d(m, 0, fp, &mn2, &mx2); /* last block */
+                if (mn2 < mn) mn = mn2;
+                if (mx2 > mx) mx = mx2;
+                if (blocks[d] > 2) {
+                    mu_range_1d(m, 0, 0, &mn2, &mx2); /* interior blocks */
+                    if (mn2 < mn) mn = mn2;
+                    if (mx2 > mx) mx = mx2;
+                }
+            } else {
+                if (precond == ORACLE_PC_BJ_CHEB && (!blocks || blocks[d] < 1)) return ORACLE_E_ARG;
+                mu_range_1d(n[d], fm, fp, &mn, &mx);
+            }
+            lo += mn / (h[d] * h[d]);
+            hi += mx / (h[d] * h[d]);
+        }
+        *a = lmin_scale * lo;
+        *b = lmax_scale * hi;
+        if (!(*b > *a) || !(*a > 0.0)) return ORACLE_E_ARG;
+        return ORACLE_OK;
+    }
     int64_t m[3] = {n[0], n[1], n[2]};
     if (precond == ORACLE_PC_BJ_CHEB) {
         for (int d = 0; d < 3; ++d) {
@@ -231,10 +358,11 @@ int oracle_precond_apply(const int64_t n[3], const double h[3], const oracle_pc 
         return ORACLE_OK;
     }
     double a, b;
-    int st = oracle_cheb_interval(n, h, pc->type, pc->blocks, pc->lmin_scale, pc->lmax_scale, &a, &b);
+    int st = oracle_cheb_interval_bc(n, h, pc->bc, pc->type, pc->blocks, pc->lmin_scale, pc->lmax_scale, &a,
+                                     &b);
     if (st) return st;
     const int32_t *blk = (pc->type == ORACLE_PC_CHEB) ? NULL : pc->blocks;
-    return oracle_cheb(n, h, blk, a, b, pc->degree, in, out);
+    return oracle_cheb_bc(n, h, pc->bc, blk, a, b, pc->degree, in, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -284,7 +412,7 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
     }
     /* r0 = b - A x0 */
     if (use_x0) {
-        st = oracle_apply_A(n, h, NULL, x, t);
+        st = oracle_apply_A_bc(n, h, pc->bc, NULL, x, t);
         if (st) goto out;
         for (int64_t q = 0; q < N; ++q) r[q] = bvec[q] - t[q];
     } else {
@@ -303,7 +431,7 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
         res->iterations = i;
         int e = oracle_precond_apply(n, h, pc, p, ph); /* M p^ = p */
         if (e) { st = e; break; }
-        e = oracle_apply_A(n, h, NULL, ph, w); /* w = A p^ */
+        e = oracle_apply_A_bc(n, h, pc->bc, NULL, ph, w); /* w = A p^ */
         if (e) { st = e; break; }
         const double sig1 = oracle_dot(N, rt, w);
         if (!finite(sig1)) { st = ORACLE_NONFINITE; break; }
@@ -322,7 +450,7 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
         }
         e = oracle_precond_apply(n, h, pc, s, rh); /* M r^ = s */
         if (e) { st = e; break; }
-        e = oracle_apply_A(n, h, NULL, rh, t); /* t = A r^ */
+        e = oracle_apply_A_bc(n, h, pc->bc, NULL, rh, t); /* t = A r^ */
         if (e) { st = e; break; }
         const double tt = oracle_dot(N, t, t);
         const double ts = oracle_dot(N, t, s);
@@ -344,7 +472,7 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
         double beta = (rho_new / rho) * (alpha / omega);
         if (rr_every > 0 && i % rr_every == 0 && i < maxit) {
             /* residual replacement (see above) */
-            e = oracle_apply_A(n, h, NULL, x, t);
+            e = oracle_apply_A_bc(n, h, pc->bc, NULL, x, t);
             if (e) { st = e; break; }
             for (int64_t q = 0; q < N; ++q) r[q] = bvec[q] - t[q];
             rnorm = sqrt(oracle_dot(N, r, r));
@@ -364,7 +492,7 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
 out:
     if (st != ORACLE_E_ARG && st != ORACLE_E_OOM && N > 0 && r && t) {
         /* true residual ||b - A x|| / ||b|| of the returned x */
-        if (oracle_apply_A(n, h, NULL, x, t) == ORACLE_OK) {
+        if (oracle_apply_A_bc(n, h, pc->bc, NULL, x, t) == ORACLE_OK) {
             for (int64_t q = 0; q < N; ++q) r[q] = bvec[q] - t[q];
             const double nbb = sqrt(oracle_dot(N, bvec, bvec));
             res->rel_res_true = nbb > 0.0 ? sqrt(oracle_dot(N, r, r)) / nbb : 0.0;

@@ -38,6 +38,9 @@ typedef struct {
     int32_t blocks[3];  /* number of equal blocks along x, y, z (BJ/GNoComm)  */
     double lmin_scale;  /* lower bound handed to CI = lmin_scale * lambda_min */
     double lmax_scale;  /* upper bound handed to CI = lmax_scale * lambda_max */
+    int32_t bc[6];      /* face conditions of the operator (A and M), x-, x+,
+                           y-, y+, z-, z+: 0 zero Dirichlet (D, Eq. 4), 1 zero-
+                           flux Neumann (N, Eq. 5)                           */
 } oracle_pc;
 
 typedef struct {
@@ -53,6 +56,16 @@ double oracle_dot(int64_t N, const double *a, const double *b);
 int oracle_apply_A(const int64_t n[3], const double h[3], const int32_t blocks[3],
                    const double *u, double *out);
 int oracle_eig_bounds(const int64_t n[3], const double h[3], double *lmin, double *lmax);
+/* The same with face conditions (NULL: all Dirichlet; see oracle_pc.bc). */
+int oracle_apply_A_bc(const int64_t n[3], const double h[3], const int32_t bc[6], const int32_t blocks[3],
+                      const double *u, double *out);
+int oracle_eig_bounds_bc(const int64_t n[3], const double h[3], const int32_t bc[6], double *lmin,
+                         double *lmax);
+int oracle_cheb_bc(const int64_t n[3], const double h[3], const int32_t bc[6], const int32_t blocks[3],
+                   double a, double b, int32_t degree, const double *rhs, double *x);
+int oracle_cheb_interval_bc(const int64_t n[3], const double h[3], const int32_t bc[6], int32_t precond,
+                            const int32_t blocks[3], double lmin_scale, double lmax_scale, double *a,
+                            double *b);
 int oracle_cheb(const int64_t n[3], const double h[3], const int32_t blocks[3],
                 double a, double b, int32_t degree, const double *rhs, double *x);
 int oracle_cheb_interval(const int64_t n[3], const double h[3], int32_t precond,

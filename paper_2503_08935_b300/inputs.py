@@ -45,6 +45,71 @@ def default_h(shape_zyx) -> tuple:
     return (1.0 / (nx + 1), 1.0 / (ny + 1), 1.0 / (nz + 1))
 
 
+# Face conditions, ordered x-, x+, y-, y+, z-, z+: 0 zero Dirichlet, 1 zero-flux
+# Neumann.  The experimental set-up's problem has Dirichlet faces at x-, y+, z+
+# and Neumann faces at x+, y-, z-.
+PAPER_BC = (0, 1, 1, 0, 1, 0)
+
+
+def axis_coords(n: int, h: float, lo: float, bc_minus: int) -> np.ndarray:
+    """Coordinates of the n unknowns along one axis whose domain starts at ``lo``:
+    with a Dirichlet minus face the boundary node ``lo`` is known and the first
+    unknown is ``lo + h``; with a Neumann minus face the boundary node is itself
+    the first unknown."""
+    return lo + (np.arange(n) + (0 if bc_minus == 1 else 1)) * h
+
+
+def default_h_bc(shape_zyx, bc) -> tuple:
+    """Unit-interval spacing per axis for face conditions ``bc``: 1/(n+1) with two
+    Dirichlet faces (both boundary nodes known), 1/n with one Neumann face, 1/(n-1)
+    with two (the boundary nodes are unknowns)."""
+    nz, ny, nx = shape_zyx
+    out = []
+    for d, n in enumerate((nx, ny, nz)):
+        k = bc[2 * d] + bc[2 * d + 1]
+        out.append(1.0 / (n + 1 - k))
+    return tuple(out)
+
+
+def rhs_manufactured_bc(shape_zyx, bc) -> np.ndarray:
+    """f = -Laplace(u) for u = prod_d g_d(x_d) on the unit cube, with g_d
+    meeting the face conditions of axis d: sin(pi x) (Dirichlet both), sin(pi x/2)
+    (Neumann at x = 1), cos(pi x/2) (Neumann at x = 0), cos(pi x) (Neumann both);
+    f = (k_x^2 + k_y^2 + k_z^2) u.  Returns (f, u) at the unknowns."""
+    nz, ny, nx = shape_zyx
+    h = default_h_bc(shape_zyx, bc)
+    gs, ks = [], []
+    for d, n in enumerate((nx, ny, nz)):
+        x = axis_coords(n, h[d], 0.0, bc[2 * d])
+        fm, fp = bc[2 * d], bc[2 * d + 1]
+        if not fm and not fp:
+            k, g = math.pi, np.sin(math.pi * x)
+        elif not fm:
+            k, g = math.pi / 2, np.sin(math.pi * x / 2)
+        elif not fp:
+            k, g = math.pi / 2, np.cos(math.pi * x / 2)
+        else:
+            k, g = math.pi, np.cos(math.pi * x)
+        gs.append(g)
+        ks.append(k)
+    u = gs[2][:, None, None] * gs[1][None, :, None] * gs[0][None, None, :]
+    return (ks[0] ** 2 + ks[1] ** 2 + ks[2] ** 2) * u, u
+
+
+def rhs_paper_problem(shape_zyx, h=(0.1, 0.1, 0.1), lo=(3.0, 2.5, 10.0), bc=PAPER_BC) -> np.ndarray:
+    """The experimental set-up's right-hand side sin x + cos y + 3 sin z - 2 y z + 2
+    on the box starting at ``lo`` (x in [3, 28.5], y in [2.5, 28], z in [10, 35.5] at
+    h = 0.1), sampled at the unknowns of face conditions ``bc`` and normalised to
+    unit 2-norm (the paper normalises the right-hand side)."""
+    nz, ny, nx = shape_zyx
+    x = axis_coords(nx, h[0], lo[0], bc[0])
+    y = axis_coords(ny, h[1], lo[1], bc[2])
+    z = axis_coords(nz, h[2], lo[2], bc[4])
+    f = (np.sin(x)[None, None, :] + np.cos(y)[None, :, None] + 3.0 * np.sin(z)[:, None, None]
+         - 2.0 * y[None, :, None] * z[:, None, None] + 2.0)
+    return f / np.linalg.norm(f)
+
+
 def rhs_uniform(shape_zyx, seed: int = 1) -> np.ndarray:
     """b ~ U[-1, 1) per point, linear index order (x fastest)."""
     n = int(np.prod(shape_zyx))

@@ -32,6 +32,13 @@ MUTANTS = {
     "bicg_alpha_uses_r_not_rtilde": ("const double sig1 = oracle_dot(N, rt, w);",
                                      "const double sig1 = oracle_dot(N, r, w);"),
     "dot2_drops_product_error": ("s = s + (q + r);", "s = s + q;"),
+    "neumann_minus_face_reflects_to_itself": ("if (c[d] < 0 && bc && bc[2 * d] == 1) c[d] = home[d] + 1;",
+                                              "if (c[d] < 0 && bc && bc[2 * d] == 1) c[d] = home[d];"),
+    "neumann_plus_face_ignored": ("if (c[d] >= n[d] && bc && bc[2 * d + 1] == 1) c[d] = home[d] - 1;", ""),
+    "mixed_spectrum_off_by_half": ("const double s1 = sin(pi / (4.0 * (double)m));",
+                                   "const double s1 = sin(pi / (2.0 * (double)m));"),
+    "bj_interval_skips_last_block": ("mu_range_1d(m, 0, fp, &mn2, &mx2); /* last block */",
+                                     "mu_range_1d(m, 0, 0, &mn2, &mx2); /* last block */"),
 }
 
 

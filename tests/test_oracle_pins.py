@@ -431,3 +431,138 @@ def test_residual_replacement_rejects_negative_period():
     b = I.rhs_uniform((4, 4, 4), seed=1)
     with pytest.raises(ValueError):
         O.bicgstab(b, I.default_h((4, 4, 4)), rr_every=-1)
+
+
+# ------------------------------------------------ Neumann faces (Eq. 5) --
+# Face conditions x-, x+, y-, y+, z-, z+: 0 Dirichlet (D, Eq. 4), 1 zero-flux
+# Neumann (N, Eq. 5: first row (2, -2) for a Neumann minus face, last row
+# (-2, 2) for a Neumann plus face).
+def N1(n, fm, fp):
+    M = D1(n)
+    if fm:
+        M[0, 1] = -2.0
+    if fp:
+        M[n - 1, n - 2] = -2.0
+    return M
+
+
+def axis_matrix(n, fm, fp, nblocks=1):
+    """1-D operator of one axis, block-diagonal over `nblocks` equal blocks: the
+    domain's faces keep their condition, faces between blocks are Dirichlet (Eq. 14)."""
+    m = n // nblocks
+    M = np.zeros((n, n))
+    for b in range(nblocks):
+        M[b * m:(b + 1) * m, b * m:(b + 1) * m] = N1(m, fm if b == 0 else 0, fp if b == nblocks - 1 else 0)
+    return M
+
+
+def dense_P_bc(shape, h, bc, blocks=(1, 1, 1)):
+    """Eq. 6 with each O_d the D or N matrix its faces call for."""
+    nz, ny, nx = shape
+    hx, hy, hz = h
+    Ox = axis_matrix(nx, bc[0], bc[1], blocks[0]) / hx ** 2
+    Oy = axis_matrix(ny, bc[2], bc[3], blocks[1]) / hy ** 2
+    Oz = axis_matrix(nz, bc[4], bc[5], blocks[2]) / hz ** 2
+    return (np.kron(np.eye(nz), np.kron(np.eye(ny), Ox)) + np.kron(np.eye(nz), np.kron(Oy, np.eye(nx)))
+            + np.kron(Oz, np.kron(np.eye(ny), np.eye(nx))))
+
+
+BCS = [I.PAPER_BC, (1, 0, 0, 1, 0, 1), (1, 1, 0, 0, 0, 1), (0, 0, 0, 1, 0, 0)]
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("blocks", [None, (2, 1, 2)])
+def test_neumann_stencil_equals_dense_kronecker(bc, blocks):
+    shape = (4, 6, 8)
+    h = (0.25, 0.2, 0.3)
+    u = I.rhs_uniform(shape, seed=81)
+    P = dense_P_bc(shape, h, bc, blocks if blocks else (1, 1, 1))
+    assert np.allclose(O.apply_A(u, h, blocks=blocks, bc=bc).ravel(), P @ u.ravel(), rtol=1e-13, atol=1e-12)
+
+
+@pytest.mark.parametrize("bc", BCS)
+def test_neumann_eig_bounds_match_dense_spectrum(bc):
+    shape = (5, 6, 7)
+    h = (0.3, 0.2, 0.25)
+    ev = np.linalg.eigvals(dense_P_bc(shape, h, bc))
+    assert np.max(np.abs(ev.imag)) < 1e-8  # N is similar to a symmetric matrix
+    lo, hi = O.eig_bounds((shape[2], shape[1], shape[0]), h, bc=bc)
+    assert lo == pytest.approx(ev.real.min(), rel=1e-10) and hi == pytest.approx(ev.real.max(), rel=1e-10)
+
+
+@pytest.mark.parametrize("bc", [I.PAPER_BC, (1, 1, 0, 0, 0, 1)])
+def test_neumann_bj_interval_covers_every_block(bc):
+    shape = (6, 6, 9)
+    h = (0.2, 0.25, 0.3)
+    blocks = (3, 2, 3)
+    ev = np.linalg.eigvals(dense_P_bc(shape, h, bc, blocks)).real
+    a, b = O.cheb_interval(shape, h, O.PC_BJ_CHEB, blocks=blocks, bc=bc)
+    assert a == pytest.approx(ev.min(), rel=1e-10) and b == pytest.approx(ev.max(), rel=1e-10)
+    # G(CI) / GNoComm(CI): the whole grid's bounds
+    ev_g = np.linalg.eigvals(dense_P_bc(shape, h, bc)).real
+    for pc in (O.PC_CHEB, O.PC_GNOCOMM_CHEB):
+        a, b = O.cheb_interval(shape, h, pc, blocks=blocks, bc=bc)
+        assert a == pytest.approx(ev_g.min(), rel=1e-10) and b == pytest.approx(ev_g.max(), rel=1e-10)
+
+
+@pytest.mark.parametrize("bc", BCS[:2])
+def test_neumann_chebyshev_matches_spectral_closed_form(bc):
+    """Algorithm 2 applies p_d(A) b with p_d the Chebyshev residual polynomial's
+    companion (x = (1 - T_{d+1}-shaped residual) / lambda); checked through the
+    eigen-decomposition of the (nonsymmetric, diagonalisable) dense operator."""
+    shape = (4, 5, 6)
+    h = (0.2, 0.3, 0.25)
+    P = dense_P_bc(shape, h, bc)
+    lam, V = np.linalg.eig(P)
+    lam, V = lam.real, V.real
+    a, b = O.cheb_interval(shape, h, O.PC_CHEB, bc=bc)
+    rhs = I.rhs_uniform(shape, seed=82)
+    for d in (1, 3, 6):
+        x = O.cheb(rhs, h, a, b, d, bc=bc).ravel()
+        theta, delta = (b + a) / 2, (b - a) / 2
+        t = (theta - lam) / delta
+        s = theta / delta
+        Tk = lambda k, z: np.cosh(k * np.arccosh(z)) if np.all(z >= 1) else np.cos(k * np.arccos(np.clip(z, -1, 1)))
+        res_poly = Tk(d + 1, t) / np.cosh((d + 1) * np.arccosh(s))  # residual polynomial on the spectrum
+        coef = np.linalg.solve(V, rhs.ravel())
+        expect = V @ ((1 - res_poly) / lam * coef)
+        assert rel(x, expect) <= 1e-9, d
+
+
+@pytest.mark.parametrize("bc", BCS[:3])
+@pytest.mark.parametrize("pc", [(O.PC_NONE, 0, (1, 1, 1)), (O.PC_CHEB, 4, (1, 1, 1)),
+                                (O.PC_BJ_CHEB, 3, (2, 1, 2)), (O.PC_GNOCOMM_CHEB, 3, (2, 1, 2))])
+def test_neumann_bicgstab_matches_dense_solve(bc, pc):
+    shape = (4, 6, 8)
+    h = (0.25, 0.2, 0.3)
+    P = dense_P_bc(shape, h, bc)
+    b = I.rhs_uniform(shape, seed=83)
+    x, res = O.bicgstab(b, h, rtol=1e-12, maxit=2000, precond=pc[0], degree=pc[1], blocks=pc[2], bc=bc)
+    assert res.status == O.OK
+    assert rel(x, np.linalg.solve(P, b.ravel())) <= 10 * np.linalg.cond(P) * 1e-12
+    assert res.rel_res_true <= 1e-11
+
+
+def test_neumann_manufactured_second_order_convergence():
+    """u = sin(pi x/2) cos(pi y/2) cos(pi z/2) meets the set-up's face conditions
+    (Dirichlet at x = 0, y = 1, z = 1; Neumann at x = 1, y = 0, z = 0); the
+    discrete solution converges to it at second order."""
+    errs = []
+    for n in (8, 16, 32):
+        shape = (n, n, n)
+        f, u = I.rhs_manufactured_bc(shape, I.PAPER_BC)
+        h = I.default_h_bc(shape, I.PAPER_BC)
+        x, res = O.bicgstab(f, h, rtol=1e-12, maxit=4000, precond=O.PC_CHEB, degree=6, bc=I.PAPER_BC)
+        assert res.status == O.OK
+        errs.append(np.max(np.abs(x - u)))
+    assert 3.3 < errs[0] / errs[1] < 4.7 and 3.3 < errs[1] / errs[2] < 4.7, errs
+
+
+def test_neumann_rejects_bad_faces():
+    u = I.rhs_uniform((4, 4, 4), seed=1)
+    with pytest.raises(ValueError):
+        O.apply_A(u, (0.1, 0.1, 0.1), bc=(2, 0, 0, 0, 0, 0))
+    with pytest.raises(ValueError):  # a Neumann face needs two points per block on its axis
+        O.apply_A(u, (0.1, 0.1, 0.1), blocks=(4, 1, 1), bc=(1, 0, 0, 0, 0, 0))
+    with pytest.raises(ValueError):  # Neumann on every face: singular, no Chebyshev interval
+        O.cheb_interval((4, 4, 4), (0.1, 0.1, 0.1), O.PC_CHEB, bc=(1, 1, 1, 1, 1, 1))
