@@ -597,9 +597,39 @@ def extra_512_mixed(B, I, torch, stream):
     return res
 
 
+def extra_paper_problem(B, I, torch, stream):
+    """The experimental set-up's own problem: Dirichlet faces x-, y+, z+ and
+    zero-flux Neumann faces x+, y-, z- (Eq. 5), f = sin x + cos y + 3 sin z - 2yz + 2
+    (normalised) on its box at h = 0.1 (256^3) or h = 0.4 (64^3), rtol 1e-10,
+    24 Chebyshev iterations, the paper's bound rescaling for G(CI) and GNoComm(CI).
+    One GPU and no subdivision of the domain across devices; the paper's iteration
+    counts (Table 2: 64 MI250X GCDs, 4x4x4 subdomains; single device: 14) are
+    context for the iteration counts, not for the times."""
+    out = {}
+    scaled = dict(lmin_scale=100.0, lmax_scale=1 - 1e-4)
+    cases = [("256_g_ci24_scaled", (256,) * 3, 0.1, B.PC_CHEB, 24, (1, 1, 1), scaled, "50+-2"),
+             ("256_gnocomm_ci24_scaled_4x4x4", (256,) * 3, 0.1, B.PC_GNOCOMM_CHEB, 24, (4, 4, 4), scaled, "140+-12"),
+             ("256_bj_ci24_4x4x4", (256,) * 3, 0.1, B.PC_BJ_CHEB, 24, (4, 4, 4), {}, "172+-20"),
+             ("256_none", (256,) * 3, 0.1, B.PC_NONE, 0, (1, 1, 1), {}, "1543+-245"),
+             ("64_gnocomm_ci24_x10", (64,) * 3, 0.4, B.PC_GNOCOMM_CHEB, 24, (1, 1, 1),
+              dict(lmin_scale=10.0, lmax_scale=1 - 1e-4), "14 (single device)")]
+    for name, shape, hv, pc, deg, blocks, kw, paper in cases:
+        h = (hv, hv, hv)
+        b = torch.from_numpy(I.rhs_paper_problem(shape, h=h)).cuda()
+        x = torch.zeros_like(b)
+        with B.Solver(shape, h, bc=I.PAPER_BC, blocks=blocks, stream=stream, **kw) as s:
+            s.solve(b, x, rtol=1e-10, maxit=5000, precond=pc, degree=deg)  # warm-up
+            ms, info = _timed_cuda(lambda: s.solve(b, x, rtol=1e-10, maxit=5000, precond=pc, degree=deg), stream,
+                                   torch, 1)
+        out[name] = {"status": info.status_name, "iterations": info.iterations, "time_ms": ms,
+                     "rel_res_true": info.rel_res_true, "paper_iterations": paper}
+    return out
+
+
 def run_extras(args, B, I, torch, stream):
     out = {"config1_32cubed": extra_small_latency(B, I, torch, stream),
-           "config4_batch64": extra_batch(B, I, torch, stream)}
+           "config4_batch64": extra_batch(B, I, torch, stream),
+           "paper_problem": extra_paper_problem(B, I, torch, stream)}
     if args.extras == "full":
         out["config3_512_mixed"] = extra_512_mixed(B, I, torch, stream)
         out["config5_serving"] = extra_serve(B, I, torch, stream, 2000, factors=(0.8, 1.2))

@@ -167,14 +167,21 @@ typedef struct {
 typedef struct psolve_ctx psolve_ctx;
 
 /* Create a solver for one grid.
- *   grid[3] = (nx, ny, nz) interior points, each >= 1, product < 2^31.
+ *   grid[3] = (nx, ny, nz) unknowns per axis, each >= 1, product < 2^31.
  *   h[3]    = (hx, hy, hz) > 0.
- *   bc[6]   = boundary type of the faces x-, x+, y-, y+, z-, z+; only 0 (zero
- *             Dirichlet, Eq. 4) is implemented; NULL means all Dirichlet.
+ *   bc[6]   = condition on the faces x-, x+, y-, y+, z-, z+: 0 zero Dirichlet
+ *             (the boundary node is known and 0; matrix D, Eq. 4), 1 zero-flux
+ *             Neumann (the boundary node is the first / last unknown and its
+ *             outside neighbour equals its inside one; matrix N, Eq. 5).  A
+ *             Neumann face needs at least 2 unknowns on its axis (and 2 per
+ *             block for BJ/GNoComm); at least one face must be Dirichlet.
+ *             NULL means all Dirichlet.  The Chebyshev bounds use the closed
+ *             form of each axis's spectrum (D: Eq. 9; N with one Neumann face:
+ *             4 sin^2((2i-1) pi / (4n)); Neumann on both faces: [0, 4]).
  *   opts    = NULL for psolve_opts_default().
  *   stream  = cudaStream_t (as uintptr_t) that orders all work.
  * Allocates the device workspace (at most 12 grid vectors) once; returns
- * PSOLVE_E_ARG for bad sizes, blocks < 1 or a Neumann face, PSOLVE_E_OOM if
+ * PSOLVE_E_ARG for bad sizes, blocks < 1 or bad face conditions, PSOLVE_E_OOM if
  * it does not fit.  *out is set only on success. */
 PSOLVE_API psolve_status psolve_create(const int64_t grid[3], const double h[3], const int32_t bc[6],
                             const psolve_opts *opts, uintptr_t stream, psolve_ctx **out);

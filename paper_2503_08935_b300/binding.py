@@ -208,7 +208,9 @@ def _info(r: Result) -> SolveInfo:
 class Solver:
     """One grid (shape (nz, ny, nx)) with its device workspace (psolve_create)."""
 
-    def __init__(self, shape_zyx, h=None, opts: Opts | None = None, stream=None, **opt_kw):
+    def __init__(self, shape_zyx, h=None, opts: Opts | None = None, stream=None, bc=None, **opt_kw):
+        """``bc``: face conditions (x-, x+, y-, y+, z-, z+), 0 zero Dirichlet, 1 zero-flux
+        Neumann; None = all Dirichlet."""
         nz, ny, nx = shape_zyx
         self.shape = (nz, ny, nx)
         if h is None:
@@ -219,7 +221,8 @@ class Solver:
         grid = (ctypes.c_int64 * 3)(nx, ny, nz)
         hh = (ctypes.c_double * 3)(*self.h)
         ctx = ctypes.c_void_p()
-        st = lib().psolve_create(grid, hh, None, ctypes.byref(self.opts), self._stream, ctypes.byref(ctx))
+        bcs = (ctypes.c_int32 * 6)(*[int(v) for v in bc]) if bc is not None else None
+        st = lib().psolve_create(grid, hh, bcs, ctypes.byref(self.opts), self._stream, ctypes.byref(ctx))
         if st != OK:
             raise PsolveError(st, "psolve_create")
         self.ctx = ctx

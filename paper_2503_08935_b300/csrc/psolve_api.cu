@@ -328,11 +328,16 @@ psolve_status check_solve_args(double rtol, int maxit, int precond, int degree)
 psolve_status check_blocks(const Problem &P, int precond)
 {
     if (precond != PSOLVE_PC_BJ_CHEB && precond != PSOLVE_PC_GNOCOMM_CHEB) return PSOLVE_OK;
-    for (int d = 0; d < 3; ++d)
+    for (int d = 0; d < 3; ++d) {
         if (P.n[d] % P.blocks[d] != 0) {
             set_error("blocks[%d] = %d does not divide the grid size %lld", d, P.blocks[d], (long long)P.n[d]);
             return PSOLVE_E_ARG;
         }
+        if ((P.bc[2 * d] || P.bc[2 * d + 1]) && P.n[d] / P.blocks[d] < 2) {
+            set_error("axis %d has a Neumann face: its blocks need at least 2 unknowns", d);
+            return PSOLVE_E_ARG;
+        }
+    }
     return PSOLVE_OK;
 }
 
@@ -466,12 +471,24 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
         set_error("grid spacing must be finite and > 0");
         return PSOLVE_E_ARG;
     }
-    if (bc)
-        for (int f = 0; f < 6; ++f)
-            if (bc[f] != 0) {
-                set_error("face %d: only zero Dirichlet boundaries (0) are implemented", f);
+    if (bc) {
+        int dirichlet = 0;
+        for (int f = 0; f < 6; ++f) {
+            if (bc[f] != 0 && bc[f] != 1) {
+                set_error("face %d: condition %d is neither 0 (Dirichlet) nor 1 (Neumann)", f, bc[f]);
                 return PSOLVE_E_ARG;
             }
+            if (bc[f] == 1 && grid[f / 2] < 2) {
+                set_error("face %d: a Neumann face needs at least 2 unknowns on its axis", f);
+                return PSOLVE_E_ARG;
+            }
+            dirichlet += bc[f] == 0;
+        }
+        if (!dirichlet) {
+            set_error("every face is Neumann: the operator is singular");
+            return PSOLVE_E_ARG;
+        }
+    }
     psolve_opts o;
     psolve_opts_default(&o);
     if (opts) o = *opts;
@@ -498,6 +515,8 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
         P.h[d] = h[d];
         P.blocks[d] = o.blocks[d];
     }
+    if (bc)
+        for (int f = 0; f < 6; ++f) P.bc[f] = bc[f];
     P.prec = o.cheb_prec;
     P.have_rt = o.use_x0 != 0;
     problem_geometry(P, c->di.sms);
@@ -616,6 +635,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : P.prec;
     R.plan.exact_bounds = c->opts.lmin_scale == 1.0 && c->opts.lmax_scale == 1.0;
     R.plan.rr_every = c->opts.rr_every;
+    R.plan.neumann = P.desc.bcm != 0;
     R.use_graph = c->opts.use_graph != 0;
     R.timing = c->opts.timing != 0;
     R.npts = (double)P.npts();
@@ -812,6 +832,7 @@ psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, 
     plan.degree = degree;
     plan.prec = P.prec;
     plan.exact_bounds = c->opts.lmin_scale == 1.0 && c->opts.lmax_scale == 1.0;
+    plan.neumann = P.desc.bcm != 0;
     Launcher L = ctx_launcher(c);
     enqueue_precond(L, plan);
     PS_CK(L.err);

@@ -3,6 +3,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 namespace psolve {
 
 static thread_local std::string g_error;
@@ -163,10 +165,10 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
 
 // --------------------------------------------------- per-iteration kernels --
 template <class T, bool BLK>
-static void iteration_cheb(Launcher &L, int d, bool eb, bool rr)
+static void iteration_cheb(Launcher &L, int d, bool eb, bool rr, bool neu)
 {
-    if (eb) prog_iteration_cheb<T, BLK, false>(L, d, L.iter, rr);
-    else prog_iteration_cheb<T, BLK, true>(L, d, L.iter, rr);
+    if (eb) prog_iteration_cheb<T, BLK, false>(L, d, L.iter, rr, neu);
+    else prog_iteration_cheb<T, BLK, true>(L, d, L.iter, rr, neu);
 }
 
 void enqueue_iteration(Launcher &L, const Plan &plan)
@@ -180,16 +182,16 @@ void enqueue_iteration(Launcher &L, const Plan &plan)
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
     switch (plan.prec) {
     case PSOLVE_FP32:
-        if (blk) iteration_cheb<float, true>(L, plan.degree, plan.exact_bounds, rr);
-        else iteration_cheb<float, false>(L, plan.degree, plan.exact_bounds, rr);
+        if (blk) iteration_cheb<float, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
+        else iteration_cheb<float, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
         break;
     case PSOLVE_BF16:
-        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, rr);
-        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, rr);
+        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
+        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
         break;
     default:
-        if (blk) iteration_cheb<double, true>(L, plan.degree, plan.exact_bounds, rr);
-        else iteration_cheb<double, false>(L, plan.degree, plan.exact_bounds, rr);
+        if (blk) iteration_cheb<double, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
+        else iteration_cheb<double, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
         break;
     }
 }
@@ -220,7 +222,7 @@ void enqueue_dot(Launcher &L)
 // reads v through ROLE_R (the caller points ROLE_R at v and sets first = 1,
 // iter = 0), then the sweeps, then a widening copy of p^ into ROLE_V.
 template <class T, bool BLK>
-static void precond_cheb(Launcher &L, int d, bool eb)
+static void precond_cheb(Launcher &L, int d, bool eb, bool neu)
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
@@ -229,8 +231,8 @@ static void precond_cheb(Launcher &L, int d, bool eb)
     a.in = ROLE_PCUR;
     a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
     L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
-    if (eb) prog_sweeps<T, TB, BLK, false>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0);
-    else prog_sweeps<T, TB, BLK, true>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0);
+    if (eb) prog_sweeps<T, TB, BLK, false>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu);
+    else prog_sweeps<T, TB, BLK, true>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu);
     KArgs w{};
     w.in = ROLE_PH;
     w.out = ROLE_V;
@@ -242,16 +244,16 @@ void enqueue_precond(Launcher &L, const Plan &plan)
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
     switch (plan.prec) {
     case PSOLVE_FP32:
-        if (blk) precond_cheb<float, true>(L, plan.degree, plan.exact_bounds);
-        else precond_cheb<float, false>(L, plan.degree, plan.exact_bounds);
+        if (blk) precond_cheb<float, true>(L, plan.degree, plan.exact_bounds, plan.neumann);
+        else precond_cheb<float, false>(L, plan.degree, plan.exact_bounds, plan.neumann);
         break;
     case PSOLVE_BF16:
-        if (blk) precond_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds);
-        else precond_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds);
+        if (blk) precond_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, plan.neumann);
+        else precond_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, plan.neumann);
         break;
     default:
-        if (blk) precond_cheb<double, true>(L, plan.degree, plan.exact_bounds);
-        else precond_cheb<double, false>(L, plan.degree, plan.exact_bounds);
+        if (blk) precond_cheb<double, true>(L, plan.degree, plan.exact_bounds, plan.neumann);
+        else precond_cheb<double, false>(L, plan.degree, plan.exact_bounds, plan.neumann);
         break;
     }
 }
@@ -268,7 +270,7 @@ static void tune_probe(Launcher &L)
     s.z = ROLE_YB;
     s.b = is_mixed<T>() ? ROLE_BC : ROLE_PH;
     s.out = ROLE_RH;
-    L.go<OpCiSweep<T, TB, BLK, false>>(PSOLVE_K_CI_SWEEP4, 0, s, 0.0);
+    L.go<OpCiSweep<T, TB, BLK, false, false>>(PSOLVE_K_CI_SWEEP4, 0, s, 0.0);
     KArgs t{};
     t.in = ROLE_RH;
     L.go<OpStencil2Dot<T>>(PSOLVE_K_STENCIL_2DOT, 0, t, 0.0);
@@ -348,6 +350,9 @@ void problem_geometry(Problem &P, int sms, int zc_choice)
     if (D.bx < 1) D.bx = 1;
     if (D.by < 1) D.by = 1;
     if (D.bz < 1) D.bz = 1;
+    D.bcm = 0;
+    for (int f = 0; f < 6; ++f)
+        if (P.bc[f]) D.bcm |= 1 << f;
     D.cx = 1.0 / (P.h[0] * P.h[0]);
     D.cy = 1.0 / (P.h[1] * P.h[1]);
     D.cz = 1.0 / (P.h[2] * P.h[2]);
@@ -411,17 +416,58 @@ static double mu_dirichlet(long long i, long long n)
     return 4.0 * s * s; // Eq. 9
 }
 
+// Extreme eigenvalues of the 1-D operator of m unknowns with face conditions
+// fm (minus), fp (plus): Dirichlet on both (D, Eq. 9); one zero-flux Neumann
+// face (N, Eq. 5), whose eigenvectors are cosines of (2i-1) pi j / (2m) from
+// the Neumann end, so mu_i = 4 sin^2((2i-1) pi / (4m)); Neumann on both faces,
+// mu_i = 4 sin^2(i pi / (2(m-1))), i = 0..m-1.  In every case min + max = 4,
+// so with exact bounds theta = cc still holds.
+static void mu_range(long long m, int fm, int fp, double *mn, double *mx)
+{
+    if (!fm && !fp) {
+        *mn = mu_dirichlet(1, m);
+        *mx = mu_dirichlet(m, m);
+    } else if (fm != fp) {
+        const double s1 = std::sin(M_PI / (4.0 * (double)m));
+        const double s2 = std::sin((2.0 * (double)m - 1.0) * M_PI / (4.0 * (double)m));
+        *mn = 4.0 * s1 * s1;
+        *mx = 4.0 * s2 * s2;
+    } else {
+        *mn = 0.0;
+        *mx = 4.0;
+    }
+}
+
 psolve_status cheb_interval(const Problem &P, int precond, double lmin_scale, double lmax_scale,
                             double *a, double *b)
 {
-    // Eq. 10 / Eq. 11 over the whole grid (G, GNoComm) or one block (BJ)
+    // Eq. 10 / Eq. 11 over the whole grid (G, GNoComm) or the blocks (BJ).  BJ
+    // blocks differ in their outer faces (a block on a Neumann face keeps it,
+    // faces between blocks are Dirichlet ghosts), so the interval takes per
+    // axis the smallest minimum and the largest maximum over the first, the
+    // interior and the last block.
     double lo = 0.0, hi = 0.0;
     for (int d = 0; d < 3; ++d) {
-        long long m = P.n[d];
-        if (precond == PSOLVE_PC_BJ_CHEB) m = P.n[d] / P.blocks[d];
+        const int fm = P.bc[2 * d], fp = P.bc[2 * d + 1];
+        double mn, mx;
+        if (precond == PSOLVE_PC_BJ_CHEB && P.blocks[d] > 1) {
+            const long long m = P.n[d] / P.blocks[d];
+            double mn2, mx2;
+            mu_range(m, fm, 0, &mn, &mx);
+            mu_range(m, 0, fp, &mn2, &mx2);
+            mn = std::min(mn, mn2);
+            mx = std::max(mx, mx2);
+            if (P.blocks[d] > 2) {
+                mu_range(m, 0, 0, &mn2, &mx2);
+                mn = std::min(mn, mn2);
+                mx = std::max(mx, mx2);
+            }
+        } else {
+            mu_range(P.n[d], fm, fp, &mn, &mx);
+        }
         const double ih2 = 1.0 / (P.h[d] * P.h[d]);
-        lo += mu_dirichlet(1, m) * ih2;
-        hi += mu_dirichlet(m, m) * ih2;
+        lo += mn * ih2;
+        hi += mx * ih2;
     }
     *a = lmin_scale * lo;
     *b = lmax_scale * hi;

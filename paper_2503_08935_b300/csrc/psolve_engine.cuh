@@ -46,10 +46,11 @@ struct Plan {
     int prec = PSOLVE_FP64;
     bool exact_bounds = false; // scales (1, 1): the sweeps' y coefficient is zero
     int rr_every = 0;          // residual replacement period (0: none)
+    bool neumann = false;      // the grid has zero-flux Neumann faces
     bool operator==(const Plan &o) const
     {
         return precond == o.precond && degree == o.degree && prec == o.prec && exact_bounds == o.exact_bounds &&
-               rr_every == o.rr_every;
+               rr_every == o.rr_every && neumann == o.neumann;
     }
 };
 
@@ -98,6 +99,7 @@ struct Problem {
     int64_t n[3] = {0, 0, 0};
     double h[3] = {0, 0, 0};
     int blocks[3] = {1, 1, 1};
+    int bc[6] = {0, 0, 0, 0, 0, 0}; // face conditions x-, x+, y-, y+, z-, z+ (0 Dirichlet, 1 Neumann)
     int prec = PSOLVE_FP64;
     bool have_rt = false;  // r~ buffer allocated (x0 != 0 support)
     int tuned = 0;         // slab/engine from the autotuner: 1 measured, 2 cached, 0 rule

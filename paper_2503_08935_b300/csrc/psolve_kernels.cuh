@@ -336,6 +336,46 @@ __device__ __forceinline__ void flush_unit(double (&acc)[ND], double *sred, doub
     for (int j = 0; j < ND; ++j) acc[j] = 0.0;
 }
 
+// Zero-flux Neumann faces (matrix N, Eq. 5): the outside neighbour of a
+// boundary unknown equals its inside neighbour, so the pair sum across that
+// face is twice the inside value.  neumann_mask() gives, once per march, the
+// faces this thread's column touches (bits 0-3: x-, x+, y-, y+; bits 4-5: z-,
+// z+, which apply on the first / last plane); apply_neumann() runs after the
+// zero ghosts of the block restriction, which never remove the inside
+// neighbour (a Neumann face needs two unknowns per block on its axis).
+// Whether an operation handles Neumann faces (all do, except sweeps compiled
+// for grids without them).
+template <class Op, class = void>
+struct HasNeumann {
+    static constexpr bool value = true;
+};
+template <class Op>
+struct HasNeumann<Op, std::void_t<decltype(Op::NEUMANN)>> {
+    static constexpr bool value = Op::NEUMANN;
+};
+
+__device__ __forceinline__ int neumann_mask(int bcm, int i, int j, int nx, int ny)
+{
+    int m = bcm & 48;
+    if (i == 0) m |= bcm & 1;
+    if (i == nx - 1) m |= bcm & 2;
+    if (j == 0) m |= bcm & 4;
+    if (j == ny - 1) m |= bcm & 8;
+    return m;
+}
+
+template <class C>
+__device__ __forceinline__ void apply_neumann(int m, bool first_plane, bool last_plane, C &w, C &e, C &so, C &no,
+                                              C &dn, C &un)
+{
+    if (m & 1) w = e;
+    if (m & 2) e = w;
+    if (m & 4) so = no;
+    if (m & 8) no = so;
+    if ((m & 16) && first_plane) dn = un;
+    if ((m & 32) && last_plane) un = dn;
+}
+
 // ------------------------------------------------------------------------
 // Stencil march over chunks [c0, c1) of one tile.
 // Op provides: types C (arithmetic), U (own-column value), PW (pointwise
@@ -390,6 +430,7 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
         oks = (j % D.by) != 0;
         okn = (j % D.by) != D.by - 1;
     }
+    const int nbm = (HasNeumann<Op>::value && D.bcm) ? neumann_mask(D.bcm, i, j, nx, ny) : 0;
     const int kb = c0 * zc;
     const int ke = min(nz, c1 * zc);
 
@@ -430,6 +471,7 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
                 if (kk == 0) dn = C(0);
                 if (kk == D.bz - 1) un = C(0);
             }
+            if (nbm) apply_neumann(nbm, k == 0, k == nz - 1, w, e, so, no, dn, un);
             op.emit(col + k * plane, op.sv(uc), w + e, so + no, dn + un, uc, pw, acc);
         }
         C *sn = sp + (buf ^ 1) * SPL;
@@ -647,6 +689,7 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
         oks = (j % D.by) != 0;
         okn = (j % D.by) != D.by - 1;
     }
+    const int nbm = (HasNeumann<Op>::value && D.bcm) ? neumann_mask(D.bcm, i, j, nx, ny) : 0;
     const int kb = c0 * zc;
     const int ke = min(nz, c1 * zc);
     const int q0 = kb - 1, q1 = ke; // stencil-input planes q0..q1, pointwise planes kb..ke-1
@@ -761,6 +804,7 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
                 if (kk == 0) dn = C(0);
                 if (kk == D.bz - 1) un = C(0);
             }
+            if (nbm) apply_neumann(nbm, k == 0, k == nz - 1, w, e, so, no, dn, un);
             const void *h[NHA], *p[NPA];
             stage_ptrs<Op>(stage(sc.st), h, p);
             const PW pw = op.pw_s(p, mp);
@@ -1082,7 +1126,7 @@ struct OpCiFirst {
 //   w = rho_k (2 sigma y + (2/delta)(b - A y) - rho_{k-1} z),
 // y = y_{k-1} (stencil input), z = y_{k-2} (z = b/theta when k = 2).
 // TB is the storage type of the CI right-hand side b.
-template <class T, class TB, bool BLK, bool WITH_Y = true>
+template <class T, class TB, bool BLK, bool WITH_Y = true, bool NEU = true>
 struct OpCiSweep {
     using E = Elem<T>;
     using EB = Elem<TB>;
@@ -1097,6 +1141,9 @@ struct OpCiSweep {
     // the FP64 sweep is bound by the FP64 pipe and measured slower at 5 (48
     // registers), so it keeps 4
     static constexpr int MIN_BLOCKS = (BLK || sizeof(T) == 8) ? 4 : 6;
+    // NEU = false: the grid has no Neumann face, and the sweep is compiled
+    // without the face handling (the FP64 sweep is at its register budget)
+    static constexpr bool NEUMANN = NEU;
     // staged form: halo box of y_{k-1}, plain boxes of b and y_{k-2}
     using TH = T;
     using TP = T;

@@ -104,6 +104,18 @@ struct IndexOf<Op, TypeList<H, R...>> {
     static constexpr int value = 1 + IndexOf<Op, TypeList<R...>>::value;
 };
 
+// The persistent kernels carry one sweep kind, the one with Neumann-face
+// handling (with no Neumann face it computes exactly what the sweep compiled
+// without it computes); phases recorded with the latter run as the former.
+template <class Op>
+struct PersistAlias {
+    using type = Op;
+};
+template <class T, class TB, bool BLK, bool WY>
+struct PersistAlias<OpCiSweep<T, TB, BLK, WY, false>> {
+    using type = OpCiSweep<T, TB, BLK, WY, true>;
+};
+
 template <int KIND, class T, bool BLK, bool WY>
 struct PersistOps { // Chebyshev-preconditioned iteration
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
@@ -225,7 +237,7 @@ struct TableBuilder {
     void go(int, int, KArgs a, double, double = 0.0, int = 0)
     {
         if (n >= MAX_PHASES) return; // cannot happen: degree <= MAX_DEGREE
-        out[n].kind = IndexOf<Op, L>::value;
+        out[n].kind = IndexOf<typename PersistAlias<Op>::type, L>::value;
         out[n].pad_ = 0;
         out[n].a = a;
         ++n;
@@ -240,7 +252,7 @@ void table_of(const Plan &plan, bool use_x0, bool true_res, PersistState *st)
     prog_init(tb, use_x0);
     st->n_init = tb.n;
     if constexpr (KIND == 0) prog_iteration_none(tb, 2, plan.rr_every > 0);
-    else prog_iteration_cheb<T, BLK, WY>(tb, plan.degree, 2, plan.rr_every > 0);
+    else prog_iteration_cheb<T, BLK, WY>(tb, plan.degree, 2, plan.rr_every > 0, true); // one sweep kind for every grid
     st->n_iter = tb.n - st->n_init;
     if (true_res) prog_true_residual(tb);
     st->n_tail = tb.n - st->n_init - st->n_iter;
@@ -259,7 +271,7 @@ PersistKernel kernel_of()
     prog_init(m, false);
     prog_init(m, true);
     if constexpr (KIND == 0) prog_iteration_none(m, 1, true);
-    else prog_iteration_cheb<T, BLK, WY>(m, 3, 1, true);
+    else prog_iteration_cheb<T, BLK, WY>(m, 3, 1, true, true);
     prog_true_residual(m);
     return PersistKernel{k_persist<KIND, T, BLK, WY>, m.bytes, table_of<KIND, T, BLK, WY>};
 }

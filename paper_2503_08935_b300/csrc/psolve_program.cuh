@@ -36,9 +36,10 @@ __host__ __device__ void prog_replace(V &v)
 
 // Chebyshev sweeps k = 2..d (Algorithm 2 loop).  y_k overwrites y_{k-2}'s
 // buffer (read only at the same point), and the last sweep writes `final_role`.
+// neu: the grid has Neumann faces (else the sweeps compiled without them run).
 #pragma nv_exec_check_disable
 template <class T, class TB, bool BLK, bool WY, class V>
-__host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final_role, int skip)
+__host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final_role, int skip, bool neu)
 {
     const double c = sizeof(T), cb = sizeof(TB);
     for (int k = 2; k <= d; ++k) {
@@ -49,8 +50,10 @@ __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final
         a.z = (k % 2 == 0) ? ROLE_YB : ROLE_YA;
         a.out = (k == d) ? final_role : a.z;
         a.b = brole;
-        if (k == 2) v.template go<OpCiSweep<T, TB, BLK, WY>>(PSOLVE_K_CI_SWEEP3, side, a, c + cb + c);
-        else v.template go<OpCiSweep<T, TB, BLK, WY>>(PSOLVE_K_CI_SWEEP4, side, a, c + cb + c + c);
+        const int cls = (k == 2) ? PSOLVE_K_CI_SWEEP3 : PSOLVE_K_CI_SWEEP4;
+        const double bytes = (k == 2) ? c + cb + c : c + cb + c + c;
+        if (neu) v.template go<OpCiSweep<T, TB, BLK, WY, true>>(cls, side, a, bytes);
+        else v.template go<OpCiSweep<T, TB, BLK, WY, false>>(cls, side, a, bytes);
     }
 }
 
@@ -60,7 +63,7 @@ __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final
 // then, when rr, the residual replacement.
 #pragma nv_exec_check_disable
 template <class T, bool BLK, bool WY, class V>
-__host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr)
+__host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, bool neu)
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
@@ -74,7 +77,7 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr)
         const double rd = (iter == 1) ? 8.0 : 24.0;
         v.template go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, rd + 8.0 + (MIX ? c : 0.0) + c);
     }
-    prog_sweeps<T, TB, BLK, WY>(v, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP);
+    prog_sweeps<T, TB, BLK, WY>(v, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP, neu);
     {
         KArgs a{};
         a.skip = SKIP_STOP;
@@ -89,7 +92,7 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr)
         a.out = (d <= 1) ? ROLE_RH : ROLE_YA;
         v.template go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, 24.0 + (MIX ? c : 0.0) + c);
     }
-    prog_sweeps<T, TB, BLK, WY>(v, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF);
+    prog_sweeps<T, TB, BLK, WY>(v, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF, neu);
     {
         KArgs a{};
         a.skip = SKIP_STOP | SKIP_HALF;

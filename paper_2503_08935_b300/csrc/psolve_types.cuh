@@ -98,6 +98,8 @@ struct Desc {
     // role's halo-box map, tmap[2*role + 1] its plain-box map.
     int32_t tma;
     int32_t rr_every;   // residual replacement every rr_every outer iterations (0: never)
+    int32_t bcm;        // zero-flux Neumann faces: bit f for face f (x-, x+, y-, y+, z-, z+)
+    int32_t pad2_;
     const CUtensorMap *tmap;
 };
 

@@ -84,9 +84,13 @@ def test_create_rejects_bad_grids(L, grid, h):
     assert B.last_error()
 
 
-def test_create_rejects_neumann_and_bad_opts(L):
-    st, _ = _create(L, (4, 4, 4), (1, 1, 1), bc=(0, 1, 0, 0, 0, 0))
-    assert st == B.E_ARG and "Dirichlet" in B.last_error()
+def test_create_rejects_bad_faces_and_bad_opts(L):
+    st, _ = _create(L, (4, 4, 4), (1, 1, 1), bc=(0, 2, 0, 0, 0, 0))
+    assert st == B.E_ARG and "Neumann" in B.last_error()
+    st, _ = _create(L, (4, 4, 4), (1, 1, 1), bc=(1, 1, 1, 1, 1, 1))
+    assert st == B.E_ARG and "singular" in B.last_error()
+    st, _ = _create(L, (1, 4, 4), (1, 1, 1), bc=(1, 0, 0, 0, 0, 0))
+    assert st == B.E_ARG and "2 unknowns" in B.last_error()
     st, _ = _create(L, (4, 4, 4), (1, 1, 1), opts=B.default_opts(blocks=(0, 1, 1)))
     assert st == B.E_ARG
     st, _ = _create(L, (4, 4, 4), (1, 1, 1), opts=B.default_opts(cheb_prec=7))
