@@ -27,7 +27,7 @@ import numpy as np
 
 from .build_oracle import build as _build, LIB_PATH
 
-PC_NONE, PC_CHEB, PC_BJ_CHEB, PC_GNOCOMM_CHEB = 0, 1, 2, 3
+PC_NONE, PC_CHEB, PC_BJ_CHEB, PC_GNOCOMM_CHEB, PC_G_BICGS, PC_BJ_BICGS = 0, 1, 2, 3, 4, 5
 OK, E_ARG, E_OOM, NOT_CONVERGED, BREAKDOWN, NONFINITE = 0, 1, 2, 4, 5, 6
 
 _lib = None
@@ -41,6 +41,9 @@ class _PC(ctypes.Structure):
         ("lmin_scale", ctypes.c_double),
         ("lmax_scale", ctypes.c_double),
         ("bc", ctypes.c_int32 * 6),
+        ("inner_rtol", ctypes.c_double),
+        ("inner_maxit", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
     ]
 
 
@@ -185,8 +188,10 @@ def cheb(rhs, h, a, b, degree, blocks=None, bc=None):
     return x
 
 
-def _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc=None):
+def _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc=None, inner_rtol=1e-2, inner_maxit=500):
     pc = _PC()
+    pc.inner_rtol = float(inner_rtol)
+    pc.inner_maxit = int(inner_maxit)
     pc.type = int(precond)
     pc.degree = int(degree)
     for d in range(3):
@@ -198,10 +203,11 @@ def _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc=None):
     return pc
 
 
-def precond_apply(v, h, precond, degree, blocks=(1, 1, 1), lmin_scale=1.0, lmax_scale=1.0, bc=None):
+def precond_apply(v, h, precond, degree, blocks=(1, 1, 1), lmin_scale=1.0, lmax_scale=1.0, bc=None,
+                  inner_rtol=1e-2, inner_maxit=500):
     v = _vec(v)
     out = np.empty_like(v)
-    pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc)
+    pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc, inner_rtol, inner_maxit)
     _check(lib().oracle_precond_apply(_n(v.shape), _h(h), ctypes.byref(pc), _dp(v), _dp(out)),
            "precond_apply")
     return out
@@ -219,7 +225,8 @@ class Result:
 
 
 def bicgstab(b, h, rtol=1e-10, maxit=2000, precond=PC_NONE, degree=0, blocks=(1, 1, 1),
-             lmin_scale=1.0, lmax_scale=1.0, x0=None, half_step_check=True, rr_every=0, bc=None):
+             lmin_scale=1.0, lmax_scale=1.0, x0=None, half_step_check=True, rr_every=0, bc=None,
+             inner_rtol=1e-2, inner_maxit=500):
     """Algorithm 1.  Returns (x, Result).  ``x0`` None means x0 = 0.
     ``rr_every`` > 0 adds residual replacement (not part of the paper's method).
     ``bc`` = face conditions of the operator (None: all zero Dirichlet)."""
@@ -227,7 +234,7 @@ def bicgstab(b, h, rtol=1e-10, maxit=2000, precond=PC_NONE, degree=0, blocks=(1,
     x = np.zeros_like(b) if x0 is None else _vec(x0).copy()
     hs = np.full(max(maxit, 1), np.nan)
     hr = np.full(max(maxit, 1), np.nan)
-    pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc)
+    pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc, inner_rtol, inner_maxit)
     r = _Res()
     if rr_every:
         lib().oracle_bicgstab_rr(_n(b.shape), _h(h), _dp(b), _dp(x), 1 if x0 is not None else 0, float(rtol),

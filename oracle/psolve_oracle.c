@@ -349,6 +349,68 @@ int oracle_cheb_interval_bc(const int64_t n[3], const double h[3], const int32_t
     return ORACLE_OK;
 }
 
+/* Inner Bi-CGSTAB of the flexible preconditioners (Sec. on G(BiCGS) and
+ * BJ(BiCGS)): out = approximate solution of A out = in from out = 0, stopped at
+ * inner_rtol relative to ||in|| or after inner_maxit iterations (the last
+ * iterate is used either way). */
+static int inner_solve(const int64_t n[3], const double h[3], const int32_t bc[6], const oracle_pc *pc,
+                       const double *in, double *out)
+{
+    oracle_pc none;
+    memset(&none, 0, sizeof none);
+    none.type = ORACLE_PC_NONE;
+    for (int f = 0; f < 6; ++f) none.bc[f] = bc ? bc[f] : 0;
+    oracle_result r;
+    const int st = oracle_bicgstab_rr(n, h, in, out, 0, pc->inner_rtol, pc->inner_maxit, &none, 1, 0, &r, NULL,
+                                      NULL);
+    return (st == ORACLE_OK || st == ORACLE_NOT_CONVERGED) ? ORACLE_OK : st;
+}
+
+/* BJ(BiCGS): the block-diagonal system (Eq. 13-14) solved block by block; a
+ * block keeps the domain's condition on the faces it shares with the domain
+ * and has zero Dirichlet ghosts towards its neighbours. */
+static int block_inner_solves(const int64_t n[3], const double h[3], const oracle_pc *pc, const double *in,
+                              double *out)
+{
+    int64_t m[3];
+    for (int d = 0; d < 3; ++d) {
+        if (pc->blocks[d] < 1 || n[d] % pc->blocks[d]) return ORACLE_E_ARG;
+        m[d] = n[d] / pc->blocks[d];
+    }
+    const int64_t M = m[0] * m[1] * m[2];
+    double *bi = (double *)malloc(sizeof(double) * (size_t)M);
+    double *xi = (double *)malloc(sizeof(double) * (size_t)M);
+    if (!bi || !xi) {
+        free(bi); free(xi);
+        return ORACLE_E_OOM;
+    }
+    int st = ORACLE_OK;
+    for (int64_t Bz = 0; Bz < pc->blocks[2] && !st; ++Bz)
+        for (int64_t By = 0; By < pc->blocks[1] && !st; ++By)
+            for (int64_t Bx = 0; Bx < pc->blocks[0] && !st; ++Bx) {
+                const int64_t B[3] = {Bx, By, Bz};
+                int32_t bbc[6];
+                for (int d = 0; d < 3; ++d) {
+                    bbc[2 * d] = (B[d] == 0) ? pc->bc[2 * d] : 0;
+                    bbc[2 * d + 1] = (B[d] == pc->blocks[d] - 1) ? pc->bc[2 * d + 1] : 0;
+                }
+                for (int64_t k = 0; k < m[2]; ++k)
+                    for (int64_t j = 0; j < m[1]; ++j)
+                        for (int64_t i = 0; i < m[0]; ++i)
+                            bi[i + m[0] * (j + m[1] * k)] =
+                                in[(Bx * m[0] + i) + n[0] * ((By * m[1] + j) + n[1] * (Bz * m[2] + k))];
+                st = inner_solve(m, h, bbc, pc, bi, xi);
+                for (int64_t k = 0; k < m[2] && !st; ++k)
+                    for (int64_t j = 0; j < m[1]; ++j)
+                        for (int64_t i = 0; i < m[0]; ++i)
+                            out[(Bx * m[0] + i) + n[0] * ((By * m[1] + j) + n[1] * (Bz * m[2] + k))] =
+                                xi[i + m[0] * (j + m[1] * k)];
+            }
+    free(bi);
+    free(xi);
+    return st;
+}
+
 int oracle_precond_apply(const int64_t n[3], const double h[3], const oracle_pc *pc,
                          const double *in, double *out)
 {
@@ -357,6 +419,8 @@ int oracle_precond_apply(const int64_t n[3], const double h[3], const oracle_pc 
         memcpy(out, in, sizeof(double) * (size_t)N);
         return ORACLE_OK;
     }
+    if (pc->type == ORACLE_PC_G_BICGS) return inner_solve(n, h, pc->bc, pc, in, out);
+    if (pc->type == ORACLE_PC_BJ_BICGS) return block_inner_solves(n, h, pc, in, out);
     double a, b;
     int st = oracle_cheb_interval_bc(n, h, pc->bc, pc->type, pc->blocks, pc->lmin_scale, pc->lmax_scale, &a,
                                      &b);

@@ -29,7 +29,9 @@ enum {
     ORACLE_PC_NONE = 0,        /* M = I                                       */
     ORACLE_PC_CHEB = 1,        /* G(CI): Chebyshev on the whole grid          */
     ORACLE_PC_BJ_CHEB = 2,     /* BJ(CI): Chebyshev per block, block bounds   */
-    ORACLE_PC_GNOCOMM_CHEB = 3 /* GNoComm(CI): per block, whole-grid bounds   */
+    ORACLE_PC_GNOCOMM_CHEB = 3, /* GNoComm(CI): per block, whole-grid bounds  */
+    ORACLE_PC_G_BICGS = 4,      /* G(BiCGS): inner Bi-CGSTAB on the whole grid */
+    ORACLE_PC_BJ_BICGS = 5      /* BJ(BiCGS): inner Bi-CGSTAB on each block     */
 };
 
 typedef struct {
@@ -41,6 +43,9 @@ typedef struct {
     int32_t bc[6];      /* face conditions of the operator (A and M), x-, x+,
                            y-, y+, z-, z+: 0 zero Dirichlet (D, Eq. 4), 1 zero-
                            flux Neumann (N, Eq. 5)                           */
+    double inner_rtol;  /* G(BiCGS) / BJ(BiCGS): inner relative tolerance  */
+    int32_t inner_maxit;/* and iteration limit of the inner Bi-CGSTAB      */
+    int32_t pad_;
 } oracle_pc;
 
 typedef struct {

@@ -39,6 +39,8 @@ MUTANTS = {
                                    "const double s1 = sin(pi / (2.0 * (double)m));"),
     "bj_interval_skips_last_block": ("mu_range_1d(m, 0, fp, &mn2, &mx2); /* last block */",
                                      "mu_range_1d(m, 0, 0, &mn2, &mx2); /* last block */"),
+    "bj_bicgs_blocks_lose_domain_faces": ("bbc[2 * d] = (B[d] == 0) ? pc->bc[2 * d] : 0;", "bbc[2 * d] = 0;"),
+    "bj_bicgs_writes_block_back_shifted": ("out[(Bx * m[0] + i) + n[0] *", "out[(Bx * m[0] + (i + 1) % m[0]) + n[0] *"),
 }
 
 

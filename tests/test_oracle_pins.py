@@ -566,3 +566,44 @@ def test_neumann_rejects_bad_faces():
         O.apply_A(u, (0.1, 0.1, 0.1), blocks=(4, 1, 1), bc=(1, 0, 0, 0, 0, 0))
     with pytest.raises(ValueError):  # Neumann on every face: singular, no Chebyshev interval
         O.cheb_interval((4, 4, 4), (0.1, 0.1, 0.1), O.PC_CHEB, bc=(1, 1, 1, 1, 1, 1))
+
+
+# ------------------------- flexible preconditioners G(BiCGS), BJ(BiCGS) --
+# M_i^-1 v is an inner Bi-CGSTAB solve of A z = v (whole grid, or each block
+# with Dirichlet ghosts towards its neighbours) from z = 0, stopped at an
+# inner tolerance; the outer iteration is Algorithm 1 with that M_i.
+@pytest.mark.parametrize("bc", [None, I.PAPER_BC])
+def test_inner_solve_preconditioners_approach_exact_inverses(bc):
+    shape = (4, 6, 8)
+    h = (0.25, 0.2, 0.3)
+    bcs = bc if bc is not None else (0,) * 6
+    v = I.rhs_uniform(shape, seed=91)
+    z = O.precond_apply(v, h, O.PC_G_BICGS, 0, bc=bc, inner_rtol=1e-13, inner_maxit=1000)
+    assert rel(z, np.linalg.solve(dense_P_bc(shape, h, bcs), v.ravel())) <= 1e-10
+    blocks = (2, 1, 2)
+    zb = O.precond_apply(v, h, O.PC_BJ_BICGS, 0, blocks=blocks, bc=bc, inner_rtol=1e-13, inner_maxit=1000)
+    assert rel(zb, np.linalg.solve(dense_P_bc(shape, h, bcs, blocks), v.ravel())) <= 1e-10
+
+
+def test_exact_inner_solve_makes_the_outer_iteration_stop_at_the_first_half_step():
+    """With M = A (inner solve to round-off), p^ = A^-1 r0, w = r0, alpha = 1 and s = 0."""
+    shape = (5, 6, 7)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=92)
+    x, res = O.bicgstab(b, h, rtol=1e-10, maxit=50, precond=O.PC_G_BICGS, inner_rtol=1e-14, inner_maxit=2000)
+    assert res.status == O.OK and res.iterations == 1 and res.half_step_exit
+    assert rel(x, np.linalg.solve(dense_P(shape, h), b.ravel())) <= 1e-11
+
+
+@pytest.mark.parametrize("pc,blocks,tol", [(O.PC_G_BICGS, (1, 1, 1), 1e-2), (O.PC_BJ_BICGS, (2, 2, 2), 1e-6)])
+@pytest.mark.parametrize("bc", [None, I.PAPER_BC])
+def test_flexible_bicgstab_matches_dense_solve(pc, blocks, tol, bc):
+    shape = (8, 8, 12)
+    h = (0.1, 0.12, 0.09)
+    bcs = bc if bc is not None else (0,) * 6
+    b = I.rhs_uniform(shape, seed=93)
+    x, res = O.bicgstab(b, h, rtol=1e-10, maxit=500, precond=pc, blocks=blocks, bc=bc, inner_rtol=tol,
+                        inner_maxit=500)
+    P = dense_P_bc(shape, h, bcs)
+    assert res.status == O.OK and res.rel_res_true <= 1.1e-10
+    assert rel(x, np.linalg.solve(P, b.ravel())) <= 10 * np.linalg.cond(P) * 1e-10
