@@ -597,14 +597,17 @@ def extra_512_mixed(B, I, torch, stream):
     return res
 
 
-def extra_paper_problem(B, I, torch, stream):
+def extra_paper_problem(B, I, torch, stream, full=False):
     """The experimental set-up's own problem: Dirichlet faces x-, y+, z+ and
     zero-flux Neumann faces x+, y-, z- (Eq. 5), f = sin x + cos y + 3 sin z - 2yz + 2
     (normalised) on its box at h = 0.1 (256^3) or h = 0.4 (64^3), rtol 1e-10,
     24 Chebyshev iterations, the paper's bound rescaling for G(CI) and GNoComm(CI).
     One GPU and no subdivision of the domain across devices; the paper's iteration
     counts (Table 2: 64 MI250X GCDs, 4x4x4 subdomains; single device: 14) are
-    context for the iteration counts, not for the times."""
+    context for the iteration counts, not for the times.  The flexible forms
+    (FBiCGS-G(BiCGS), inner tolerance 1e-2; FBiCGS-BJ(BiCGS), 1e-6; at most 500
+    inner iterations) run at 64^3 always and at 256^3 with ``full`` (one timed
+    solve after a one-iteration warm-up: they take seconds)."""
     out = {}
     scaled = dict(lmin_scale=100.0, lmax_scale=1 - 1e-4)
     cases = [("256_g_ci24_scaled", (256,) * 3, 0.1, B.PC_CHEB, 24, (1, 1, 1), scaled, "50+-2"),
@@ -623,13 +626,29 @@ def extra_paper_problem(B, I, torch, stream):
                                    torch, 1)
         out[name] = {"status": info.status_name, "iterations": info.iterations, "time_ms": ms,
                      "rel_res_true": info.rel_res_true, "paper_iterations": paper}
+    flex = [("64_fbicgs_g_bicgs", (64,) * 3, 0.4, B.PC_G_BICGS, (1, 1, 1), 1e-2, "-"),
+            ("64_fbicgs_bj_bicgs_2x2x2", (64,) * 3, 0.4, B.PC_BJ_BICGS, (2, 2, 2), 1e-6, "-")]
+    if full:
+        flex += [("256_fbicgs_g_bicgs", (256,) * 3, 0.1, B.PC_G_BICGS, (1, 1, 1), 1e-2, "13+-3 (950+-10 inner)"),
+                 ("256_fbicgs_bj_bicgs_4x4x4", (256,) * 3, 0.1, B.PC_BJ_BICGS, (4, 4, 4), 1e-6,
+                  "125+-12 (370+-2 inner)")]
+    for name, shape, hv, pc, blocks, irt, paper in flex:
+        h = (hv, hv, hv)
+        b = torch.from_numpy(I.rhs_paper_problem(shape, h=h)).cuda()
+        x = torch.zeros_like(b)
+        with B.Solver(shape, h, bc=I.PAPER_BC, blocks=blocks, stream=stream, inner_rtol=irt, inner_maxit=500) as s:
+            s.solve(b, x, rtol=1e-10, maxit=1, precond=pc, raise_on_error=False)  # inner set-up and graphs
+            ms, info = _timed_cuda(lambda: s.solve(b, x, rtol=1e-10, maxit=1000, precond=pc), stream, torch, 1)
+        out[name] = {"status": info.status_name, "iterations": info.iterations, "time_ms": ms,
+                     "inner_iterations_per_outer": info.inner_iterations / max(1, info.iterations),
+                     "rel_res_true": info.rel_res_true, "paper_iterations": paper}
     return out
 
 
 def run_extras(args, B, I, torch, stream):
     out = {"config1_32cubed": extra_small_latency(B, I, torch, stream),
            "config4_batch64": extra_batch(B, I, torch, stream),
-           "paper_problem": extra_paper_problem(B, I, torch, stream)}
+           "paper_problem": extra_paper_problem(B, I, torch, stream, full=args.extras == "full")}
     if args.extras == "full":
         out["config3_512_mixed"] = extra_512_mixed(B, I, torch, stream)
         out["config5_serving"] = extra_serve(B, I, torch, stream, 2000, factors=(0.8, 1.2))

@@ -64,8 +64,14 @@ typedef enum {
     PSOLVE_PC_CHEB = 1,         /* G(CI): Chebyshev iteration on the whole grid   */
     PSOLVE_PC_BJ_CHEB = 2,      /* BJ(CI): Chebyshev per block (Eq. 14), bounds
                                    of one block                                   */
-    PSOLVE_PC_GNOCOMM_CHEB = 3  /* GNoComm(CI): per block, bounds of the whole
+    PSOLVE_PC_GNOCOMM_CHEB = 3, /* GNoComm(CI): per block, bounds of the whole
                                    grid                                           */
+    PSOLVE_PC_G_BICGS = 4,      /* G(BiCGS): an inner Bi-CGSTAB solve of A z = v
+                                   on the whole grid (opts.inner_rtol,
+                                   inner_maxit); the outer iteration is then the
+                                   flexible Bi-CGSTAB (FBiCGS) of the paper       */
+    PSOLVE_PC_BJ_BICGS = 5      /* BJ(BiCGS): inner Bi-CGSTAB solves on each block
+                                   (Eq. 13-14), all blocks in one batched solve   */
 } psolve_precond;
 
 /* Storage precision of the Chebyshev preconditioner's vectors.  The outer
@@ -122,12 +128,18 @@ typedef struct {
                                 the environment variable PSOLVE_TUNE_CACHE
                                 names a file, in that file across processes.
                                 0: built-in rule.                            */
-    int32_t reserved[2];
+    int32_t inner_maxit;     /* G(BiCGS) / BJ(BiCGS): inner iteration limit
+                                (default 500)                                */
+    int32_t reserved_;
+    double inner_rtol;       /* and inner relative tolerance; 0 = the
+                                experimental set-up's 1e-2 for G(BiCGS) and
+                                1e-6 for BJ(BiCGS)                           */
 } psolve_opts;
 
 /* Fill *o with the defaults: scales 1, 1; blocks 1,1,1; FP64; half-step check
  * on; x0 = 0; poll auto; graphs on; timing off; true residual on; rr off;
- * engine auto; per-kernel launches (persistent off); autotune off. */
+ * engine auto; per-kernel launches (persistent off); autotune off; inner
+ * solves (G(BiCGS), BJ(BiCGS)) at the set-up's tolerances, 500 iterations. */
 PSOLVE_API void psolve_opts_default(psolve_opts *o);
 
 /* Kernel classes reported by timing mode (psolve_result.kclass_*). */
@@ -157,6 +169,9 @@ typedef struct {
     double seconds;            /* wall time of the call                        */
     double model_bytes;        /* algorithmic HBM bytes of the work done       */
     int64_t kernel_launches;   /* kernels launched by this call (incl. no-ops) */
+    int64_t inner_iterations;  /* G(BiCGS) / BJ(BiCGS): inner Bi-CGSTAB
+                                  iterations over all inner solves (for BJ the
+                                  largest block count of each solve)          */
     /* timing mode only: per kernel class, summed CUDA-event milliseconds,
      * number of launches that did work, and algorithmic bytes they moved. */
     double kclass_ms[PSOLVE_K_NCLASS];
@@ -193,10 +208,19 @@ PSOLVE_API psolve_status psolve_create(const int64_t grid[3], const double h[3],
  *   maxit >= 0.
  *   precond : psolve_precond; degree = Chebyshev iterations d of Algorithm 2
  *             (0 <= d <= 64; = number of A applications; 0 gives b/theta).
+ *             Ignored by G(BiCGS) and BJ(BiCGS).
+ * G(BiCGS) / BJ(BiCGS) run the flexible Bi-CGSTAB: x is updated with the
+ * preconditioned vectors themselves, each an inner Bi-CGSTAB solve from x0 = 0
+ * with the half-step test, stopped at opts.inner_rtol or opts.inner_maxit (an
+ * inner solve that runs out of iterations still counts as an approximation;
+ * an inner breakdown or non-finite value ends the solve with that status).
+ * They need cheb_prec = PSOLVE_FP64, persistent = 0, timing = 0 and
+ * rr_every = 0, and allocate their inner workspaces (for BJ: one per block
+ * plus two block-ordered copies of a grid vector) at the first such solve.
  * Returns the solve's status (also in res->status; res may be NULL).
  * PSOLVE_E_ARG: bad rtol/maxit/precond/degree, blocks not dividing the grid
- * for BJ/GNoComm, or an empty Chebyshev interval (scaled lambda_min >=
- * scaled lambda_max). */
+ * for BJ/GNoComm/BJ(BiCGS), an empty Chebyshev interval (scaled lambda_min >=
+ * scaled lambda_max), or a flexible form with an option it does not take. */
 PSOLVE_API psolve_status psolve_solve(psolve_ctx *ctx, const double *rhs_dev, double *x_dev, double rtol,
                            int32_t maxit, int32_t precond, int32_t degree, psolve_result *res);
 
@@ -218,10 +242,11 @@ PSOLVE_API void psolve_destroy(psolve_ctx *ctx);
 PSOLVE_API psolve_status psolve_apply_A(psolve_ctx *ctx, const double *u_dev, double *out_dev,
                              int32_t block_restricted);
 
-/* out = M^{-1} v for the Chebyshev preconditioner (precond, degree) exactly
- * as psolve_solve applies it, at the context's opts.cheb_prec (the result is
- * widened to double).  precond must not be PSOLVE_PC_NONE.  v and out must
- * not overlap. */
+/* out = M^{-1} v for the preconditioner (precond, degree) exactly as
+ * psolve_solve applies it: for the Chebyshev forms at the context's
+ * opts.cheb_prec (the result is widened to double); for G(BiCGS) / BJ(BiCGS)
+ * one inner solve (or one per block) at opts.inner_rtol and inner_maxit.
+ * precond must not be PSOLVE_PC_NONE.  v and out must not overlap. */
 PSOLVE_API psolve_status psolve_precond_apply(psolve_ctx *ctx, const double *v_dev, double *out_dev,
                                    int32_t precond, int32_t degree);
 
@@ -288,7 +313,8 @@ PSOLVE_API psolve_status psolve_selfcheck_grid_timeout(int64_t limit_ns, int32_t
  * the iteration loop is replayed from one CUDA graph.  Problem q has grid
  * grids[3q..3q+2] = (nx, ny, nz), spacing h[3q..3q+2], right-hand side
  * rhs_dev[q] and solution x_dev[q] (device, caller-owned, same conventions as
- * psolve_solve).  All problems share rtol, maxit, precond, degree and opts.
+ * psolve_solve).  All problems share rtol, maxit, precond, degree and opts;
+ * precond is PSOLVE_PC_NONE or one of the Chebyshev forms.
  * results[q] receives problem q's result.  Each problem's iterates are
  * bitwise the same as when it is solved alone with the same opts. */
 PSOLVE_API psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const double *h,

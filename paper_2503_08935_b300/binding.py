@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libpsolve.so")
 OK, E_ARG, E_OOM, E_CUDA, NOT_CONVERGED, BREAKDOWN, NONFINITE, TIMEOUT, PENDING, REJECTED = range(10)
 STATUS_NAMES = ["OK", "E_ARG", "E_OOM", "E_CUDA", "NOT_CONVERGED", "BREAKDOWN", "NONFINITE", "TIMEOUT",
                 "PENDING", "REJECTED"]
-PC_NONE, PC_CHEB, PC_BJ_CHEB, PC_GNOCOMM_CHEB = 0, 1, 2, 3
+PC_NONE, PC_CHEB, PC_BJ_CHEB, PC_GNOCOMM_CHEB, PC_G_BICGS, PC_BJ_BICGS = 0, 1, 2, 3, 4, 5
 FP64, FP32, BF16 = 0, 1, 2
 K_INIT, K_CI_FIRST, K_CI_SWEEP3, K_CI_SWEEP4, K_STENCIL_DOT, K_STENCIL_2DOT, K_UPDATE, K_OTHER = range(8)
 K_NCLASS = 8
@@ -51,7 +51,9 @@ class Opts(ctypes.Structure):
         ("engine", ctypes.c_int32),
         ("persistent", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("inner_maxit", ctypes.c_int32),
+        ("reserved_", ctypes.c_int32),
+        ("inner_rtol", ctypes.c_double),
     ]
 
 
@@ -68,6 +70,7 @@ class Result(ctypes.Structure):
         ("seconds", ctypes.c_double),
         ("model_bytes", ctypes.c_double),
         ("kernel_launches", ctypes.c_int64),
+        ("inner_iterations", ctypes.c_int64),
         ("kclass_ms", ctypes.c_double * K_NCLASS),
         ("kclass_launches", ctypes.c_int64 * K_NCLASS),
         ("kclass_bytes", ctypes.c_double * K_NCLASS),
@@ -193,6 +196,7 @@ class SolveInfo:
     engine: int = 0
     slab_planes: int = 0
     tuned: int = 0
+    inner_iterations: int = 0
 
     @property
     def status_name(self):
@@ -202,7 +206,8 @@ class SolveInfo:
 def _info(r: Result) -> SolveInfo:
     d = r.as_dict()
     return SolveInfo(r.status, r.iterations, bool(r.half_step_exit), r.rel_res_recursive, r.rel_res_true,
-                     r.seconds, r.model_bytes, r.kernel_launches, d["kclass"], r.engine, r.slab_planes, r.tuned)
+                     r.seconds, r.model_bytes, r.kernel_launches, d["kclass"], r.engine, r.slab_planes, r.tuned,
+                     r.inner_iterations)
 
 
 class Solver:

@@ -314,7 +314,7 @@ psolve_status check_solve_args(double rtol, int maxit, int precond, int degree)
         set_error("maxit must be >= 0");
         return PSOLVE_E_ARG;
     }
-    if (precond < PSOLVE_PC_NONE || precond > PSOLVE_PC_GNOCOMM_CHEB) {
+    if (precond < PSOLVE_PC_NONE || precond > PSOLVE_PC_BJ_BICGS) {
         set_error("unknown preconditioner %d", precond);
         return PSOLVE_E_ARG;
     }
@@ -327,7 +327,8 @@ psolve_status check_solve_args(double rtol, int maxit, int precond, int degree)
 
 psolve_status check_blocks(const Problem &P, int precond)
 {
-    if (precond != PSOLVE_PC_BJ_CHEB && precond != PSOLVE_PC_GNOCOMM_CHEB) return PSOLVE_OK;
+    if (precond != PSOLVE_PC_BJ_CHEB && precond != PSOLVE_PC_GNOCOMM_CHEB && precond != PSOLVE_PC_BJ_BICGS)
+        return PSOLVE_OK;
     for (int d = 0; d < 3; ++d) {
         if (P.n[d] % P.blocks[d] != 0) {
             set_error("blocks[%d] = %d does not divide the grid size %lld", d, P.blocks[d], (long long)P.n[d]);
@@ -384,6 +385,64 @@ void fill_result(const Scal &s, const Problem &P, const Plan &plan, bool use_x0,
     }
 }
 
+// Inner solver of the flexible preconditioners: one problem (G(BiCGS), the
+// whole grid) or one per block (BJ(BiCGS)), each with its own Krylov
+// workspace and scalars, solved together over one launch list.
+struct FlexInner {
+    int precond = -1;          // the flexible preconditioner the buffers were built for
+    int nblk = 0;
+    std::vector<Problem> probs;
+    char *mem = nullptr;       // Krylov workspaces
+    double *bbuf = nullptr;    // BJ: block-contiguous right-hand sides
+    double *xbuf = nullptr;    // BJ: block-contiguous solutions
+    Scal *d_sc = nullptr;
+    Desc *d_desc = nullptr, *h_desc = nullptr;
+    CUtensorMap *d_tmap = nullptr, *h_tmap = nullptr;
+    int32_t *d_list = nullptr, *h_list = nullptr;
+    Scal *h_sc = nullptr;      // 2 x nblk pinned
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    std::vector<GraphEntry> graphs;
+    std::vector<cudaEvent_t> events;
+    long long units = 0;
+
+    void release()
+    {
+        for (GraphEntry &g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        events.clear();
+        for (cudaEvent_t &e : ev)
+            if (e) {
+                cudaEventDestroy(e);
+                e = nullptr;
+            }
+        cudaFree(mem);
+        cudaFree(bbuf);
+        cudaFree(xbuf);
+        cudaFree(d_sc);
+        cudaFree(d_desc);
+        cudaFree(d_tmap);
+        cudaFree(d_list);
+        cudaFreeHost(h_desc);
+        cudaFreeHost(h_tmap);
+        cudaFreeHost(h_list);
+        cudaFreeHost(h_sc);
+        mem = nullptr;
+        bbuf = xbuf = nullptr;
+        d_sc = nullptr;
+        d_desc = h_desc = nullptr;
+        d_tmap = h_tmap = nullptr;
+        d_list = h_list = nullptr;
+        h_sc = nullptr;
+        probs.clear();
+        precond = -1;
+        nblk = 0;
+    }
+};
+
+bool is_flexible(int precond) { return precond == PSOLVE_PC_G_BICGS || precond == PSOLVE_PC_BJ_BICGS; }
+
 } // namespace
 
 // ====================================================================== ctx
@@ -405,6 +464,7 @@ struct psolve_ctx {
     std::vector<cudaEvent_t> events;
     double *d_hb = nullptr, *d_hx = nullptr; // device copies for psolve_solve_host
     bool tma_ok = true; // false: the autotuner chose the general engine
+    FlexInner flex;     // G(BiCGS) / BJ(BiCGS) inner solver, built on first use
 };
 
 extern "C" {
@@ -435,6 +495,7 @@ void psolve_destroy(psolve_ctx *c)
     if (!c) return;
     cudaSetDevice(c->di.dev);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    c->flex.release();
     for (GraphEntry &g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     for (PersistEntry &g : c->pgraphs)
@@ -584,6 +645,283 @@ static Launcher ctx_launcher(psolve_ctx *c)
     return L;
 }
 
+// ============================================================ flexible
+// G(BiCGS) and BJ(BiCGS): the preconditioner is an inner Bi-CGSTAB solve, on
+// the whole grid or on each block, so it changes from one application to the
+// next; Algorithm 1 accommodates that because x is updated with the
+// preconditioned vectors p^ and r^ themselves (flexible Bi-CGSTAB).  The
+// outer iteration runs its phases as separate launches around the inner
+// solves, and the host reads the outer scalars after the half step and after
+// the update; each inner solve is the graph-replayed solve loop over its own
+// problem list.
+
+// Build the inner problems for `precond` on c's grid (once per kind).
+static psolve_status flex_setup(psolve_ctx *c, int precond)
+{
+    FlexInner &F = c->flex;
+    if (F.precond == precond) return PSOLVE_OK;
+    F.release();
+    const Problem &P = c->P;
+    const bool bj = precond == PSOLVE_PC_BJ_BICGS;
+    int nb[3] = {1, 1, 1};
+    int64_t m[3] = {P.n[0], P.n[1], P.n[2]};
+    if (bj)
+        for (int d = 0; d < 3; ++d) {
+            nb[d] = P.blocks[d];
+            m[d] = P.n[d] / nb[d];
+        }
+    const int nblk = nb[0] * nb[1] * nb[2];
+    F.probs.assign((size_t)nblk, Problem());
+    size_t total = 0;
+    std::vector<size_t> offs((size_t)nblk);
+    for (int q = 0; q < nblk; ++q) {
+        Problem &Q = F.probs[q];
+        const int B[3] = {q % nb[0], (q / nb[0]) % nb[1], q / (nb[0] * nb[1])};
+        for (int d = 0; d < 3; ++d) {
+            Q.n[d] = m[d];
+            Q.h[d] = P.h[d];
+            // a block keeps the domain's condition on the faces it shares with the
+            // domain, and has zero Dirichlet ghosts towards its neighbours
+            Q.bc[2 * d] = B[d] == 0 ? P.bc[2 * d] : 0;
+            Q.bc[2 * d + 1] = B[d] == nb[d] - 1 ? P.bc[2 * d + 1] : 0;
+        }
+        Q.prec = PSOLVE_FP64;
+        problem_geometry(Q, c->di.sms);
+        offs[q] = total;
+        total += problem_bytes(Q.n, PSOLVE_FP64, false, c->di.sms);
+    }
+    const size_t M = (size_t)(m[0] * m[1] * m[2]);
+    const size_t list_bytes = sizeof(int32_t) * (LIST_HDR_INTS + 2 * (size_t)nblk);
+#define FLEX_CK(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            set_error("inner solver set-up: %s: %s", #call, cudaGetErrorString(e_));       \
+            F.release();                                                                   \
+            return e_ == cudaErrorMemoryAllocation ? PSOLVE_E_OOM : PSOLVE_E_CUDA;         \
+        }                                                                                  \
+    } while (0)
+    FLEX_CK(cudaMalloc(&F.mem, total));
+    if (bj) {
+        FLEX_CK(cudaMalloc(&F.bbuf, sizeof(double) * M * nblk));
+        FLEX_CK(cudaMalloc(&F.xbuf, sizeof(double) * M * nblk));
+    }
+    FLEX_CK(cudaMalloc(&F.d_sc, sizeof(Scal) * nblk));
+    FLEX_CK(cudaMalloc(&F.d_desc, sizeof(Desc) * nblk));
+    FLEX_CK(cudaMalloc(&F.d_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * nblk));
+    FLEX_CK(cudaMalloc(&F.d_list, list_bytes));
+    FLEX_CK(cudaHostAlloc(&F.h_desc, sizeof(Desc) * nblk, cudaHostAllocDefault));
+    FLEX_CK(cudaHostAlloc(&F.h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * nblk, cudaHostAllocDefault));
+    FLEX_CK(cudaHostAlloc(&F.h_list, list_bytes, cudaHostAllocDefault));
+    FLEX_CK(cudaHostAlloc(&F.h_sc, 2 * sizeof(Scal) * nblk, cudaHostAllocDefault));
+    for (int k = 0; k < 2; ++k) FLEX_CK(cudaEventCreateWithFlags(&F.ev[k], cudaEventDisableTiming));
+    F.h_list[0] = nblk;
+    F.h_list[2] = F.h_list[3] = 0;
+    int32_t ub = 0;
+    for (int q = 0; q < nblk; ++q) {
+        Problem &Q = F.probs[q];
+        problem_bind(Q, F.mem + offs[q]);
+        Q.desc.sc = F.d_sc + q;
+        Q.desc.tmap = F.d_tmap + (size_t)TMAPS_PER_PROBLEM * q;
+        Q.desc.half_check = 1;
+        F.h_list[LIST_HDR_INTS + 2 * q] = q;
+        F.h_list[LIST_HDR_INTS + 1 + 2 * q] = ub;
+        ub += Q.desc.units;
+    }
+    F.h_list[1] = ub;
+    F.units = ub;
+    FLEX_CK(cudaMemcpyAsync(F.d_list, F.h_list, list_bytes, cudaMemcpyHostToDevice, c->stream));
+#undef FLEX_CK
+    F.nblk = nblk;
+    F.precond = precond;
+    return PSOLVE_OK;
+}
+
+// out = inner Bi-CGSTAB approximation of A^-1 v (v, out: device grid vectors,
+// distinct).  *inner_iters += the iteration count (the largest block count).
+static psolve_status flex_inner(psolve_ctx *c, const double *v, double *out, double rtol, int maxit,
+                                int64_t *inner_iters, int64_t *launches)
+{
+    FlexInner &F = c->flex;
+    const bool bj = F.precond == PSOLVE_PC_BJ_BICGS;
+    const size_t M = (size_t)(F.probs[0].npts());
+    if (bj) {
+        enqueue_gather_blocks(c->stream, v, F.bbuf, c->P.n, c->P.blocks, true);
+        PS_CK(cudaGetLastError());
+        ++*launches;
+    }
+    for (int q = 0; q < F.nblk; ++q) {
+        Problem &Q = F.probs[q];
+        Desc &D = Q.desc;
+        D.rtol = rtol;
+        D.maxit = maxit;
+        D.vec[ROLE_B] = bj ? (void *)(F.bbuf + q * M) : (void *)v;
+        D.vec[ROLE_X] = bj ? (void *)(F.xbuf + q * M) : (void *)out;
+        D.vec[ROLE_RT] = D.vec[ROLE_B]; // x0 = 0: r~ = r0 = b
+        problem_encode_tmaps(Q, F.h_tmap + (size_t)TMAPS_PER_PROBLEM * q, c->opts.engine != 1);
+        F.h_desc[q] = D;
+    }
+    PS_CK(cudaMemcpyAsync(F.d_tmap, F.h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * F.nblk,
+                          cudaMemcpyHostToDevice, c->stream));
+    PS_CK(cudaMemcpyAsync(F.d_desc, F.h_desc, sizeof(Desc) * F.nblk, cudaMemcpyHostToDevice, c->stream));
+    PS_CK(cudaMemsetAsync(F.d_sc, 0, sizeof(Scal) * F.nblk, c->stream));
+    Runner R;
+    R.stream = c->stream;
+    R.cap = c->cap;
+    R.d_desc = F.d_desc;
+    R.d_list = F.d_list;
+    R.sms = c->di.sms;
+    R.units = F.units;
+    R.plan.precond = PSOLVE_PC_NONE;
+    R.use_graph = c->opts.use_graph != 0;
+    R.npts = (double)c->P.npts();
+    R.graphs = &F.graphs;
+    R.events = &F.events;
+    R.d_sc = F.d_sc;
+    R.nsc = F.nblk;
+    R.h_sc[0] = F.h_sc;
+    R.h_sc[1] = F.h_sc + F.nblk;
+    R.poll_ev[0] = F.ev[0];
+    R.poll_ev[1] = F.ev[1];
+    R.K = 4;
+    Launcher L = R.launcher();
+    L.iter = 0;
+    enqueue_init(L, false);
+    *launches += L.launches;
+    PS_CK(L.err);
+    psolve_status st = run_loop(R, maxit);
+    *launches += R.launches;
+    if (st != PSOLVE_OK) return st;
+    const Scal *sc = R.h_sc[R.last_slot];
+    int worst = 0;
+    for (int q = 0; q < F.nblk; ++q) {
+        worst = std::max(worst, sc[q].iter);
+        // a breakdown or a non-finite value ends the outer solve; a solve that
+        // ran out of iterations still gives a usable approximation
+        if (sc[q].status != PSOLVE_OK && sc[q].status != PSOLVE_NOT_CONVERGED) {
+            set_error("inner Bi-CGSTAB of problem %d stopped with status %d", q, sc[q].status);
+            return (psolve_status)sc[q].status;
+        }
+    }
+    *inner_iters += worst;
+    if (bj) {
+        enqueue_gather_blocks(c->stream, F.xbuf, out, c->P.n, c->P.blocks, false);
+        PS_CK(cudaGetLastError());
+        ++*launches;
+    }
+    return PSOLVE_OK;
+}
+
+// The flexible forms keep p^ and r^ in FP64 and drive the outer phases from
+// the host.
+static psolve_status check_flexible(const psolve_ctx *c)
+{
+    if (c->P.prec != PSOLVE_FP64) {
+        set_error("G(BiCGS) and BJ(BiCGS) need a context with cheb_prec = PSOLVE_FP64");
+        return PSOLVE_E_ARG;
+    }
+    if (c->opts.persistent || c->opts.timing || c->opts.rr_every) {
+        set_error("G(BiCGS) and BJ(BiCGS) run without persistent, timing and rr_every");
+        return PSOLVE_E_ARG;
+    }
+    return PSOLVE_OK;
+}
+
+static double flex_rtol(const psolve_ctx *c, int precond)
+{
+    if (c->opts.inner_rtol > 0.0) return c->opts.inner_rtol;
+    return precond == PSOLVE_PC_G_BICGS ? 1e-2 : 1e-6; // the experimental set-up's tolerances
+}
+
+static int flex_maxit(const psolve_ctx *c) { return c->opts.inner_maxit > 0 ? c->opts.inner_maxit : 500; }
+
+// The outer flexible iteration on c's workspace (FP64 vectors p^ = ROLE_PH,
+// r^ = ROLE_RH); D, the descriptor, is already uploaded.
+static psolve_status flex_solve(psolve_ctx *c, int precond, int maxit, bool use_x0, bool tr, double t0,
+                                psolve_result *res)
+{
+    psolve_status st = flex_setup(c, precond);
+    if (st != PSOLVE_OK) return st;
+    Problem &P = c->P;
+    Scal *hs = c->h_sc + 2;
+    int64_t launches = 0, inner_iters = 0;
+    const double irtol = flex_rtol(c, precond);
+    const int imaxit = flex_maxit(c);
+    auto read = [&]() -> psolve_status {
+        PS_CK(cudaMemcpyAsync(hs, P.d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
+        PS_CK(cudaStreamSynchronize(c->stream));
+        return PSOLVE_OK;
+    };
+    Launcher L = ctx_launcher(c);
+    L.iter = 0;
+    enqueue_init(L, use_x0);
+    PS_CK(L.err);
+    launches += L.launches;
+    st = read();
+    if (st != PSOLVE_OK) return st;
+    double *ph = (double *)P.desc.vec[ROLE_PH], *rh = (double *)P.desc.vec[ROLE_RH];
+    L.launches = 0;
+    for (int it = 1; it <= maxit && !hs->stop; ++it) {
+        L.iter = it;
+        enqueue_flex_phase(L, FLEX_PUPDATE);
+        PS_CK(L.err);
+        st = flex_inner(c, (const double *)P.desc.vec[ROLE_P], ph, irtol, imaxit, &inner_iters, &launches);
+        if (st != PSOLVE_OK) return st;
+        enqueue_flex_phase(L, FLEX_W);
+        enqueue_flex_phase(L, FLEX_S);
+        PS_CK(L.err);
+        st = read();
+        if (st != PSOLVE_OK) return st;
+        if (hs->stop) break;
+        if (!hs->half) {
+            st = flex_inner(c, (const double *)P.desc.vec[ROLE_S], rh, irtol, imaxit, &inner_iters, &launches);
+            if (st != PSOLVE_OK) return st;
+            enqueue_flex_phase(L, FLEX_T);
+        }
+        enqueue_flex_phase(L, FLEX_UPDATE);
+        PS_CK(L.err);
+        st = read();
+        if (st != PSOLVE_OK) return st;
+    }
+    launches += L.launches;
+    if (hs->zero_x) PS_CK(cudaMemsetAsync(P.desc.vec[ROLE_X], 0, sizeof(double) * (size_t)P.npts(), c->stream));
+    if (tr) {
+        Launcher T = ctx_launcher(c);
+        T.iter = -1;
+        enqueue_true_residual(T);
+        launches += T.launches;
+        PS_CK(T.err);
+    }
+    st = read();
+    if (st != PSOLVE_OK) return st;
+    Plan plan; // PSOLVE_PC_NONE; the byte model below replaces its figure
+    psolve_result tmp;
+    std::memset(&tmp, 0, sizeof tmp);
+    fill_result(*hs, P, plan, use_x0, tr, t0, launches, &tmp);
+    tmp.inner_iterations = inner_iters;
+    {
+        // algorithmic bytes of the outer phases (the inner solves excluded)
+        std::vector<LaunchRec> recs;
+        Launcher D;
+        D.dry = true;
+        D.npts = (double)P.npts();
+        D.recs = &recs;
+        D.iter = 0;
+        enqueue_init(D, use_x0);
+        for (int it = 1; it <= hs->iter; ++it) {
+            D.iter = it;
+            for (int ph = FLEX_PUPDATE; ph <= FLEX_UPDATE; ++ph) enqueue_flex_phase(D, ph);
+        }
+        if (tr) {
+            D.iter = -1;
+            enqueue_true_residual(D);
+        }
+        tmp.model_bytes = model_bytes_for(recs, hs->iter, hs->half_exit);
+    }
+    if (res) *res = tmp;
+    return (psolve_status)hs->status;
+}
+
 psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double rtol, int32_t maxit,
                            int32_t precond, int32_t degree, psolve_result *res)
 {
@@ -602,6 +940,10 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     }
     st = check_rr(c->opts.rr_every);
     if (st != PSOLVE_OK) return st;
+    if (is_flexible(precond)) {
+        st = check_flexible(c);
+        if (st != PSOLVE_OK) return st;
+    }
     PS_CK(cudaSetDevice(c->di.dev));
     Problem &P = c->P;
     st = problem_set_cheb(P, precond, degree, c->opts.lmin_scale, c->opts.lmax_scale);
@@ -622,6 +964,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     D.vec[ROLE_U] = D.vec[ROLE_V] = nullptr;
     st = upload_desc(c);
     if (st != PSOLVE_OK) return st;
+    if (is_flexible(precond)) return flex_solve(c, precond, maxit, use_x0, c->opts.true_residual != 0, t0, res);
 
     Runner R;
     R.stream = c->stream;
@@ -807,12 +1150,26 @@ psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, 
     psolve_status st = check_solve_args(0.0, 0, precond, degree);
     if (st != PSOLVE_OK) return st;
     if (precond == PSOLVE_PC_NONE) {
-        set_error("psolve_precond_apply needs a Chebyshev preconditioner");
+        set_error("psolve_precond_apply needs a preconditioner");
         return PSOLVE_E_ARG;
     }
     st = check_blocks(c->P, precond);
     if (st != PSOLVE_OK) return st;
     PS_CK(cudaSetDevice(c->di.dev));
+    if (is_flexible(precond)) {
+        if (c->P.prec != PSOLVE_FP64) return check_flexible(c);
+        if (v == out) {
+            set_error("the inner solve of %s needs distinct v and out", precond == PSOLVE_PC_G_BICGS ? "G(BiCGS)" : "BJ(BiCGS)");
+            return PSOLVE_E_ARG;
+        }
+        st = flex_setup(c, precond);
+        if (st != PSOLVE_OK) return st;
+        int64_t iters = 0, launches = 0;
+        st = flex_inner(c, v, out, flex_rtol(c, precond), flex_maxit(c), &iters, &launches);
+        if (st != PSOLVE_OK) return st;
+        PS_CK(cudaStreamSynchronize(c->stream));
+        return PSOLVE_OK;
+    }
     Problem &P = c->P;
     st = problem_set_cheb(P, precond, degree, c->opts.lmin_scale, c->opts.lmax_scale);
     if (st != PSOLVE_OK) return st;
@@ -866,6 +1223,10 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     }
     psolve_status st = check_solve_args(rtol, maxit, precond, degree);
     if (st != PSOLVE_OK) return st;
+    if (is_flexible(precond)) {
+        set_error("batched solves take G(CI), BJ(CI), GNoComm(CI) or no preconditioner");
+        return PSOLVE_E_ARG;
+    }
     psolve_opts o;
     psolve_opts_default(&o);
     if (opts) o = *opts;

@@ -289,6 +289,59 @@ void enqueue_tune_probe(Launcher &L, int prec, bool blk)
     }
 }
 
+void enqueue_flex_phase(Launcher &L, int phase)
+{
+    KArgs a{};
+    a.skip = SKIP_STOP;
+    switch (phase) {
+    case FLEX_PUPDATE: L.go<OpPUpdate>(PSOLVE_K_OTHER, 0, a, L.iter == 1 ? 16.0 : 32.0); break;
+    case FLEX_W:
+        a.in = ROLE_PH;
+        L.go<OpStencilDot<double>>(PSOLVE_K_STENCIL_DOT, 0, a, 24.0);
+        break;
+    case FLEX_S: L.go<OpSUpdate>(PSOLVE_K_OTHER, 0, a, 24.0); break;
+    case FLEX_T:
+        a.skip = SKIP_STOP | SKIP_HALF;
+        a.in = ROLE_RH;
+        L.go<OpStencil2Dot<double>>(PSOLVE_K_STENCIL_2DOT, 1, a, 24.0);
+        break;
+    default:
+        a.in = ROLE_PH;
+        a.aux = ROLE_RH;
+        L.go<OpUpdate<double>>(PSOLVE_K_UPDATE, 0, a, 64.0, 24.0, 1);
+        break;
+    }
+}
+
+// One thread per grid point: (i, j, k) -> block (i / mx, j / my, k / mz),
+// position inside the block; copies in the direction asked for.
+__global__ void k_gather_blocks(const double *src, double *dst, int nx, int ny, int nz, int mx, int my, int mz,
+                                int bx, int by, int to_blocks)
+{
+    const long long N = (long long)nx * ny * nz;
+    const long long M = (long long)mx * my * mz;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((long long)nx * ny));
+        const int Bx = i / mx, By = j / my, Bz = k / mz;
+        const long long q = Bx + (long long)bx * (By + (long long)by * Bz);
+        const long long l = q * M + (i - Bx * mx) + (long long)mx * ((j - By * my) + (long long)my * (k - Bz * mz));
+        if (to_blocks) dst[l] = src[g];
+        else dst[g] = src[l];
+    }
+}
+
+void enqueue_gather_blocks(cudaStream_t s, const double *src, double *dst, const int64_t n[3], const int blocks[3],
+                           bool to_blocks)
+{
+    const long long N = n[0] * n[1] * n[2];
+    const int threads = 256;
+    const long long want = (N + threads - 1) / threads;
+    const int grid = (int)(want < 65535 * 4 ? want : 65535 * 4);
+    k_gather_blocks<<<grid, threads, 0, s>>>(src, dst, (int)n[0], (int)n[1], (int)n[2], (int)(n[0] / blocks[0]),
+                                             (int)(n[1] / blocks[1]), (int)(n[2] / blocks[2]), blocks[0], blocks[1],
+                                             to_blocks ? 1 : 0);
+}
+
 bool launch_did_work(const LaunchRec &r, int final_iter, int half_exit)
 {
     if (r.side == 2) // replacement: counted on the multiples of rr_every before the exit iteration
@@ -483,8 +536,8 @@ psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_
 {
     Desc &D = P.desc;
     D.degree = degree;
-    if (precond == PSOLVE_PC_NONE) {
-        D.theta_inv = D.two_over_delta = D.two_sigma = 0.0;
+    if (precond == PSOLVE_PC_NONE || precond == PSOLVE_PC_G_BICGS || precond == PSOLVE_PC_BJ_BICGS) {
+        D.theta_inv = D.two_over_delta = D.two_sigma = 0.0; // no Chebyshev iteration
         return PSOLVE_OK;
     }
     double a, b;

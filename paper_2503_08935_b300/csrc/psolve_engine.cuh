@@ -133,6 +133,21 @@ void enqueue_true_residual(Launcher &L);
 void enqueue_apply_A(Launcher &L, bool blocked);
 void enqueue_dot(Launcher &L);
 void enqueue_precond(Launcher &L, const Plan &plan);
+// Outer phases of the flexible Bi-CGSTAB (G(BiCGS), BJ(BiCGS)): the inner
+// solves between them write p^ (ROLE_PH) and r^ (ROLE_RH) in FP64.
+enum FlexPhase {
+    FLEX_PUPDATE = 0, // p = r + beta (p - omega w), in place (p = r first)
+    FLEX_W,           // w = A p^, r~ . w -> alpha
+    FLEX_S,           // s = r - alpha w, ||s||^2 -> half-step test
+    FLEX_T,           // t = A r^, t.s, t.t -> omega
+    FLEX_UPDATE       // x, r and r~.r, r.r -> beta, stop test
+};
+void enqueue_flex_phase(Launcher &L, int phase);
+// Gather a grid vector into block-contiguous storage (block q = Bx + bx (By +
+// by Bz), x fastest inside a block) and back.
+void enqueue_gather_blocks(cudaStream_t s, const double *src, double *dst, const int64_t n[3], const int blocks[3],
+                           bool to_blocks);
+
 // The autotuner's probe kernels (a sweep, a stencil with two dots, an update)
 // for Chebyshev vectors of precision `prec`; needs every role bound.
 void enqueue_tune_probe(Launcher &L, int prec, bool blk);
