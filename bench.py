@@ -39,10 +39,18 @@ WORKLOAD = "poisson 256^3 FP64, Bi-CGSTAB + G(CI) Chebyshev degree 8, exact boun
 GOLDEN_256 = os.path.join(ROOT, "tests", "golden", "oracle_256_cheb8.json")
 NCU_SUMMARY = os.path.join(ROOT, "profiles", "ncu_ci_sweep4_256_{prec}.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2503_08935_b300", "csrc", "psolve_kernels.cuh")
-# FP64 instructions per point of a Chebyshev sweep k >= 3 as the kernel writes it:
-# three neighbour-pair sums, one multiply and four fused multiply-adds (exact bounds:
-# the y coefficient vanishes, see OpCiSweep).
-SWEEP_FP64_OPS_PER_POINT = 8
+# FP64 instructions per point of a Chebyshev sweep k >= 3 (exact bounds, where the
+# y coefficient vanishes; see OpCiSweep): b, y_{k-2} and the six neighbours of
+# y_{k-1} are combined with three neighbour-pair sums and four fused multiply-adds
+# (7, the least for eight inputs) in the sweeps before the last, whose iterates are
+# stored scaled so that b enters with coefficient 1; the last sweep (unscaled
+# output) adds one multiply (8).
+
+
+def sweep4_fp64_ops_per_point(degree):
+    """Mean FP64 instructions per point over the sweeps k = 3..degree."""
+    n = degree - 2
+    return (7.0 * (n - 1) + 8.0) / n if n > 0 else 8.0
 
 
 def dist_env():
@@ -317,12 +325,13 @@ def run_gpu(args):
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
             mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2032.0
             peak_ops = 2.0 * sms * mhz * 1e6
-            ops = SWEEP_FP64_OPS_PER_POINT * npts / (avg_ms * 1e-3)
+            opp = sweep4_fp64_ops_per_point(DEGREE)
+            ops = opp * npts / (avg_ms * 1e-3)
             roof.update({"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12, "unit": "TFP64op/s",
                          "frac": ops / peak_ops,
                          "peak_kind": (f"derived: 2 FP64 pipe instructions/clock/SM x {sms} SMs x "
                                        f"{mhz:.0f} MHz median SM clock of this run"),
-                         "ops_per_point": SWEEP_FP64_OPS_PER_POINT})
+                         "ops_per_point": opp})
         else:
             roof.update({"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy test)"})

@@ -979,6 +979,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     R.plan.exact_bounds = c->opts.lmin_scale == 1.0 && c->opts.lmax_scale == 1.0;
     R.plan.rr_every = c->opts.rr_every;
     R.plan.neumann = P.desc.bcm != 0;
+    R.plan.split = sweep_split(R.plan.prec, P.desc.zc);
     R.use_graph = c->opts.use_graph != 0;
     R.timing = c->opts.timing != 0;
     R.npts = (double)P.npts();
@@ -1190,6 +1191,7 @@ psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, 
     plan.prec = P.prec;
     plan.exact_bounds = c->opts.lmin_scale == 1.0 && c->opts.lmax_scale == 1.0;
     plan.neumann = P.desc.bcm != 0;
+    plan.split = sweep_split(plan.prec, P.desc.zc);
     Launcher L = ctx_launcher(c);
     enqueue_precond(L, plan);
     PS_CK(L.err);
@@ -1398,6 +1400,11 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
     R.plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : o.cheb_prec;
     R.plan.exact_bounds = o.lmin_scale == 1.0 && o.lmax_scale == 1.0;
     R.plan.rr_every = o.rr_every;
+    {
+        int min_zc = 1 << 30;
+        for (const Problem &P : probs) min_zc = std::min(min_zc, (int)P.desc.zc);
+        R.plan.split = sweep_split(R.plan.prec, min_zc);
+    }
     R.use_graph = o.use_graph != 0;
     R.timing = o.timing != 0;
     R.npts = 0;

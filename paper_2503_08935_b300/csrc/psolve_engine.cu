@@ -89,7 +89,8 @@ void Launcher::go(int cls, int side, KArgs a, double bytes_per_pt, double half_b
     }
     if (configure) return;
     long long g = (long long)occ * sms;
-    if (units < g) g = units;
+    const long long work = (Op::STENCIL && Op::ND == 0 && a.split > 1) ? units * a.split : units;
+    if (work < g) g = work;
     if (g < 1) g = 1;
     a.descs = d_desc;
     a.list = d_list;
@@ -165,10 +166,10 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
 
 // --------------------------------------------------- per-iteration kernels --
 template <class T, bool BLK>
-static void iteration_cheb(Launcher &L, int d, bool eb, bool rr, bool neu)
+static void iteration_cheb(Launcher &L, int d, bool eb, bool rr, bool neu, int split)
 {
-    if (eb) prog_iteration_cheb<T, BLK, false>(L, d, L.iter, rr, neu);
-    else prog_iteration_cheb<T, BLK, true>(L, d, L.iter, rr, neu);
+    if (eb) prog_iteration_cheb<T, BLK, false>(L, d, L.iter, rr, neu, split);
+    else prog_iteration_cheb<T, BLK, true>(L, d, L.iter, rr, neu, split);
 }
 
 void enqueue_iteration(Launcher &L, const Plan &plan)
@@ -182,16 +183,16 @@ void enqueue_iteration(Launcher &L, const Plan &plan)
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
     switch (plan.prec) {
     case PSOLVE_FP32:
-        if (blk) iteration_cheb<float, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
-        else iteration_cheb<float, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
+        if (blk) iteration_cheb<float, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
+        else iteration_cheb<float, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
         break;
     case PSOLVE_BF16:
-        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
-        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
+        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
+        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
         break;
     default:
-        if (blk) iteration_cheb<double, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
-        else iteration_cheb<double, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann);
+        if (blk) iteration_cheb<double, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
+        else iteration_cheb<double, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
         break;
     }
 }
@@ -222,7 +223,7 @@ void enqueue_dot(Launcher &L)
 // reads v through ROLE_R (the caller points ROLE_R at v and sets first = 1,
 // iter = 0), then the sweeps, then a widening copy of p^ into ROLE_V.
 template <class T, bool BLK>
-static void precond_cheb(Launcher &L, int d, bool eb, bool neu)
+static void precond_cheb(Launcher &L, int d, bool eb, bool neu, int split)
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
@@ -231,8 +232,8 @@ static void precond_cheb(Launcher &L, int d, bool eb, bool neu)
     a.in = ROLE_PCUR;
     a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
     L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
-    if (eb) prog_sweeps<T, TB, BLK, false>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu);
-    else prog_sweeps<T, TB, BLK, true>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu);
+    if (eb) prog_sweeps<T, TB, BLK, false>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split);
+    else prog_sweeps<T, TB, BLK, true>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split);
     KArgs w{};
     w.in = ROLE_PH;
     w.out = ROLE_V;
@@ -244,16 +245,16 @@ void enqueue_precond(Launcher &L, const Plan &plan)
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
     switch (plan.prec) {
     case PSOLVE_FP32:
-        if (blk) precond_cheb<float, true>(L, plan.degree, plan.exact_bounds, plan.neumann);
-        else precond_cheb<float, false>(L, plan.degree, plan.exact_bounds, plan.neumann);
+        if (blk) precond_cheb<float, true>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
+        else precond_cheb<float, false>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
         break;
     case PSOLVE_BF16:
-        if (blk) precond_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, plan.neumann);
-        else precond_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, plan.neumann);
+        if (blk) precond_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
+        else precond_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
         break;
     default:
-        if (blk) precond_cheb<double, true>(L, plan.degree, plan.exact_bounds, plan.neumann);
-        else precond_cheb<double, false>(L, plan.degree, plan.exact_bounds, plan.neumann);
+        if (blk) precond_cheb<double, true>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
+        else precond_cheb<double, false>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
         break;
     }
 }
@@ -261,16 +262,17 @@ void enqueue_precond(Launcher &L, const Plan &plan)
 // The autotuner's probe: one Chebyshev sweep (k >= 3 form), one stencil with
 // two dots and one update, with every role on workspace vectors and no skips.
 template <class T, bool BLK>
-static void tune_probe(Launcher &L)
+static void tune_probe(Launcher &L, int split)
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     KArgs s{};
     s.k = 3;
+    s.split = split;
     s.in = ROLE_YA;
     s.z = ROLE_YB;
     s.b = is_mixed<T>() ? ROLE_BC : ROLE_PH;
     s.out = ROLE_RH;
-    L.go<OpCiSweep<T, TB, BLK, false, false>>(PSOLVE_K_CI_SWEEP4, 0, s, 0.0);
+    L.go<OpCiSweep<T, TB, BLK, false, false, !is_mixed<T>()>>(PSOLVE_K_CI_SWEEP4, 0, s, 0.0);
     KArgs t{};
     t.in = ROLE_RH;
     L.go<OpStencil2Dot<T>>(PSOLVE_K_STENCIL_2DOT, 0, t, 0.0);
@@ -280,12 +282,14 @@ static void tune_probe(Launcher &L)
     L.go<OpUpdate<T>>(PSOLVE_K_UPDATE, 0, u, 0.0);
 }
 
-void enqueue_tune_probe(Launcher &L, int prec, bool blk)
+void enqueue_tune_probe(Launcher &L, int prec, bool blk, int split)
 {
     switch (prec) {
-    case PSOLVE_FP32: blk ? tune_probe<float, true>(L) : tune_probe<float, false>(L); break;
-    case PSOLVE_BF16: blk ? tune_probe<__nv_bfloat16, true>(L) : tune_probe<__nv_bfloat16, false>(L); break;
-    default: blk ? tune_probe<double, true>(L) : tune_probe<double, false>(L); break;
+    case PSOLVE_FP32: blk ? tune_probe<float, true>(L, split) : tune_probe<float, false>(L, split); break;
+    case PSOLVE_BF16:
+        blk ? tune_probe<__nv_bfloat16, true>(L, split) : tune_probe<__nv_bfloat16, false>(L, split);
+        break;
+    default: blk ? tune_probe<double, true>(L, split) : tune_probe<double, false>(L, split); break;
     }
 }
 
@@ -550,6 +554,33 @@ psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_
     D.two_sigma = 2.0 * sigma;
     D.rho[0] = 1.0 / sigma;
     for (int k = 1; k <= MAX_DEGREE; ++k) D.rho[k] = 1.0 / (2.0 * sigma - D.rho[k - 1]);
+    // CI sweep 1: y_1 = (2 rho_1/delta)(2u - A u / theta), A u written with
+    // the neighbour-pair sums: A u = cc u - cx sx - cy sy - cz sz
+    const double tod = D.two_over_delta, c1 = tod * D.rho[1];
+    D.ci1[0] = c1 * (2.0 - D.cc * D.theta_inv);
+    D.ci1[1] = c1 * D.theta_inv * D.cx;
+    D.ci1[2] = c1 * D.theta_inv * D.cy;
+    D.ci1[3] = c1 * D.theta_inv * D.cz;
+    // sweeps k >= 2: w = rho_k (2 sigma y + (2/delta)(b - A y) - rho_{k-1} z)
+    //   = rho_k (2 sigma - (2/delta) cc) y + rho_k (2/delta) b - rho_k rho_{k-1} z
+    //     + rho_k (2/delta)(cx sx + cy sy + cz sz),  z = b/theta when k = 2,
+    // with FP64 vectors stored as yhat_j = y_j / s_j, s_j = the b coefficient
+    // of sweep j for 2 <= j < d (1 otherwise), so b enters with coefficient 1
+    const bool scaled = P.prec == PSOLVE_FP64;
+    auto b_coef = [&](int j) { return j == 2 ? D.rho[2] * tod - D.rho[2] * D.rho[1] * D.theta_inv : D.rho[j] * tod; };
+    auto scale = [&](int j) { return (scaled && j >= 2 && j < degree) ? b_coef(j) : 1.0; };
+    std::memset(D.cik, 0, sizeof D.cik);
+    for (int k = 2; k <= degree && k <= MAX_DEGREE; ++k) {
+        const double rk = D.rho[k], rk1 = D.rho[k - 1];
+        const double sk = scale(k), q1 = scale(k - 1) / sk, q2 = scale(k - 2) / sk;
+        double *c = D.cik[k];
+        c[0] = rk * (D.two_sigma - tod * D.cc) * q1;
+        c[1] = b_coef(k) / sk; // exactly 1 when scaled and k < d
+        c[2] = -rk * rk1 * q2;
+        c[3] = rk * tod * D.cx * q1;
+        c[4] = rk * tod * D.cy * q1;
+        c[5] = rk * tod * D.cz * q1;
+    }
     return PSOLVE_OK;
 }
 

@@ -47,12 +47,20 @@ struct Plan {
     bool exact_bounds = false; // scales (1, 1): the sweeps' y coefficient is zero
     int rr_every = 0;          // residual replacement period (0: none)
     bool neumann = false;      // the grid has zero-flux Neumann faces
+    int split = 1;             // sub-units per work unit for the Chebyshev sweeps (see sweep_split)
     bool operator==(const Plan &o) const
     {
         return precond == o.precond && degree == o.degree && prec == o.prec && exact_bounds == o.exact_bounds &&
-               rr_every == o.rr_every && neumann == o.neumann;
+               rr_every == o.rr_every && neumann == o.neumann && split == o.split;
     }
 };
+
+// Sub-units per work unit for the Chebyshev sweeps of a launch list whose
+// smallest slab is min_zc planes.  The FP64 sweeps are bound by the FP64
+// pipe, to which a unit's two extra halo planes add no work, so halving a
+// 32-plane unit only evens out the end of each launch (256^3: 247 -> 230 us
+// per sweep); the FP32/BF16 sweeps keep whole units.
+inline int sweep_split(int prec, int min_zc) { return (prec == PSOLVE_FP64 && min_zc >= 32) ? 2 : 1; }
 
 inline size_t ci_elem_bytes(int prec) { return prec == PSOLVE_FP64 ? 8 : (prec == PSOLVE_FP32 ? 4 : 2); }
 
@@ -149,8 +157,9 @@ void enqueue_gather_blocks(cudaStream_t s, const double *src, double *dst, const
                            bool to_blocks);
 
 // The autotuner's probe kernels (a sweep, a stencil with two dots, an update)
-// for Chebyshev vectors of precision `prec`; needs every role bound.
-void enqueue_tune_probe(Launcher &L, int prec, bool blk);
+// for Chebyshev vectors of precision `prec`; needs every role bound.  split:
+// the sweep's sub-units per work unit (sweep_split).
+void enqueue_tune_probe(Launcher &L, int prec, bool blk, int split);
 
 // Encode the tensor maps of every bound vector of P into maps[0..2*NROLES)
 // and set P.desc.tma (1 when the TMA engine can run this problem: nx % 8 == 0,

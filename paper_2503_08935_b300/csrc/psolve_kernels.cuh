@@ -377,7 +377,7 @@ __device__ __forceinline__ void apply_neumann(int m, bool first_plane, bool last
 }
 
 // ------------------------------------------------------------------------
-// Stencil march over chunks [c0, c1) of one tile.
+// Stencil march over planes [kb, ke) of chunk c0 of one tile.
 // Op provides: types C (arithmetic), U (own-column value), PW (pointwise
 // operands); ND; BLOCKED; U load(idx); C sv(U); PW pw(bool, idx);
 // void emit(idx, C u, C sx, C sy, C sz, U uc, PW, acc) with u the centre value
@@ -387,7 +387,7 @@ __device__ __forceinline__ void apply_neumann(int m, bool first_plane, bool last
 // per SM), not HBM, bounds the FP64 kernels, so every FP64 instruction counts.
 // ------------------------------------------------------------------------
 template <class Op>
-__device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, int c0, int c1,
+__device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, int c0, int kb, int ke,
                                               typename Op::C *sp, double *sred)
 {
     using C = typename Op::C;
@@ -398,7 +398,7 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
     constexpr int SW = TILE_X + 2;
     constexpr int SPL = SW * (TILE_Y + 2);
 
-    const int nx = D.nx, ny = D.ny, nz = D.nz, zc = D.zc;
+    const int nx = D.nx, ny = D.ny, nz = D.nz;
     const int plane = nx * ny;
     const int tid = threadIdx.x, tx = tid % TILE_X, ty = tid / TILE_X;
     const int i0 = (tile % D.tiles_x) * TILE_X, j0 = (tile / D.tiles_x) * TILE_Y;
@@ -431,8 +431,6 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
         okn = (j % D.by) != D.by - 1;
     }
     const int nbm = (HasNeumann<Op>::value && D.bcm) ? neumann_mask(D.bcm, i, j, nx, ny) : 0;
-    const int kb = c0 * zc;
-    const int ke = min(nz, c1 * zc);
 
     __syncthreads(); // the previous run's readers of sp are done
     U um = (in && kb >= 1) ? op.load(col + (kb - 1) * plane) : U(0);
@@ -449,8 +447,7 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
 #pragma unroll
     for (int q = 0; q < NDA; ++q) acc[q] = 0.0;
     const int ntiles = D.tiles_x * D.tiles_y;
-    int unit = c0 * ntiles + tile; // units are numbered chunk-major
-    int cend = min(nz, (c0 + 1) * zc);
+    const int unit = c0 * ntiles + tile; // units are numbered chunk-major
     int buf = 0;
 
     for (int k = kb; k < ke; ++k) {
@@ -486,14 +483,8 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
         if constexpr (Op::BLOCKED) {
             if (++kk == D.bz) kk = 0;
         }
-        if constexpr (ND > 0) {
-            if (k + 1 == cend) {
-                flush_unit<ND>(acc, sred, D.partials, unit);
-                unit += ntiles;
-                cend = min(nz, cend + zc);
-            }
-        }
     }
+    if constexpr (ND > 0) flush_unit<ND>(acc, sred, D.partials, unit);
 }
 
 // Pointwise march (no stencil) over chunks [c0, c1) of one tile.  Planes are
@@ -649,7 +640,7 @@ __device__ __forceinline__ void stage_ptrs(unsigned char *stage, const void *(&h
     for (int a = 0; a < Op::NP; ++a) p[a] = stage + Op::NH * R::HSTRIDE + a * R::PSTRIDE;
 }
 
-// Stencil march over chunks [c0, c1) of one tile, operands staged by TMA.
+// Stencil march over planes [kb, ke) of chunk c0 of one tile, operands staged by TMA.
 // `seq` counts the planes this CTA has staged so far (all threads agree); plane
 // number n lives in stage n % STAGES and completes phase (n / STAGES) & 1.
 // The stages (and mbarrier parities) of planes k-1, k, k+1 are carried as
@@ -657,7 +648,7 @@ __device__ __forceinline__ void stage_ptrs(unsigned char *stage, const void *(&h
 // planes in registers (a z-queue), so a point costs four in-plane neighbour
 // reads from shared memory plus one for the next plane's centre.
 template <class Op>
-__device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c0, int c1,
+__device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c0, int kb, int ke,
                                           unsigned char *ring, uint64_t *bars, uint32_t &seq,
                                           double *sred, int *s_dead)
 {
@@ -672,7 +663,7 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
     constexpr int NHA = Op::NH > 0 ? Op::NH : 1;
     constexpr int NPA = Op::NP > 0 ? Op::NP : 1;
 
-    const int nx = D.nx, ny = D.ny, nz = D.nz, zc = D.zc;
+    const int nx = D.nx, ny = D.ny, nz = D.nz;
     const int plane = nx * ny;
     const int tid = threadIdx.x, tx = tid % TILE_X, ty = tid / TILE_X;
     const int i0 = (tile % D.tiles_x) * TILE_X, j0 = (tile / D.tiles_x) * TILE_Y;
@@ -690,8 +681,6 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
         okn = (j % D.by) != D.by - 1;
     }
     const int nbm = (HasNeumann<Op>::value && D.bcm) ? neumann_mask(D.bcm, i, j, nx, ny) : 0;
-    const int kb = c0 * zc;
-    const int ke = min(nz, c1 * zc);
     const int q0 = kb - 1, q1 = ke; // stencil-input planes q0..q1, pointwise planes kb..ke-1
     const int nplanes = q1 - q0 + 1;
     const uint32_t seq0 = seq;
@@ -774,8 +763,7 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
     int kk = 0;
     if constexpr (Op::BLOCKED) kk = kb % D.bz;
     const int ntiles = D.tiles_x * D.tiles_y;
-    int unit = c0 * ntiles + tile;
-    int cend = min(nz, (c0 + 1) * zc);
+    const int unit = c0 * ntiles + tile;
 
     for (int k = kb; k < ke; ++k) {
         wait(sn);
@@ -828,14 +816,8 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
         if constexpr (Op::BLOCKED) {
             if (++kk == D.bz) kk = 0;
         }
-        if constexpr (ND > 0) {
-            if (k + 1 == cend) {
-                flush_unit<ND>(acc, sred, D.partials, unit);
-                unit += ntiles;
-                cend = min(nz, cend + zc);
-            }
-        }
     }
+    if constexpr (ND > 0) flush_unit<ND>(acc, sred, D.partials, unit);
     // every issued plane was waited for (q1 in the last step; planes beyond q1
     // are never issued), so nothing is left in flight
     seq = seq0 + nplanes;
@@ -876,17 +858,23 @@ __device__ __forceinline__ void engine_body(const KArgs &a, EngineShared &sh)
     const int2 *ent = reinterpret_cast<const int2 *>(a.list + LIST_HDR_INTS);
     uint32_t *sched = reinterpret_cast<uint32_t *>(const_cast<int32_t *>(a.list)) + 2; // next, done
     const int G = gridDim.x;
+    // A stencil operation without dot products may split every work unit into
+    // S sub-units of consecutive planes (finer scheduling at the end of a
+    // launch); dot products keep whole units (their partials are per unit).
+    const int S = (Op::STENCIL && Op::ND == 0 && a.split > 1) ? a.split : 1;
+    const int total = hdr.total * S;
     // the first unit of a CTA is its index; the rest come from the counter
     // (never touched when the list has no more units than the launch has CTAs)
-    const bool dynamic = hdr.total > G;
+    const bool dynamic = total > G;
     int u = blockIdx.x;
     int e = 0; // list entry of the last unit taken
-    while (u < hdr.total) {
-        if (e + 1 < hdr.n && ent[e + 1].y <= u) { // the last entry whose first unit <= u
+    while (u < total) {
+        const int ub = S > 1 ? u / S : u; // the work unit
+        if (e + 1 < hdr.n && ent[e + 1].y <= ub) { // the last entry whose first unit <= ub
             int lo = e + 1, hi = hdr.n - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (ent[mid].y <= u) lo = mid;
+                if (ent[mid].y <= ub) lo = mid;
                 else hi = mid - 1;
             }
             e = lo;
@@ -900,12 +888,20 @@ __device__ __forceinline__ void engine_body(const KArgs &a, EngineShared &sh)
         if (!skip) {
             Op op(D, a, sc);
             const int ntiles = D.tiles_x * D.tiles_y;
-            const int l = u - en.y; // problem-local unit, chunk-major
+            const int l = ub - en.y; // problem-local unit, chunk-major
             const int c0 = l / ntiles;
             const int tile = l - c0 * ntiles;
             if constexpr (Op::STENCIL) {
-                if (D.tma) march_tma<Op>(op, D, tile, c0, c0 + 1, sh.dyn, sh.bars, sh.seq, sh.sred, sh.s_dead);
-                else march_stencil<Op>(op, D, tile, c0, c0 + 1, sp, sh.sred);
+                int kb = c0 * D.zc, ke = min(D.nz, kb + D.zc);
+                if (S > 1) { // sub-unit u - ub S of the unit's planes
+                    const int part = (D.zc + S - 1) / S;
+                    kb += (u - ub * S) * part;
+                    ke = min(ke, kb + part);
+                }
+                if (kb < ke) {
+                    if (D.tma) march_tma<Op>(op, D, tile, c0, kb, ke, sh.dyn, sh.bars, sh.seq, sh.sred, sh.s_dead);
+                    else march_stencil<Op>(op, D, tile, c0, kb, ke, sp, sh.sred);
+                }
             } else {
                 march_point<Op>(op, D, tile, c0, c0 + 1, sh.sred);
             }
@@ -1082,11 +1078,11 @@ struct OpCiFirst {
         tinv = (C)D.theta_inv;
         // y_1 = (2 rho_1/delta)(2u - A u / theta)
         //     = c (2 - cc/theta) u + (c/theta)(cx sx + cy sy + cz sz),  c = 2 rho_1/delta
-        const double c = D.two_over_delta * D.rho[1];
-        a_u = (C)(c * (2.0 - D.cc * D.theta_inv));
-        a_x = (C)(c * D.theta_inv * D.cx);
-        a_y = (C)(c * D.theta_inv * D.cy);
-        a_z = (C)(c * D.theta_inv * D.cz);
+        // (folded on the host)
+        a_u = (C)D.ci1[0];
+        a_x = (C)D.ci1[1];
+        a_y = (C)D.ci1[2];
+        a_z = (C)D.ci1[3];
     }
     __device__ __forceinline__ double load(int idx) const
     {
@@ -1126,7 +1122,19 @@ struct OpCiFirst {
 //   w = rho_k (2 sigma y + (2/delta)(b - A y) - rho_{k-1} z),
 // y = y_{k-1} (stencil input), z = y_{k-2} (z = b/theta when k = 2).
 // TB is the storage type of the CI right-hand side b.
-template <class T, class TB, bool BLK, bool WITH_Y = true, bool NEU = true>
+//
+// Scaled iterates (FP64 vectors only).  Written out, w is a combination of
+// b, z and the three neighbour-pair sums of y; each coefficient costs one
+// FP64 instruction, and the FP64 pipe bounds this kernel.  The intermediate
+// iterates are therefore stored as yhat_j = y_j / s_j with s_j = the
+// coefficient of b in sweep j (2 <= j < d), so that b enters with
+// coefficient exactly 1 and the sweep saves its multiply (UNIT); y_1 and the
+// last iterate y_d (p^ or r^) keep s = 1.  The other coefficients take the
+// ratios of the scales (problem_set_cheb folds them), and s_j > 0 is a fixed
+// per-sweep number (no accumulated product), so the iterates stay in range.
+// A sweep compiled without UNIT computes the same values (its b coefficient
+// is then c/c = 1).
+template <class T, class TB, bool BLK, bool WITH_Y = true, bool NEU = true, bool UNIT = false>
 struct OpCiSweep {
     using E = Elem<T>;
     using EB = Elem<TB>;
@@ -1144,6 +1152,8 @@ struct OpCiSweep {
     // NEU = false: the grid has no Neumann face, and the sweep is compiled
     // without the face handling (the FP64 sweep is at its register budget)
     static constexpr bool NEUMANN = NEU;
+    static constexpr bool SCALED = std::is_same<T, double>::value;
+    static_assert(SCALED || !UNIT, "scaled iterates are FP64 only");
     // staged form: halo box of y_{k-1}, plain boxes of b and y_{k-2}
     using TH = T;
     using TP = T;
@@ -1170,16 +1180,20 @@ struct OpCiSweep {
         // w = rho_k (2 sigma y + (2/delta)(b - A y) - rho_{k-1} z) with A y expanded:
         //   = rho_k (2 sigma - (2/delta) cc) y + rho_k (2/delta) b - rho_k rho_{k-1} z
         //     + rho_k (2/delta)(cx sx + cy sy + cz sz);  z = b/theta when k = 2
-        const double rk = D.rho[a.k], rk1 = D.rho[a.k - 1], tod = D.two_over_delta;
-        // WITH_Y = false: exact closed-form bounds, where lambda_min + lambda_max = 2 cc
-        // (Eq. 9: sin^2 a + cos^2 a = 1 per axis, for the grid and for every block), so
-        // theta = cc and the y coefficient vanishes; the kernel then skips its multiply.
-        c_y = (C)(rk * (D.two_sigma - tod * D.cc));
-        c_b = (C)(a.k == 2 ? rk * tod - rk * rk1 * D.theta_inv : rk * tod);
-        c_z = (C)(-rk * rk1);
-        c_x = (C)(rk * tod * D.cx);
-        c_yy = (C)(rk * tod * D.cy);
-        c_zz = (C)(rk * tod * D.cz);
+        // the coefficients, scaled as above, come folded from the host (the
+        // operation is built per work unit by every thread: computing them
+        // here cost the FP64 pipe several percent of the sweep).  WITH_Y =
+        // false: exact closed-form bounds, where lambda_min + lambda_max = 2 cc
+        // (Eq. 9: sin^2 a + cos^2 a = 1 per axis, for the grid and for every
+        // block), so theta = cc and the y coefficient vanishes; the kernel
+        // then skips its multiply.
+        const double *ck = D.cik[a.k];
+        c_y = (C)ck[0];
+        c_b = (C)ck[1];
+        c_z = (C)ck[2];
+        c_x = (C)ck[3];
+        c_yy = (C)ck[4];
+        c_zz = (C)ck[5];
     }
     __device__ __forceinline__ C load(int idx) const { return E::ld(y, idx); }
     __device__ __forceinline__ C load_s(const void *const *h, int x) const { return E::lds(h[0], x); }
@@ -1203,7 +1217,9 @@ struct OpCiSweep {
     __device__ __forceinline__ void emit(int idx, C yc, C sx, C sy, C sz, C, const PW &p, double (&)[NA]) const
     {
         C v;
-        if constexpr (WITH_Y) v = fma(c_b, p.b, c_y * yc);
+        if constexpr (UNIT && WITH_Y) v = fma(c_y, yc, p.b);
+        else if constexpr (UNIT) v = p.b;
+        else if constexpr (WITH_Y) v = fma(c_b, p.b, c_y * yc);
         else v = c_b * p.b;
         if (k >= 3) v = fma(c_z, p.z, v);
         E::st(out, idx, fma(c_zz, sz, fma(c_yy, sy, fma(c_x, sx, v))));

@@ -111,17 +111,27 @@ template <class Op>
 struct PersistAlias {
     using type = Op;
 };
-template <class T, class TB, bool BLK, bool WY>
-struct PersistAlias<OpCiSweep<T, TB, BLK, WY, false>> {
-    using type = OpCiSweep<T, TB, BLK, WY, true>;
+template <class T, class TB, bool BLK, bool WY, bool UNIT>
+struct PersistAlias<OpCiSweep<T, TB, BLK, WY, false, UNIT>> {
+    using type = OpCiSweep<T, TB, BLK, WY, true, UNIT>;
+};
+
+template <class L, class Op>
+struct Append;
+template <class... Ops, class Op>
+struct Append<TypeList<Ops...>, Op> {
+    using type = TypeList<Ops..., Op>;
 };
 
 template <int KIND, class T, bool BLK, bool WY>
 struct PersistOps { // Chebyshev-preconditioned iteration
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
-    using List = TypeList<OpInit0, OpResidual<true>, OpResidual<false>, OpCiFirst<T, BLK, SIDE_P>,
+    using Base = TypeList<OpInit0, OpResidual<true>, OpResidual<false>, OpCiFirst<T, BLK, SIDE_P>,
                           OpCiSweep<T, TB, BLK, WY>, OpStencilDot<T>, OpCiFirst<T, BLK, SIDE_S>, OpStencil2Dot<T>,
                           OpUpdate<T>, OpReplace>;
+    // FP64: the sweeps before the last one run the scaled-iterate form
+    using List = typename std::conditional<is_mixed<T>(), Base,
+                                           typename Append<Base, OpCiSweep<T, TB, BLK, WY, true, true>>::type>::type;
 };
 template <class T, bool BLK, bool WY>
 struct PersistOps<0, T, BLK, WY> { // unpreconditioned iteration
@@ -252,7 +262,8 @@ void table_of(const Plan &plan, bool use_x0, bool true_res, PersistState *st)
     prog_init(tb, use_x0);
     st->n_init = tb.n;
     if constexpr (KIND == 0) prog_iteration_none(tb, 2, plan.rr_every > 0);
-    else prog_iteration_cheb<T, BLK, WY>(tb, plan.degree, 2, plan.rr_every > 0, true); // one sweep kind for every grid
+    else prog_iteration_cheb<T, BLK, WY>(tb, plan.degree, 2, plan.rr_every > 0, true,
+                                         plan.split); // one sweep kind for every grid
     st->n_iter = tb.n - st->n_init;
     if (true_res) prog_true_residual(tb);
     st->n_tail = tb.n - st->n_init - st->n_iter;

@@ -34,26 +34,42 @@ __host__ __device__ void prog_replace(V &v)
     v.template go<OpReplace>(PSOLVE_K_OTHER, 2, a, 32.0);
 }
 
+// One sweep of kind (NEU, UNIT) chosen at run time.
+#pragma nv_exec_check_disable
+template <class T, class TB, bool BLK, bool WY, class V>
+__host__ __device__ void prog_sweep(V &v, int cls, int side, const KArgs &a, double bytes, bool neu, bool unit)
+{
+    constexpr bool U = !is_mixed<T>(); // the scaled-iterate form exists for FP64 vectors
+    if (neu && unit) v.template go<OpCiSweep<T, TB, BLK, WY, true, U>>(cls, side, a, bytes);
+    else if (neu) v.template go<OpCiSweep<T, TB, BLK, WY, true, false>>(cls, side, a, bytes);
+    else if (unit) v.template go<OpCiSweep<T, TB, BLK, WY, false, U>>(cls, side, a, bytes);
+    else v.template go<OpCiSweep<T, TB, BLK, WY, false, false>>(cls, side, a, bytes);
+}
+
 // Chebyshev sweeps k = 2..d (Algorithm 2 loop).  y_k overwrites y_{k-2}'s
 // buffer (read only at the same point), and the last sweep writes `final_role`.
 // neu: the grid has Neumann faces (else the sweeps compiled without them run).
+// split: sub-units per work unit (KArgs::split).
+// With FP64 vectors the sweeps k < d store scaled iterates (OpCiSweep); the
+// descriptor's degree must equal d.
 #pragma nv_exec_check_disable
 template <class T, class TB, bool BLK, bool WY, class V>
-__host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final_role, int skip, bool neu)
+__host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final_role, int skip, bool neu,
+                                     int split = 1)
 {
     const double c = sizeof(T), cb = sizeof(TB);
     for (int k = 2; k <= d; ++k) {
         KArgs a{};
         a.k = k;
         a.skip = skip;
+        a.split = split;
         a.in = (k % 2 == 0) ? ROLE_YA : ROLE_YB;
         a.z = (k % 2 == 0) ? ROLE_YB : ROLE_YA;
         a.out = (k == d) ? final_role : a.z;
         a.b = brole;
         const int cls = (k == 2) ? PSOLVE_K_CI_SWEEP3 : PSOLVE_K_CI_SWEEP4;
         const double bytes = (k == 2) ? c + cb + c : c + cb + c + c;
-        if (neu) v.template go<OpCiSweep<T, TB, BLK, WY, true>>(cls, side, a, bytes);
-        else v.template go<OpCiSweep<T, TB, BLK, WY, false>>(cls, side, a, bytes);
+        prog_sweep<T, TB, BLK, WY>(v, cls, side, a, bytes, neu, !is_mixed<T>() && k < d);
     }
 }
 
@@ -63,7 +79,7 @@ __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final
 // then, when rr, the residual replacement.
 #pragma nv_exec_check_disable
 template <class T, bool BLK, bool WY, class V>
-__host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, bool neu)
+__host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, bool neu, int split = 1)
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
@@ -77,7 +93,7 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, boo
         const double rd = (iter == 1) ? 8.0 : 24.0;
         v.template go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, rd + 8.0 + (MIX ? c : 0.0) + c);
     }
-    prog_sweeps<T, TB, BLK, WY>(v, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP, neu);
+    prog_sweeps<T, TB, BLK, WY>(v, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP, neu, split);
     {
         KArgs a{};
         a.skip = SKIP_STOP;
@@ -92,7 +108,7 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, boo
         a.out = (d <= 1) ? ROLE_RH : ROLE_YA;
         v.template go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, 24.0 + (MIX ? c : 0.0) + c);
     }
-    prog_sweeps<T, TB, BLK, WY>(v, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF, neu);
+    prog_sweeps<T, TB, BLK, WY>(v, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF, neu, split);
     {
         KArgs a{};
         a.skip = SKIP_STOP | SKIP_HALF;

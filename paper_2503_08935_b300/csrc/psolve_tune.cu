@@ -121,7 +121,7 @@ psolve_status time_candidate(Problem &P, int sms, int zc, bool tma, cudaStream_t
     // warm-up, timed once to size the measurement: enough repetitions for
     // about 300 us of work, and the best of two trials
     PS_CK(cudaEventRecord(ev[0], s));
-    enqueue_tune_probe(L, P.prec, false);
+    enqueue_tune_probe(L, P.prec, false, sweep_split(P.prec, D.zc));
     PS_CK(cudaEventRecord(ev[1], s));
     PS_CK(L.err);
     PS_CK(cudaEventSynchronize(ev[1]));
@@ -132,7 +132,7 @@ psolve_status time_candidate(Problem &P, int sms, int zc, bool tma, cudaStream_t
     double best = -1.0;
     for (int trial = 0; trial < 2; ++trial) {
         PS_CK(cudaEventRecord(ev[0], s));
-        for (int rep = 0; rep < reps; ++rep) enqueue_tune_probe(L, P.prec, false);
+        for (int rep = 0; rep < reps; ++rep) enqueue_tune_probe(L, P.prec, false, sweep_split(P.prec, D.zc));
         PS_CK(cudaEventRecord(ev[1], s));
         PS_CK(L.err);
         PS_CK(cudaEventSynchronize(ev[1]));

@@ -90,6 +90,11 @@ struct Desc {
     // Chebyshev (Eq. 15): 1/theta, 2/delta, 2 sigma and rho_0..rho_d
     double theta_inv, two_over_delta, two_sigma;
     double rho[MAX_DEGREE + 1];
+    // the same folded into per-sweep coefficients on the host, so that a
+    // kernel spends no FP64 instruction on them: CI sweep 1 (a_u, a_x, a_y,
+    // a_z) and sweep k >= 2 (c_y, c_b, c_z, c_x, c_yy, c_zz)
+    double ci1[4];
+    double cik[MAX_DEGREE + 1][6];
     void *vec[NROLES];
     Scal *sc;
     double *partials;   // units * MAX_DOTS doubles
@@ -124,6 +129,7 @@ struct KArgs {
     int32_t k;           // Chebyshev step index (sweeps)
     int32_t skip;        // SKIP_* bits
     int32_t in, b, z, out, aux; // roles used by the operation
+    int32_t split;       // stencil operations without dots: sub-units per work unit (0, 1: none)
 };
 
 constexpr int TMAPS_PER_PROBLEM = 2 * NROLES;
