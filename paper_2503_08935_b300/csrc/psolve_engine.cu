@@ -231,7 +231,9 @@ static void precond_cheb(Launcher &L, int d, bool eb, bool neu, int split)
     a.skip = 0;
     a.in = ROLE_PCUR;
     a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
-    L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
+    constexpr bool U = !MIX; // y_1 stored scaled (FP64, d >= 2)
+    if (U && d >= 2) L.go<OpCiFirst<T, BLK, SIDE_P, U>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
+    else L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
     if (eb) prog_sweeps<T, TB, BLK, false>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split);
     else prog_sweeps<T, TB, BLK, true>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split);
     KArgs w{};
@@ -556,19 +558,26 @@ psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_
     for (int k = 1; k <= MAX_DEGREE; ++k) D.rho[k] = 1.0 / (2.0 * sigma - D.rho[k - 1]);
     // CI sweep 1: y_1 = (2 rho_1/delta)(2u - A u / theta), A u written with
     // the neighbour-pair sums: A u = cc u - cx sx - cy sy - cz sz
+    // With FP64 vectors and d >= 2, y_1 is stored divided by its x-pair
+    // coefficient (> 0), s_1 below.
+    const bool scaled = P.prec == PSOLVE_FP64;
     const double tod = D.two_over_delta, c1 = tod * D.rho[1];
-    D.ci1[0] = c1 * (2.0 - D.cc * D.theta_inv);
-    D.ci1[1] = c1 * D.theta_inv * D.cx;
-    D.ci1[2] = c1 * D.theta_inv * D.cy;
-    D.ci1[3] = c1 * D.theta_inv * D.cz;
+    const double ax = c1 * D.theta_inv * D.cx;
+    const double s1 = (scaled && degree >= 2) ? ax : 1.0;
+    D.ci1[0] = c1 * (2.0 - D.cc * D.theta_inv) / s1;
+    D.ci1[1] = ax / s1; // exactly 1 when scaled
+    D.ci1[2] = c1 * D.theta_inv * D.cy / s1;
+    D.ci1[3] = c1 * D.theta_inv * D.cz / s1;
     // sweeps k >= 2: w = rho_k (2 sigma y + (2/delta)(b - A y) - rho_{k-1} z)
     //   = rho_k (2 sigma - (2/delta) cc) y + rho_k (2/delta) b - rho_k rho_{k-1} z
     //     + rho_k (2/delta)(cx sx + cy sy + cz sz),  z = b/theta when k = 2,
     // with FP64 vectors stored as yhat_j = y_j / s_j, s_j = the b coefficient
     // of sweep j for 2 <= j < d (1 otherwise), so b enters with coefficient 1
-    const bool scaled = P.prec == PSOLVE_FP64;
     auto b_coef = [&](int j) { return j == 2 ? D.rho[2] * tod - D.rho[2] * D.rho[1] * D.theta_inv : D.rho[j] * tod; };
-    auto scale = [&](int j) { return (scaled && j >= 2 && j < degree) ? b_coef(j) : 1.0; };
+    auto scale = [&](int j) {
+        if (j == 1) return s1;
+        return (scaled && j >= 2 && j < degree) ? b_coef(j) : 1.0;
+    };
     std::memset(D.cik, 0, sizeof D.cik);
     for (int k = 2; k <= degree && k <= MAX_DEGREE; ++k) {
         const double rk = D.rho[k], rk1 = D.rho[k - 1];

@@ -1027,8 +1027,12 @@ __device__ __forceinline__ C apply_A_terms(C cc, C cx, C cy, C cz, C u, C sx, C 
 //   SIDE_S: u = s = r - alpha w                          (Alg. 1) and ||s||^2
 // It writes u (FP64), the CI copy of u rounded to T (mixed precision only),
 // and z = u/theta (degree 0) or y_1 = (2 rho_1/delta)(2u - A u/theta).
+// UNIT (FP64, degree >= 2): y_1 is stored divided by its (positive)
+// coefficient of the x-pair sum, which then enters with coefficient 1 (6
+// FP64 instructions instead of 7; the sweeps take the scale into account,
+// see OpCiSweep).
 constexpr int SIDE_P = 0, SIDE_S = 1;
-template <class T, bool BLK, int SIDE>
+template <class T, bool BLK, int SIDE, bool UNIT = false>
 struct OpCiFirst {
     using E = Elem<T>;
     using C = typename E::C;
@@ -1038,6 +1042,7 @@ struct OpCiFirst {
     static constexpr int EPI = SIDE == SIDE_S ? EPI_SNORM : EPI_NONE;
     static constexpr bool STENCIL = true, BLOCKED = BLK;
     static constexpr bool MIXED = !std::is_same<T, double>::value;
+    static_assert(!UNIT || !MIXED, "scaled iterates are FP64 only");
     // staged form: halo boxes of r (and w, p_{i-2}); u is formed once per plane
     using TH = double;
     using TP = double;
@@ -1113,7 +1118,8 @@ struct OpCiFirst {
         uout[idx] = uc;
         if constexpr (SIDE == SIDE_S) acc[0] += uc * uc;
         if constexpr (MIXED) E::st(bc, idx, b);
-        if (degree == 0) E::st(out, idx, b * tinv);
+        if constexpr (UNIT) E::st(out, idx, fma(a_z, sz, fma(a_y, sy, fma(a_u, b, sx))));
+        else if (degree == 0) E::st(out, idx, b * tinv);
         else E::st(out, idx, fma(a_z, sz, fma(a_y, sy, fma(a_x, sx, a_u * b))));
     }
 };
@@ -1128,8 +1134,9 @@ struct OpCiFirst {
 // FP64 instruction, and the FP64 pipe bounds this kernel.  The intermediate
 // iterates are therefore stored as yhat_j = y_j / s_j with s_j = the
 // coefficient of b in sweep j (2 <= j < d), so that b enters with
-// coefficient exactly 1 and the sweep saves its multiply (UNIT); y_1 and the
-// last iterate y_d (p^ or r^) keep s = 1.  The other coefficients take the
+// coefficient exactly 1 and the sweep saves its multiply (UNIT); y_1 is
+// stored divided by its x-pair coefficient (OpCiFirst), and the last iterate
+// y_d (p^ or r^) keeps s = 1.  The other coefficients take the
 // ratios of the scales (problem_set_cheb folds them), and s_j > 0 is a fixed
 // per-sweep number (no accumulated product), so the iterates stay in range.
 // A sweep compiled without UNIT computes the same values (its b coefficient

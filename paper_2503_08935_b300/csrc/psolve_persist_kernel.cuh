@@ -129,9 +129,12 @@ struct PersistOps { // Chebyshev-preconditioned iteration
     using Base = TypeList<OpInit0, OpResidual<true>, OpResidual<false>, OpCiFirst<T, BLK, SIDE_P>,
                           OpCiSweep<T, TB, BLK, WY>, OpStencilDot<T>, OpCiFirst<T, BLK, SIDE_S>, OpStencil2Dot<T>,
                           OpUpdate<T>, OpReplace>;
-    // FP64: the sweeps before the last one run the scaled-iterate form
-    using List = typename std::conditional<is_mixed<T>(), Base,
-                                           typename Append<Base, OpCiSweep<T, TB, BLK, WY, true, true>>::type>::type;
+    // FP64: sweep 1 and the sweeps before the last one run the scaled-iterate form
+    using Scaled = typename Append<
+        typename Append<typename Append<Base, OpCiSweep<T, TB, BLK, WY, true, true>>::type,
+                        OpCiFirst<T, BLK, SIDE_P, true>>::type,
+        OpCiFirst<T, BLK, SIDE_S, true>>::type;
+    using List = typename std::conditional<is_mixed<T>(), Base, Scaled>::type;
 };
 template <class T, bool BLK, bool WY>
 struct PersistOps<0, T, BLK, WY> { // unpreconditioned iteration

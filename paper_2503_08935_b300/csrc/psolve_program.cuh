@@ -83,6 +83,7 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, boo
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
+    constexpr bool U = !MIX; // FP64 vectors: y_1 stored scaled when d >= 2 (OpCiFirst)
     const double c = sizeof(T);
     {
         // p side: p_{i-1} = r + beta (p_{i-2} - omega w) fused with CI sweep 1
@@ -91,7 +92,9 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, boo
         a.in = ROLE_PCUR;
         a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
         const double rd = (iter == 1) ? 8.0 : 24.0;
-        v.template go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, rd + 8.0 + (MIX ? c : 0.0) + c);
+        const double bytes = rd + 8.0 + (MIX ? c : 0.0) + c;
+        if (U && d >= 2) v.template go<OpCiFirst<T, BLK, SIDE_P, U>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
+        else v.template go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
     }
     prog_sweeps<T, TB, BLK, WY>(v, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP, neu, split);
     {
@@ -106,7 +109,9 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, boo
         a.skip = SKIP_STOP;
         a.in = ROLE_S;
         a.out = (d <= 1) ? ROLE_RH : ROLE_YA;
-        v.template go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, 24.0 + (MIX ? c : 0.0) + c);
+        const double bytes = 24.0 + (MIX ? c : 0.0) + c;
+        if (U && d >= 2) v.template go<OpCiFirst<T, BLK, SIDE_S, U>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
+        else v.template go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
     }
     prog_sweeps<T, TB, BLK, WY>(v, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF, neu, split);
     {

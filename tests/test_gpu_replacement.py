@@ -47,11 +47,14 @@ def test_replacement_matches_oracle(shape, precond, degree, rr):
     xo, ro = O.bicgstab(bn, I.default_h(shape), rtol=1e-10, maxit=500, precond=precond, degree=degree,
                         rr_every=rr)
     assert info.status == B.OK and ro.status == O.OK
-    # G(CI): +-2 iterations.  Unpreconditioned Bi-CGSTAB on these grids is
-    # rounding-sensitive (the oracle alone ends anywhere in 61..71 iterations as
-    # rr_every runs over 0..7 on the 16x18x20 grid), so the iteration-count
-    # slack of the unpreconditioned parity cases applies: max(2, 15%).
-    slack = 2 if precond == B.PC_CHEB else max(2, int(0.15 * ro.iterations))
+    # The replacement makes the stopping iteration rounding-sensitive: on the
+    # 37x19x23 grid with G(CI) d = 4 and rr_every = 3 the oracle itself stops
+    # anywhere in 29..33 iterations over 12 right-hand sides perturbed by 1e-15
+    # relative noise (32 for all of them without replacement), and
+    # unpreconditioned Bi-CGSTAB ends anywhere in 61..71 as rr_every runs over
+    # 0..7 on the 16x18x20 grid.  The solution and the true residual are the
+    # parity checks; the count may move by max(3, 20%).
+    slack = max(3, int(0.2 * ro.iterations))
     assert abs(info.iterations - ro.iterations) <= slack
     assert rel(x, xo) <= 1e-8
     assert info.rel_res_true <= 1.1e-10
