@@ -314,7 +314,9 @@ def run_gpu(args):
         gbs = per_launch / (avg_ms * 1e-3) / 1e9
         tpp = ncu_traffic_per_point(args.prec)
         ctype = {"fp64": "double", "fp32": "float", "bf16": "__nv_bfloat16"}[args.prec]
-        roof = {"kernel": f"k_engine<OpCiSweep<{ctype},{ctype},false>> (Chebyshev sweep k>=3)",
+        kname = ("k_engine<OpCiSweep<double,double,...>> (Chebyshev sweeps k>=3: scaled form for k<d, plain for k=d)"
+                 if args.prec == "fp64" else f"k_engine<OpCiSweep<{ctype},{ctype},...>> (Chebyshev sweeps k>=3)")
+        roof = {"kernel": kname,
                 "traffic": (tpp * npts) if tpp is not None else None,
                 "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms, "launches": kn,
                 "share_of_step": kms / ms if ms > 0 else None,
