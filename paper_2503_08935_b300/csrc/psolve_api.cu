@@ -686,7 +686,7 @@ static psolve_status flex_setup(psolve_ctx *c, int precond)
             Q.bc[2 * d + 1] = B[d] == nb[d] - 1 ? P.bc[2 * d + 1] : 0;
         }
         Q.prec = PSOLVE_FP64;
-        problem_geometry(Q, c->di.sms);
+        problem_geometry(Q, c->di.sms, 0, nblk); // the blocks share every launch
         offs[q] = total;
         total += problem_bytes(Q.n, PSOLVE_FP64, false, c->di.sms);
     }

@@ -371,7 +371,7 @@ double model_bytes_for(const std::vector<LaunchRec> &recs, int final_iter, int h
 // ------------------------------------------------------------- workspace --
 static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-void problem_geometry(Problem &P, int sms, int zc_choice)
+void problem_geometry(Problem &P, int sms, int zc_choice, int copies)
 {
     Desc &D = P.desc;
     D.nx = (int)P.n[0];
@@ -387,12 +387,13 @@ void problem_geometry(Problem &P, int sms, int zc_choice)
     // the deeper slab.  Over 125 grid shapes (16^3 .. 256^3, FP64 and FP32)
     // the autotuner measured this choice within 4% of the best one (geometric
     // mean).  It depends on the grid shape and the GPU only, so reductions do
-    // not depend on the batch mix.
+    // not depend on the batch mix.  `copies` equal problems that always share
+    // their launches (the blocks of BJ(BiCGS)) are counted together.
     long long zc = 1;
     double best_cost = -1.0;
     for (long long z = 1; z <= 32; z *= 2) {
         if (z > D.nz && z > 1) break;
-        const long long u = tiles * ((D.nz + z - 1) / z);
+        const long long u = (copies > 1 ? copies : 1) * tiles * ((D.nz + z - 1) / z);
         const double cost = (double)((u + 3LL * sms - 1) / (3LL * sms)) * (double)(z + 2);
         if (best_cost < 0.0 || cost <= best_cost) {
             best_cost = cost;

@@ -123,8 +123,8 @@ struct Problem {
 size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms);
 // Fill the geometry fields of P.desc from P.n, P.h, P.blocks.  The slab depth
 // (planes per unit) is zc_choice when > 0 (a tuned value, at most nz), else
-// the built-in rule.
-void problem_geometry(Problem &P, int sms, int zc_choice = 0);
+// the built-in rule, applied to `copies` such problems sharing every launch.
+void problem_geometry(Problem &P, int sms, int zc_choice = 0, int copies = 1);
 // Lay out P's workspace inside `base` (device, problem_bytes long).
 void problem_bind(Problem &P, char *base);
 // Chebyshev interval [a, b] (Eq. 9-11 times the scales) for precond.
