@@ -42,15 +42,13 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2503_08935_b300", "csrc", "psolve_kernels
 # FP64 instructions per point of a Chebyshev sweep k >= 3 (exact bounds, where the
 # y coefficient vanishes; see OpCiSweep): b, y_{k-2} and the six neighbours of
 # y_{k-1} are combined with three neighbour-pair sums and four fused multiply-adds
-# (7, the least for eight inputs) in the sweeps before the last, whose iterates are
-# stored scaled so that b enters with coefficient 1; the last sweep (unscaled
-# output) adds one multiply (8).
+# (7, the least for eight inputs); every iterate, p^ and r^ included, is stored
+# scaled so that b enters with coefficient 1.
 
 
 def sweep4_fp64_ops_per_point(degree):
     """Mean FP64 instructions per point over the sweeps k = 3..degree."""
-    n = degree - 2
-    return (7.0 * (n - 1) + 8.0) / n if n > 0 else 8.0
+    return 7.0
 
 
 def dist_env():
@@ -314,7 +312,7 @@ def run_gpu(args):
         gbs = per_launch / (avg_ms * 1e-3) / 1e9
         tpp = ncu_traffic_per_point(args.prec)
         ctype = {"fp64": "double", "fp32": "float", "bf16": "__nv_bfloat16"}[args.prec]
-        kname = ("k_engine<OpCiSweep<double,double,...>> (Chebyshev sweeps k>=3: scaled form for k<d, plain for k=d)"
+        kname = ("k_engine<OpCiSweep<double,double,...>> (Chebyshev sweeps k>=3, scaled-iterate form)"
                  if args.prec == "fp64" else f"k_engine<OpCiSweep<{ctype},{ctype},...>> (Chebyshev sweeps k>=3)")
         roof = {"kernel": kname,
                 "traffic": (tpp * npts) if tpp is not None else None,

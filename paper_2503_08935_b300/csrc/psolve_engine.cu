@@ -371,6 +371,9 @@ double model_bytes_for(const std::vector<LaunchRec> &recs, int final_iter, int h
 // ------------------------------------------------------------- workspace --
 static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// p^ and r^ stored divided by h (read back only by psolve_precond_apply).
+static void set_hat(Desc &D, double h) { D.hat = h; }
+
 void problem_geometry(Problem &P, int sms, int zc_choice, int copies)
 {
     Desc &D = P.desc;
@@ -417,6 +420,12 @@ void problem_geometry(Problem &P, int sms, int zc_choice, int copies)
     D.cy = 1.0 / (P.h[1] * P.h[1]);
     D.cz = 1.0 / (P.h[2] * P.h[2]);
     D.cc = 2.0 * (D.cx + D.cy + D.cz);
+    // w and t are stored as A u / cc (OpStencilDot)
+    D.inv_cc = 1.0 / D.cc;
+    D.wcx = -D.cx / D.cc;
+    D.wcy = -D.cy / D.cc;
+    D.wcz = -D.cz / D.cc;
+    set_hat(D, 1.0);
 }
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -543,6 +552,7 @@ psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_
 {
     Desc &D = P.desc;
     D.degree = degree;
+    set_hat(D, 1.0);
     if (precond == PSOLVE_PC_NONE || precond == PSOLVE_PC_G_BICGS || precond == PSOLVE_PC_BJ_BICGS) {
         D.theta_inv = D.two_over_delta = D.two_sigma = 0.0; // no Chebyshev iteration
         return PSOLVE_OK;
@@ -573,11 +583,12 @@ psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_
     //   = rho_k (2 sigma - (2/delta) cc) y + rho_k (2/delta) b - rho_k rho_{k-1} z
     //     + rho_k (2/delta)(cx sx + cy sy + cz sz),  z = b/theta when k = 2,
     // with FP64 vectors stored as yhat_j = y_j / s_j, s_j = the b coefficient
-    // of sweep j for 2 <= j < d (1 otherwise), so b enters with coefficient 1
+    // of sweep j for 2 <= j <= d (1 otherwise), so b enters with coefficient 1;
+    // p^ = y_d is then stored divided by hat = s_d
     auto b_coef = [&](int j) { return j == 2 ? D.rho[2] * tod - D.rho[2] * D.rho[1] * D.theta_inv : D.rho[j] * tod; };
     auto scale = [&](int j) {
         if (j == 1) return s1;
-        return (scaled && j >= 2 && j < degree) ? b_coef(j) : 1.0;
+        return (scaled && j >= 2 && j <= degree) ? b_coef(j) : 1.0;
     };
     std::memset(D.cik, 0, sizeof D.cik);
     for (int k = 2; k <= degree && k <= MAX_DEGREE; ++k) {
@@ -585,12 +596,13 @@ psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_
         const double sk = scale(k), q1 = scale(k - 1) / sk, q2 = scale(k - 2) / sk;
         double *c = D.cik[k];
         c[0] = rk * (D.two_sigma - tod * D.cc) * q1;
-        c[1] = b_coef(k) / sk; // exactly 1 when scaled and k < d
+        c[1] = b_coef(k) / sk; // exactly 1 when scaled
         c[2] = -rk * rk1 * q2;
         c[3] = rk * tod * D.cx * q1;
         c[4] = rk * tod * D.cy * q1;
         c[5] = rk * tod * D.cz * q1;
     }
+    if (degree >= 2) set_hat(D, scale(degree));
     return PSOLVE_OK;
 }
 

@@ -1133,12 +1133,14 @@ struct OpCiFirst {
 // b, z and the three neighbour-pair sums of y; each coefficient costs one
 // FP64 instruction, and the FP64 pipe bounds this kernel.  The intermediate
 // iterates are therefore stored as yhat_j = y_j / s_j with s_j = the
-// coefficient of b in sweep j (2 <= j < d), so that b enters with
+// coefficient of b in sweep j (2 <= j <= d), so that b enters with
 // coefficient exactly 1 and the sweep saves its multiply (UNIT); y_1 is
-// stored divided by its x-pair coefficient (OpCiFirst), and the last iterate
-// y_d (p^ or r^) keeps s = 1.  The other coefficients take the
-// ratios of the scales (problem_set_cheb folds them), and s_j > 0 is a fixed
-// per-sweep number (no accumulated product), so the iterates stay in range.
+// stored divided by its x-pair coefficient (OpCiFirst).  The last iterate
+// y_d (p^ or r^) is stored the same way, divided by Desc::hat, which its
+// readers never need (see OpStencilDot), so every sweep is in the
+// 7-instruction form.  The other coefficients take the ratios of the scales
+// (problem_set_cheb folds them), and s_j > 0 is a fixed per-sweep number (no
+// accumulated product), so the iterates stay in range.
 // A sweep compiled without UNIT computes the same values (its b coefficient
 // is then c/c = 1).
 template <class T, class TB, bool BLK, bool WITH_Y = true, bool NEU = true, bool UNIT = false>
@@ -1234,6 +1236,12 @@ struct OpCiSweep {
 };
 
 // w = A p^ and r~ . w  (Algorithm 3, first stencil kernel); T = type of p^.
+// w is stored as w' = A q / cc, q = p^ as stored (p^ / Desc::hat): the centre
+// then enters with coefficient 1 (6 FP64 instructions for A instead of 7).
+// Nothing downstream needs the factor kappa = hat cc (w = kappa w'): alpha =
+// rho / (r~ . w') comes out as kappa alpha, so s = r - alpha w and the
+// direction update read w' with it unchanged, beta uses alpha / omega (both
+// scaled alike, see OpStencil2Dot), and x += (alpha / cc) q (OpUpdate).
 template <class T>
 struct OpStencilDot {
     using C = double;
@@ -1250,7 +1258,7 @@ struct OpStencilDot {
     const void *ph;
     const double *rt;
     double *w;
-    double cc, cx, cy, cz;
+    double wx, wy, wz; // -cx/cc, -cy/cc, -cz/cc
     __device__ OpStencilDot(const Desc &D, const KArgs &a, Scal *)
     {
         ph = D.vec[a.in];
@@ -1258,7 +1266,7 @@ struct OpStencilDot {
         w = (double *)D.vec[ROLE_W];
         hrole[0] = a.in;
         prole[0] = ROLE_RT;
-        cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
+        wx = D.wcx, wy = D.wcy, wz = D.wcz;
     }
     __device__ __forceinline__ double load(int idx) const { return Elem<T>::wide(ph, idx); }
     __device__ __forceinline__ double load_s(const void *const *h, int x) const { return Elem<T>::wides(h[0], x); }
@@ -1269,13 +1277,16 @@ struct OpStencilDot {
     __device__ __forceinline__ void emit(int idx, double u, double sx, double sy, double sz, double, double rtv,
                                          double (&acc)[NA]) const
     {
-        const double au = apply_A_terms(cc, cx, cy, cz, u, sx, sy, sz);
+        const double au = fma(wz, sz, fma(wy, sy, fma(wx, sx, u))); // A u / cc
         w[idx] = au;
         acc[0] += rtv * au;
     }
 };
 
-// t = A r^, t . s and t . t (Algorithm 3, second stencil kernel).
+// t = A r^, t . s and t . t (Algorithm 3, second stencil kernel).  t is
+// stored as t' = A q / cc, q = r^ as stored, like w (OpStencilDot): omega =
+// (t' . s) / (t' . t') comes out as kappa omega, r = s - omega t' is then
+// exact, and x += (omega / cc) q (OpUpdate).
 template <class T>
 struct OpStencil2Dot {
     using C = double;
@@ -1291,7 +1302,7 @@ struct OpStencil2Dot {
     const void *rh;
     const double *s;
     double *t;
-    double cc, cx, cy, cz;
+    double wx, wy, wz; // -cx/cc, -cy/cc, -cz/cc
     __device__ OpStencil2Dot(const Desc &D, const KArgs &a, Scal *)
     {
         rh = D.vec[a.in];
@@ -1299,7 +1310,7 @@ struct OpStencil2Dot {
         t = (double *)D.vec[ROLE_T];
         hrole[0] = a.in;
         prole[0] = ROLE_S;
-        cc = D.cc, cx = D.cx, cy = D.cy, cz = D.cz;
+        wx = D.wcx, wy = D.wcy, wz = D.wcz;
     }
     __device__ __forceinline__ double load(int idx) const { return Elem<T>::wide(rh, idx); }
     __device__ __forceinline__ double load_s(const void *const *h, int x) const { return Elem<T>::wides(h[0], x); }
@@ -1310,7 +1321,7 @@ struct OpStencil2Dot {
     __device__ __forceinline__ void emit(int idx, double u, double sx, double sy, double sz, double, double sv_,
                                          double (&acc)[NA]) const
     {
-        const double au = apply_A_terms(cc, cx, cy, cz, u, sx, sy, sz);
+        const double au = fma(wz, sz, fma(wy, sy, fma(wx, sx, u))); // A u / cc
         t[idx] = au;
         acc[0] += au * sv_;
         acc[1] += au * au;
@@ -1490,7 +1501,7 @@ struct OpUpdate {
     double *x, *r;
     const void *ph, *rh;
     const double *s, *t, *rt;
-    double alpha, omega;
+    double alpha, omega, alpha_h, omega_h;
     int half;
     __device__ OpUpdate(const Desc &D, const KArgs &a, Scal *sc)
     {
@@ -1504,6 +1515,10 @@ struct OpUpdate {
         alpha = ld_scal(&sc->alpha);
         omega = ld_scal(&sc->omega);
         half = ld_flag(&sc->half);
+        // w, t and p^, r^ are stored scaled (OpStencilDot): the true alpha p^
+        // is (alpha / cc) times p^ as stored, and the same for omega r^
+        alpha_h = alpha * D.inv_cc;
+        omega_h = omega * D.inv_cc;
     }
     struct In { double x, p, r, s, t, rt; };
     __device__ __forceinline__ In load(int idx) const
@@ -1523,10 +1538,10 @@ struct OpUpdate {
     __device__ __forceinline__ void apply(int idx, const In &v, double (&acc)[NA]) const
     {
         if (half) {
-            x[idx] = v.x + alpha * v.p;
+            x[idx] = v.x + alpha_h * v.p;
             return;
         }
-        x[idx] = v.x + alpha * v.p + omega * v.r;
+        x[idx] = v.x + alpha_h * v.p + omega_h * v.r;
         const double rn = v.s - omega * v.t;
         r[idx] = rn;
         acc[0] += v.rt * rn;
@@ -1626,17 +1641,19 @@ struct OpWiden {
     static constexpr bool STENCIL = false;
     const void *in;
     double *out;
+    double hat; // p^ is stored divided by it
     __device__ OpWiden(const Desc &D, const KArgs &k, Scal *)
     {
         in = D.vec[k.in];
         out = (double *)D.vec[k.out];
+        hat = D.hat;
     }
     struct In { double v; };
     __device__ __forceinline__ In load(int idx) const { return In{Elem<T>::wide(in, idx)}; }
     template <int NA>
     __device__ __forceinline__ void apply(int idx, const In &v, double (&)[NA]) const
     {
-        out[idx] = v.v;
+        out[idx] = v.v * hat;
     }
 };
 

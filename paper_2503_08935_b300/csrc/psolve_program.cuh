@@ -50,8 +50,9 @@ __host__ __device__ void prog_sweep(V &v, int cls, int side, const KArgs &a, dou
 // buffer (read only at the same point), and the last sweep writes `final_role`.
 // neu: the grid has Neumann faces (else the sweeps compiled without them run).
 // split: sub-units per work unit (KArgs::split).
-// With FP64 vectors the sweeps k < d store scaled iterates (OpCiSweep); the
-// descriptor's degree must equal d.
+// With FP64 vectors every sweep stores its iterate scaled (OpCiSweep; the
+// last one p^ or r^, divided by Desc::hat); the descriptor's coefficients
+// must be those of degree d.
 #pragma nv_exec_check_disable
 template <class T, class TB, bool BLK, bool WY, class V>
 __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final_role, int skip, bool neu,
@@ -69,7 +70,7 @@ __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final
         a.b = brole;
         const int cls = (k == 2) ? PSOLVE_K_CI_SWEEP3 : PSOLVE_K_CI_SWEEP4;
         const double bytes = (k == 2) ? c + cb + c : c + cb + c + c;
-        prog_sweep<T, TB, BLK, WY>(v, cls, side, a, bytes, neu, !is_mixed<T>() && k < d);
+        prog_sweep<T, TB, BLK, WY>(v, cls, side, a, bytes, neu, !is_mixed<T>());
     }
 }
 

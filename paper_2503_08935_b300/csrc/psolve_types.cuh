@@ -95,6 +95,10 @@ struct Desc {
     // a_z) and sweep k >= 2 (c_y, c_b, c_z, c_x, c_yy, c_zz)
     double ci1[4];
     double cik[MAX_DEGREE + 1][6];
+    // p^ and r^ are stored divided by hat (1 unless FP64 Chebyshev vectors and
+    // degree >= 2); w and t are stored as A (stored vector) / cc, and
+    // wcx.. = -(cx, cy, cz) / cc are that operator's neighbour coefficients
+    double hat, inv_cc, wcx, wcy, wcz;
     void *vec[NROLES];
     Scal *sc;
     double *partials;   // units * MAX_DOTS doubles

@@ -85,11 +85,12 @@ def test_flexible_solve_matches_oracle(bc, precond, blocks, inner_rtol):
     xo, ro = O.bicgstab(bn, h, rtol=1e-10, maxit=500, precond=precond, blocks=blocks, bc=bc,
                         inner_rtol=inner_rtol, inner_maxit=500)
     assert info.status == B.OK and ro.status == O.OK
-    # a loose inner tolerance makes the preconditioner depend on where each
-    # inner solve crosses its test, so rounding alone moves the outer count: on
-    # the mixed-face BJ case at 1e-3 the oracle itself takes 33 to 44
-    # iterations over 30 right-hand sides perturbed by 1e-15 relative noise
-    slack = 1 if inner_rtol <= 1e-6 else max(2, int(0.5 * ro.iterations))
+    # the preconditioner depends on where each inner solve crosses its test,
+    # so rounding alone moves the outer count: over right-hand sides perturbed
+    # by 1e-15 relative noise the oracle itself takes 23 to 25 iterations on
+    # the Dirichlet BJ case at 1e-6 (12 of them) and 33 to 44 on the
+    # mixed-face BJ case at 1e-3 (30 of them)
+    slack = max(2, int(0.1 * ro.iterations)) if inner_rtol <= 1e-6 else max(2, int(0.5 * ro.iterations))
     assert abs(info.iterations - ro.iterations) <= slack, (info.iterations, ro.iterations)
     assert info.inner_iterations >= info.iterations
     assert rel(x.cpu().numpy(), xo) <= 1e-8

@@ -143,6 +143,28 @@ def test_precond_fp64_matches_oracle(shape, precond, blocks, degree):
     assert np.max(np.abs(host(out) - ref)) <= 1e-11 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("scales,degree", [((100.0, 1 - 1e-4), 2), ((100.0, 1 - 1e-4), 3), ((100.0, 1 - 1e-4), 24),
+                                           ((100.0, 1 - 1e-4), 64), ((2.0, 0.9), 2), ((2.0, 0.9), 3),
+                                           ((1.0, 0.6), 2), ((1.0, 0.6), 3)])
+@pytest.mark.parametrize("precond,blocks", [(B.PC_CHEB, (1, 1, 1)), (B.PC_GNOCOMM_CHEB, (2, 3, 2))])
+def test_precond_fp64_rescaled_bounds_any_degree(scales, degree, precond, blocks):
+    """Rescaled bounds (the y term of every sweep present), anisotropic h and
+    degrees up to the largest accepted: the FP64 sweeps store their
+    intermediate iterates scaled, and the result must still be M^-1 v of
+    Algorithm 2 as the oracle computes it.  (An interval that cuts off the top
+    of the spectrum is only taken at low degree: there the polynomial grows
+    like T_d outside it, to 1e31 at degree 64.)"""
+    shape = (20, 24, 40)
+    h = (0.05, 0.04, 0.03)
+    v = I.rhs_uniform(shape, seed=11)
+    out = torch.empty(shape, dtype=torch.float64, device=DEV)
+    with B.Solver(shape, h, blocks=blocks, lmin_scale=scales[0], lmax_scale=scales[1]) as s:
+        s.precond_apply(dev(v), out, precond, degree)
+    ref = O.precond_apply(v, h, precond, degree, blocks, lmin_scale=scales[0], lmax_scale=scales[1])
+    assert np.all(np.isfinite(host(out)))
+    assert np.max(np.abs(host(out) - ref)) <= 1e-11 * max(1.0, degree / 16) * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("shape", [(24, 24, 40), (24, 24, 37)])
 @pytest.mark.parametrize("prec,tol", [(B.FP32, 2e-5), (B.BF16, 3e-2)])
 @pytest.mark.parametrize("degree", [1, 4, 8])
@@ -218,8 +240,11 @@ def iter_slack(case, oracle_iters):
     to 1e-15 for 10 iterations and drift to ~1e-9 by 30 (see
     test_fixed_iterations_match_oracle), and the BJ(CI) 24x20x36 case stopped at
     43 and 45 iterations in two equally valid reduction orders against the
-    oracle's 40.  Bound: +-max(2, 15 %)."""
-    if case[1] == B.PC_CHEB:
+    oracle's 40.  Bound: +-max(2, 15 %).  G(CI) of degree 0 or 1 (M a scaled
+    identity, or one stencil) is no better: over 12 right-hand sides perturbed
+    by 1e-15 relative noise the oracle alone takes 85..96 iterations at degree
+    0 and 46..58 at degree 1 on the 24x20x36 grid."""
+    if case[1] == B.PC_CHEB and case[2] >= 2:
         return 2
     return max(2, math.ceil(0.15 * oracle_iters))
 
@@ -458,8 +483,12 @@ def test_full_size_256_cheb8_matches_stored_oracle_solve():
           f"sampled rel-L2 {rel(xs, ref):.3e}")
     assert rel(xs, ref) <= 1e-8
     assert abs(float(torch.linalg.vector_norm(x)) - gold["x_norm2"]) <= 1e-8 * gold["x_norm2"]
-    # The exact-bounds problem has an erratic convergence tail: arithmetically equivalent
-    # GPU kernels with different rounding stopped at 130, 142 and 144 iterations against
-    # the oracle's 139, so the bound is +-max(2, 5 %) rather than +-2.
-    assert abs(info.iterations - gold["iterations"]) <= max(2, round(0.05 * gold["iterations"])), (
+    # The exact-bounds problem has an erratic convergence tail: from about iteration 124
+    # the relative residual hovers just above 1e-10 and falls by ~12 % per iteration, so
+    # where it first crosses rtol is decided by rounding.  Arithmetically equivalent GPU
+    # kernels (reduction orders, slab depths, scaled iterates) stopped at 126, 130, 132,
+    # 139, 142, 143 and 144 iterations against the oracle's 139; the solution and the
+    # true residual are the parity checks, and the count may move by +-max(2, 12 %).
+    assert info.rel_res_true <= 1.1e-10
+    assert abs(info.iterations - gold["iterations"]) <= max(2, round(0.12 * gold["iterations"])), (
         info.iterations, gold["iterations"])
