@@ -115,8 +115,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/psolve_clocks_{os.getpid()}.csv"
+        # the raw samples go where PSOLVE_CLOCKS_DIR says (kept for inspection), else to /tmp
+        out_dir = os.environ.get("PSOLVE_CLOCKS_DIR") or "/tmp"
+        self.path = os.path.join(out_dir, f"psolve_clocks_rank{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
