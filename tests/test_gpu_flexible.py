@@ -160,3 +160,23 @@ def test_flexible_argument_checks():
             s.solve(b, x, rtol=1e-8, maxit=100, precond=B.PC_BJ_BICGS)
     with pytest.raises(B.PsolveError):
         B.solve_batch([b], [x], rtol=1e-8, maxit=100, precond=B.PC_G_BICGS, degree=0)
+
+
+def test_flexible_solve_from_initial_guess():
+    """x0 != 0: the outer iteration starts from r0 = b - A x0 (r~ = r0 kept in its
+    own buffer); the inner solves still start from zero."""
+    shape = (16, 24, 32)
+    h = (0.05, 0.06, 0.07)
+    bn = I.rhs_uniform(shape, seed=907)
+    x0 = 1e-3 * I.rhs_uniform(shape, seed=908)
+    x = dev(x0)
+    with B.Solver(shape, h, use_x0=1, blocks=(2, 2, 2), inner_rtol=1e-6, inner_maxit=500) as s:
+        info = s.solve(dev(bn), x, rtol=1e-10, maxit=500, precond=B.PC_BJ_BICGS)
+    torch.cuda.synchronize()
+    xo, ro = O.bicgstab(bn, h, rtol=1e-10, maxit=500, precond=O.PC_BJ_BICGS, blocks=(2, 2, 2), x0=x0,
+                        inner_rtol=1e-6, inner_maxit=500)
+    assert info.status == B.OK and ro.status == O.OK
+    assert abs(info.iterations - ro.iterations) <= max(2, int(0.1 * ro.iterations)), (info.iterations,
+                                                                                     ro.iterations)
+    assert rel(x.cpu().numpy(), xo) <= 1e-8
+    assert info.rel_res_true <= 1.1e-10
