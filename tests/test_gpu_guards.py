@@ -1,0 +1,101 @@
+"""Poisoned guard regions around the caller's vectors: b and x are views into
+larger device buffers whose margins hold a sentinel pattern, and after every
+form of solve (both stencil engines, block preconditioners, mixed precision,
+the persistent launch, the flexible preconditioners, the host-buffer entry
+point's device copies aside) the margins and b are bitwise unchanged.  A stray
+store one element outside a vector, or into the read-only right-hand side,
+fails here."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2503_08935_b300 import binding as B
+from paper_2503_08935_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+G = 4096  # guard elements on each side (32 KB; keeps the views 16-byte aligned)
+SENTINEL = -7.25e300
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.lib()
+
+
+def guarded(values):
+    """A device buffer [guard | values | guard]; returns (buffer, view of values)."""
+    n = values.size
+    buf = torch.full((n + 2 * G,), SENTINEL, dtype=torch.float64, device=DEV)
+    buf[G:G + n] = torch.from_numpy(np.ascontiguousarray(values).ravel()).to(DEV)
+    return buf, buf[G:G + n].view(values.shape)
+
+
+def margins_intact(buf, n):
+    return bool(torch.all(buf[:G] == SENTINEL)) and bool(torch.all(buf[G + n:] == SENTINEL))
+
+
+CASES = [
+    ((24, 20, 40), B.PC_CHEB, 8, (1, 1, 1), {}),                       # TMA ring engine
+    ((23, 19, 37), B.PC_CHEB, 6, (1, 1, 1), {}),                       # general engine (nx % 8 != 0)
+    ((24, 20, 40), B.PC_BJ_CHEB, 4, (2, 2, 2), {}),
+    ((24, 20, 40), B.PC_GNOCOMM_CHEB, 4, (2, 2, 2), {"cheb_prec": B.FP32}),
+    ((24, 20, 40), B.PC_CHEB, 6, (1, 1, 1), {"cheb_prec": B.BF16}),
+    ((24, 20, 40), B.PC_CHEB, 6, (1, 1, 1), {"persistent": 1}),
+    ((24, 20, 40), B.PC_NONE, 0, (1, 1, 1), {"rr_every": 3}),
+    ((24, 20, 40), B.PC_BJ_BICGS, 0, (2, 2, 2), {"inner_rtol": 1e-4}),
+    ((24, 20, 40), B.PC_CHEB, 8, (1, 1, 1), {"use_x0": 1}),
+]
+
+
+@pytest.mark.parametrize("shape,precond,degree,blocks,kw", CASES)
+def test_solve_writes_only_x(shape, precond, degree, blocks, kw):
+    bn = I.rhs_uniform(shape, seed=1301)
+    x0 = 1e-3 * I.rhs_uniform(shape, seed=1302) if kw.get("use_x0") else np.zeros(shape)
+    n = bn.size
+    bbuf, b = guarded(bn)
+    xbuf, x = guarded(x0)
+    with B.Solver(shape, blocks=blocks, **kw) as s:
+        info = s.solve(b, x, rtol=1e-8, maxit=300, precond=precond, degree=degree, raise_on_error=False)
+    torch.cuda.synchronize()
+    assert info.status in (B.OK, B.NOT_CONVERGED)
+    assert margins_intact(bbuf, n) and margins_intact(xbuf, n)
+    assert np.array_equal(b.cpu().numpy(), bn)  # the right-hand side is read only
+    assert bool(torch.all(torch.isfinite(x)))
+
+
+def test_building_blocks_write_only_their_output():
+    shape = (24, 20, 40)
+    v = I.rhs_uniform(shape, seed=1303)
+    n = v.size
+    vbuf, vv = guarded(v)
+    obuf, out = guarded(np.zeros(shape))
+    with B.Solver(shape, blocks=(2, 2, 2)) as s:
+        s.apply_A(vv, out, block_restricted=1)
+        s.precond_apply(vv, out, B.PC_GNOCOMM_CHEB, 8)
+        s.precond_apply(vv, out, B.PC_BJ_BICGS, 0)
+        s.dot(vv, out)
+    torch.cuda.synchronize()
+    assert margins_intact(vbuf, n) and margins_intact(obuf, n)
+    assert np.array_equal(vv.cpu().numpy(), v)
+
+
+def test_batch_writes_only_each_x():
+    shapes = [(24, 20, 40), (17, 9, 33), (8, 40, 16)]
+    bufs, bs, xs, bns = [], [], [], []
+    for q, sh in enumerate(shapes):
+        bn = I.rhs_uniform(sh, seed=1310 + q)
+        bb, b = guarded(bn)
+        xb, x = guarded(np.zeros(sh))
+        bufs.append((bb, xb, bn.size))
+        bs.append(b)
+        xs.append(x)
+        bns.append(bn)
+    infos = B.solve_batch(bs, xs, rtol=1e-8, maxit=300, precond=B.PC_CHEB, degree=6)
+    torch.cuda.synchronize()
+    for q, (bb, xb, n) in enumerate(bufs):
+        assert infos[q].status == B.OK
+        assert margins_intact(bb, n) and margins_intact(xb, n)
+        assert np.array_equal(bs[q].cpu().numpy(), bns[q])
