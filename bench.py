@@ -539,11 +539,11 @@ def extra_serve(B, I, torch, stream, n_req, factors=(0.8,), budget=120e9, max_sl
     torch.cuda.synchronize()
     out = {"workload": f"{n_req} requests, sides log-uniform [16,256] (seed 3), FP32 Chebyshev d=8, rtol 1e-8, "
                        f"budget {budget / 1e9:.0f} GB", "mean_points": float(np.mean([b.numel() for b in bs]))}
-    with B.Server(budget, max_slots=max_slots, precond=B.PC_CHEB, degree=8, cheb_prec=B.FP32,
+    with B.Server(budget, max_slots=max_slots,
                   stream=stream) as srv:
         ncal = min(200, n_req)
         t0 = time.perf_counter()
-        ts = [srv.submit(bs[q], xs[q], rtol=1e-8, maxit=2000) for q in range(ncal)]
+        ts = [srv.submit(bs[q], xs[q], rtol=1e-8, maxit=2000, precond=B.PC_CHEB, degree=8, cheb_prec=B.FP32) for q in range(ncal)]
         for t in ts:
             srv.wait(t)
         mu = ncal / (time.perf_counter() - t0)
@@ -557,7 +557,7 @@ def extra_serve(B, I, torch, stream, n_req, factors=(0.8,), budget=120e9, max_sl
                 delay = start + arrivals[q] - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
-                tickets.append(srv.submit(bs[q], xs[q], rtol=1e-8, maxit=2000))
+                tickets.append(srv.submit(bs[q], xs[q], rtol=1e-8, maxit=2000, precond=B.PC_CHEB, degree=8, cheb_prec=B.FP32))
             infos = [srv.wait(t, timeout=600) for t in tickets]
             wall = time.perf_counter() - start
             lat = np.array([i.seconds for i in infos]) * 1e3

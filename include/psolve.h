@@ -130,7 +130,17 @@ typedef struct {
                                 0: built-in rule.                            */
     int32_t inner_maxit;     /* G(BiCGS) / BJ(BiCGS): inner iteration limit
                                 (default 500)                                */
-    int32_t reserved_;
+    int32_t record_history;  /* 1: psolve_solve records the relative residual
+                                norms ||s_i||/||b|| (after the alpha half step)
+                                and ||r_i||/||b|| (after the update) of every
+                                outer iteration i of Algorithm 1 -- the
+                                convergence history the paper plots -- for
+                                psolve_history.  The device writes one double
+                                per norm from the reduction that computes it
+                                (no extra pass, no host round trip); the
+                                context keeps a buffer of 2 * maxit doubles,
+                                grown when a solve asks for more iterations.
+                                Contexts only (not batch or server).         */
     double inner_rtol;       /* and inner relative tolerance; 0 = the
                                 experimental set-up's 1e-2 for G(BiCGS) and
                                 1e-6 for BJ(BiCGS)                           */
@@ -139,7 +149,8 @@ typedef struct {
 /* Fill *o with the defaults: scales 1, 1; blocks 1,1,1; FP64; half-step check
  * on; x0 = 0; poll auto; graphs on; timing off; true residual on; rr off;
  * engine auto; per-kernel launches (persistent off); autotune off; inner
- * solves (G(BiCGS), BJ(BiCGS)) at the set-up's tolerances, 500 iterations. */
+ * solves (G(BiCGS), BJ(BiCGS)) at the set-up's tolerances, 500 iterations;
+ * no residual history. */
 PSOLVE_API void psolve_opts_default(psolve_opts *o);
 
 /* Kernel classes reported by timing mode (psolve_result.kclass_*). */
@@ -208,7 +219,12 @@ PSOLVE_API psolve_status psolve_create(const int64_t grid[3], const double h[3],
  *   maxit >= 0.
  *   precond : psolve_precond; degree = Chebyshev iterations d of Algorithm 2
  *             (0 <= d <= 64; = number of A applications; 0 gives b/theta).
- *             Ignored by G(BiCGS) and BJ(BiCGS).
+ *             Ignored by G(BiCGS) and BJ(BiCGS).  For GNoComm(CI) the paper
+ *             bounds useful degrees by N_s/2, N_s the block side (beyond it
+ *             the error from the frozen block ghosts has reached every point):
+ *             a degree above half the smallest block side still runs, and
+ *             psolve_last_error() then holds a "warning: ..." message while
+ *             the status is that of the solve.
  * G(BiCGS) / BJ(BiCGS) run the flexible Bi-CGSTAB: x is updated with the
  * preconditioned vectors themselves, each an inner Bi-CGSTAB solve from x0 = 0
  * with the half-step test, stopped at opts.inner_rtol or opts.inner_maxit (an
@@ -223,6 +239,21 @@ PSOLVE_API psolve_status psolve_create(const int64_t grid[3], const double h[3],
  * scaled lambda_max), or a flexible form with an option it does not take. */
 PSOLVE_API psolve_status psolve_solve(psolve_ctx *ctx, const double *rhs_dev, double *x_dev, double rtol,
                            int32_t maxit, int32_t precond, int32_t degree, psolve_result *res);
+
+/* Residual history of the context's last psolve_solve, recorded when the
+ * context was created with opts.record_history = 1 (Algorithm 1's relative
+ * residuals, the quantity of the paper's convergence plots).  Copies
+ * min(*count, capacity) entries into the host arrays (either may be NULL):
+ *   rel_s[i-1] = ||s_i||/||b||, the half-step residual of outer iteration i;
+ *   rel_r[i-1] = ||r_i||/||b||, the residual after its update (the true
+ *                residual b - A x when residual replacement ran at i);
+ * NaN where iteration i did not produce the value (after a half-step exit
+ * there is no r_i; a solve that stopped on a breakdown leaves later entries).
+ * *count = the last solve's iteration count.  PSOLVE_E_ARG without
+ * record_history, before the first solve, or after a Chebyshev
+ * psolve_precond_apply (which reuses the solve's scalar state). */
+PSOLVE_API psolve_status psolve_history(psolve_ctx *ctx, int32_t capacity, double *rel_s, double *rel_r,
+                                        int32_t *count);
 
 /* The same solve from HOST memory: copies rhs_host (n doubles) to the device,
  * solves, and copies x back to x_host (n doubles; read as x0 when
@@ -259,7 +290,8 @@ PSOLVE_API psolve_status psolve_dot(psolve_ctx *ctx, const double *a_dev, const 
 PSOLVE_API psolve_status psolve_cheb_interval(psolve_ctx *ctx, int32_t precond, double *a, double *b);
 
 /* *result_host = a . b over a grid of grid[3] = (nx, ny, nz) points, the same
- * deterministic reduction as psolve_dot, without any context and without
+ * deterministic reduction as psolve_dot of a context created without
+ * opts.autotune (bitwise the same value), without any context and without
  * allocating device memory.  The paper has no counterpart: this exists for
  * callers that must not allocate, e.g. code running while a framework's
  * caching allocator or a serving process owns the device memory budget, or
@@ -268,10 +300,12 @@ PSOLVE_API psolve_status psolve_cheb_interval(psolve_ctx *ctx, int32_t precond, 
  * fixed 4 MiB device array inside the library, held by every GPU that loads
  * it until the process exits; grids whose partial sums do not fit (more than
  * about 2.6e5 work units: a unit is a 32 x 8 tile of columns times up to 32
- * planes, so very flat grids reach the limit first) return PSOLVE_E_ARG.  The first
- * call on a device looks the array's address up (cudaGetSymbolAddress) and
- * should come before any stream capture.  All calls share the array: calls
- * that overlap on the GPU (other streams, other host threads) race.  a_dev,
+ * planes, so very flat grids reach the limit first) return PSOLVE_E_ARG.  Every
+ * call looks the array's address up on the current device
+ * (cudaGetSymbolAddress), stages its small descriptor from host memory and
+ * waits for the result, so no call can be made inside a stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams, other
+ * host threads) race.  a_dev,
  * b_dev: device vectors of nx*ny*nz doubles; work is ordered on `stream`
  * and the call returns after the result is copied to *result_host. */
 PSOLVE_API psolve_status psolve_dot_noalloc(const int64_t grid[3], const double *a_dev,
@@ -328,24 +362,30 @@ PSOLVE_API psolve_status psolve_solve_batch(int32_t count, const int64_t *grids,
 typedef struct psolve_server psolve_server;
 
 /* A server owns a device memory pool of hbm_budget_bytes, a request queue
- * and a host thread that advances all admitted problems together, one outer
- * iteration per round, admitting queued requests at round boundaries as
- * slots (max_slots) and memory free up.  precond/degree/cheb_prec are
- * shared by all requests.  The server's kernels run on `stream`. */
-PSOLVE_API psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, int32_t precond,
-                                   int32_t degree, int32_t cheb_prec, uintptr_t stream,
-                                   psolve_server **out);
+ * and a host thread that advances all admitted problems together, a few
+ * outer iterations per round, admitting queued requests at round boundaries
+ * as slots (max_slots) and memory free up.  Requests that share the
+ * preconditioner (precond, degree, cheb_prec) share every kernel launch of a
+ * round; each distinct preconditioner is a launch group of its own in the
+ * same round (at most 32 distinct ones per server).  The server's kernels
+ * run on `stream`. */
+PSOLVE_API psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, uintptr_t stream,
+                                              psolve_server **out);
 
-/* Queue one solve.  grid/h as in psolve_create; rhs_dev/x_dev device
- * pointers that stay valid until psolve_poll returns non-PENDING.  opts may
- * be NULL (blocks and half-step check are taken from it; x0 = 0; its
- * Chebyshev scales must be 1, 1: served problems share launches, and all use
- * the exact closed-form bounds, else PSOLVE_E_ARG).
+/* Queue one solve (Algorithm 1, as psolve_solve).  grid/h as in
+ * psolve_create; rhs_dev/x_dev device pointers that stay valid until
+ * psolve_poll returns non-PENDING.  precond is PSOLVE_PC_NONE or a Chebyshev
+ * form (G(CI), BJ(CI), GNoComm(CI)) with degree as in psolve_solve.  opts may
+ * be NULL; taken from it: cheb_prec, blocks (dividing the grid for BJ /
+ * GNoComm) and the half-step check; x0 = 0; its Chebyshev scales must be
+ * 1, 1 (served problems use the exact closed-form bounds, which makes the
+ * sweeps of every request of a group the same kernels), else PSOLVE_E_ARG.
  * *ticket identifies the request.  PSOLVE_REJECTED if the request alone
  * exceeds the memory budget. */
 PSOLVE_API psolve_status psolve_submit(psolve_server *srv, const int64_t grid[3], const double h[3],
-                            const double *rhs_dev, double *x_dev, double rtol, int32_t maxit,
-                            const psolve_opts *opts, uint64_t *ticket);
+                                       const double *rhs_dev, double *x_dev, double rtol, int32_t maxit,
+                                       int32_t precond, int32_t degree, const psolve_opts *opts,
+                                       uint64_t *ticket);
 
 /* PSOLVE_PENDING while the request runs; otherwise its final status, with
  * *res filled (res may be NULL) and the ticket released. */

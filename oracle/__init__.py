@@ -4,7 +4,10 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` import this package.
 The CUDA product path never imports, links or calls it.
 
-Thin ctypes wrapper around ``psolve_oracle.c`` (plain serial C, FP64).  Arrays
+Thin ctypes wrapper around ``psolve_oracle.c`` (plain serial C, FP64).  The
+same source is also built with OpenMP (``use_build("omp")``, ``threads``) for
+the timed CPU baseline and long stored reference runs; the serial build is the
+default and the one the parity tests use.  Arrays
 are numpy float64 of shape (nz, ny, nx), C-contiguous (x fastest), matching
 the oracle's ``i + nx*(j + ny*k)`` layout.
 
@@ -25,12 +28,13 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .build_oracle import build as _build, LIB_PATH
+from .build_oracle import build as _build, build_omp as _build_omp, LIB_PATH, LIB_OMP_PATH
 
 PC_NONE, PC_CHEB, PC_BJ_CHEB, PC_GNOCOMM_CHEB, PC_G_BICGS, PC_BJ_BICGS = 0, 1, 2, 3, 4, 5
 OK, E_ARG, E_OOM, NOT_CONVERGED, BREAKDOWN, NONFINITE = 0, 1, 2, 4, 5, 6
 
-_lib = None
+_libs = {}
+_active = "serial"
 
 
 class _PC(ctypes.Structure):
@@ -58,18 +62,40 @@ class _Res(ctypes.Structure):
     ]
 
 
+def use_build(kind: str) -> str:
+    """Select the oracle build the functions below call: "serial" (default,
+    the parity oracle) or "omp" (the OpenMP build).  Returns the previous one."""
+    global _active
+    if kind not in ("serial", "omp"):
+        raise ValueError(kind)
+    prev, _active = _active, kind
+    return prev
+
+
+def threads(n: int = 0) -> int:
+    """Threads the OpenMP build uses (n > 0 sets them); 1 for the serial build."""
+    return int(lib().oracle_threads(int(n)))
+
+
 def lib():
-    global _lib
-    if _lib is None:
-        path = os.environ.get("PSOLVE_ORACLE_LIB")  # a mutant build, used by the mutation test
-        if not path:
-            path = LIB_PATH
+    L = _libs.get(_active)
+    if L is None:
+        if _active == "omp":
+            path = LIB_OMP_PATH
             if not os.path.exists(path):
-                _build()
+                _build_omp()
+        else:
+            path = os.environ.get("PSOLVE_ORACLE_LIB")  # a mutant build, used by the mutation test
+            if not path:
+                path = LIB_PATH
+                if not os.path.exists(path):
+                    _build()
         L = ctypes.CDLL(path)
         D = ctypes.POINTER(ctypes.c_double)
         I64 = ctypes.POINTER(ctypes.c_int64)
         I32 = ctypes.POINTER(ctypes.c_int32)
+        L.oracle_threads.restype = ctypes.c_int
+        L.oracle_threads.argtypes = [ctypes.c_int32]
         L.oracle_dot.restype = ctypes.c_double
         L.oracle_dot.argtypes = [ctypes.c_int64, D, D]
         L.oracle_apply_A.argtypes = [I64, D, I32, D, D]
@@ -88,8 +114,11 @@ def lib():
         L.oracle_bicgstab_rr.argtypes = [I64, D, D, D, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                          ctypes.POINTER(_PC), ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(_Res), D, D]
-        _lib = L
-    return _lib
+        L.oracle_bicgstab_snap.argtypes = [I64, D, D, D, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                           ctypes.POINTER(_PC), ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(_Res), D, D, ctypes.c_int32, I32, D]
+        _libs[_active] = L
+    return L
 
 
 def _dp(a):
@@ -222,21 +251,32 @@ class Result:
     rel_res_true: float
     hist_s: np.ndarray
     hist_r: np.ndarray
+    snapshots: dict = None
 
 
 def bicgstab(b, h, rtol=1e-10, maxit=2000, precond=PC_NONE, degree=0, blocks=(1, 1, 1),
              lmin_scale=1.0, lmax_scale=1.0, x0=None, half_step_check=True, rr_every=0, bc=None,
-             inner_rtol=1e-2, inner_maxit=500):
+             inner_rtol=1e-2, inner_maxit=500, snapshots=()):
     """Algorithm 1.  Returns (x, Result).  ``x0`` None means x0 = 0.
     ``rr_every`` > 0 adds residual replacement (not part of the paper's method).
-    ``bc`` = face conditions of the operator (None: all zero Dirichlet)."""
+    ``bc`` = face conditions of the operator (None: all zero Dirichlet).
+    ``snapshots``: outer iterations after which x is copied out; the copies
+    are returned in ``Result.snapshots`` ({iteration: x}, NaN if not reached)."""
     b = _vec(b)
     x = np.zeros_like(b) if x0 is None else _vec(x0).copy()
     hs = np.full(max(maxit, 1), np.nan)
     hr = np.full(max(maxit, 1), np.nan)
     pc = _pc(precond, degree, blocks, lmin_scale, lmax_scale, bc, inner_rtol, inner_maxit)
     r = _Res()
-    if rr_every:
+    snaps = {}
+    if snapshots:
+        at = (ctypes.c_int32 * len(snapshots))(*[int(k) for k in snapshots])
+        buf = np.full((len(snapshots),) + b.shape, np.nan)
+        lib().oracle_bicgstab_snap(_n(b.shape), _h(h), _dp(b), _dp(x), 1 if x0 is not None else 0, float(rtol),
+                                   int(maxit), ctypes.byref(pc), 1 if half_step_check else 0, int(rr_every),
+                                   ctypes.byref(r), _dp(hs), _dp(hr), len(snapshots), at, _dp(buf))
+        snaps = {int(k): buf[j] for j, k in enumerate(snapshots)}
+    elif rr_every:
         lib().oracle_bicgstab_rr(_n(b.shape), _h(h), _dp(b), _dp(x), 1 if x0 is not None else 0, float(rtol),
                                  int(maxit), ctypes.byref(pc), 1 if half_step_check else 0, int(rr_every),
                                  ctypes.byref(r), _dp(hs), _dp(hr))
@@ -248,4 +288,4 @@ def bicgstab(b, h, rtol=1e-10, maxit=2000, precond=PC_NONE, degree=0, blocks=(1,
         raise ValueError(f"oracle bicgstab failed with status {r.status}")
     it = r.iterations
     return x, Result(r.status, it, bool(r.half_step_exit), r.rel_res_recursive, r.rel_res_true,
-                     hs[:it], hr[:it])
+                     hs[:it], hr[:it], snaps)

@@ -36,13 +36,39 @@
  *
  * Build with -O2 -ffp-contract=off and without -ffast-math: Dot2's
  * error-free transformations need IEEE rounding of every operation.
+ *
+ * The same source compiles a second time with -fopenmp (liboracle_omp.so),
+ * for the timed CPU baseline and for long stored reference runs.  That build
+ * only spreads the loops over threads with a static schedule: every grid
+ * point is computed by the same expression, and the dot product is the same
+ * Dot2 recurrence run on ORACLE_DOT_CHUNKS fixed index ranges and joined in
+ * range order (see oracle_dot), so its results do not depend on the thread
+ * count.  The serial build is the one the parity tests use.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#define ORACLE_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORACLE_PAR_FOR
+#endif
+
 #include "psolve_oracle.h"
+
+int oracle_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Dot2 (Ogita, Rump, Oishi 2005): error-free TwoProduct via fma, Knuth's     */
@@ -63,18 +89,54 @@ static void two_prod(double a, double b, double *p, double *e)
     *p = x;
 }
 
-double oracle_dot(int64_t N, const double *a, const double *b)
+/* The Dot2 recurrence over a[i0..i1) b[i0..i1) (i1 > i0): running sum p and
+ * accumulated error s, result p + s. */
+static void dot2_range(int64_t i0, int64_t i1, const double *a, const double *b, double *p_out, double *s_out)
 {
-    if (N <= 0) return 0.0;
     double p, s, h, r, q;
-    two_prod(a[0], b[0], &p, &s);
-    for (int64_t i = 1; i < N; ++i) {
+    two_prod(a[i0], b[i0], &p, &s);
+    for (int64_t i = i0 + 1; i < i1; ++i) {
         two_prod(a[i], b[i], &h, &r);
         two_sum(p, h, &p, &q);
         s = s + (q + r);
     }
+    *p_out = p;
+    *s_out = s;
+}
+
+#ifdef _OPENMP
+#define ORACLE_DOT_CHUNKS 64
+/* OpenMP build: the index range is cut into ORACLE_DOT_CHUNKS fixed ranges
+ * (independent of the thread count), each summed by the recurrence above,
+ * and the range results are joined in range order by the same step (TwoSum
+ * of the running sums, errors added to s), which keeps Dot2's error bound. */
+double oracle_dot(int64_t N, const double *a, const double *b)
+{
+    if (N <= 0) return 0.0;
+    double pc[ORACLE_DOT_CHUNKS], sc[ORACLE_DOT_CHUNKS];
+    ORACLE_PAR_FOR
+    for (int c = 0; c < ORACLE_DOT_CHUNKS; ++c) {
+        const int64_t i0 = N * c / ORACLE_DOT_CHUNKS, i1 = N * (c + 1) / ORACLE_DOT_CHUNKS;
+        pc[c] = 0.0;
+        sc[c] = 0.0;
+        if (i1 > i0) dot2_range(i0, i1, a, b, &pc[c], &sc[c]);
+    }
+    double p = pc[0], s = sc[0], q;
+    for (int c = 1; c < ORACLE_DOT_CHUNKS; ++c) {
+        two_sum(p, pc[c], &p, &q);
+        s = s + (q + sc[c]);
+    }
     return p + s;
 }
+#else
+double oracle_dot(int64_t N, const double *a, const double *b)
+{
+    if (N <= 0) return 0.0;
+    double p, s;
+    dot2_range(0, N, a, b, &p, &s);
+    return p + s;
+}
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* 7-point operator, Eq. 3 / Eq. 6.                                           */
@@ -135,6 +197,7 @@ int oracle_apply_A_bc(const int64_t n[3], const double h[3], const int32_t bc[6]
         bs = bs_store;
     }
     if (check_bc(n, bs, bc)) return ORACLE_E_ARG;
+    ORACLE_PAR_FOR
     for (int64_t k = 0; k < n[2]; ++k)
         for (int64_t j = 0; j < n[1]; ++j)
             for (int64_t i = 0; i < n[0]; ++i) {
@@ -253,6 +316,7 @@ int oracle_cheb_bc(const int64_t n[3], const double h[3], const int32_t bc[6], c
         return ORACLE_E_OOM;
     }
     int st = ORACLE_OK;
+    ORACLE_PAR_FOR
     for (int64_t q = 0; q < N; ++q) z[q] = rhs[q] / theta;
     if (degree == 0) {
         memcpy(x, z, sizeof(double) * (size_t)N);
@@ -260,6 +324,7 @@ int oracle_cheb_bc(const int64_t n[3], const double h[3], const int32_t bc[6], c
     }
     st = oracle_apply_A_bc(n, h, bc, blocks, rhs, Av);
     if (st) goto done;
+    ORACLE_PAR_FOR
     for (int64_t q = 0; q < N; ++q)
         y[q] = 2.0 * rho_cur / delta * (2.0 * rhs[q] - Av[q] / theta);
     for (int32_t it = 2; it <= degree; ++it) {
@@ -267,6 +332,7 @@ int oracle_cheb_bc(const int64_t n[3], const double h[3], const int32_t bc[6], c
         rho_cur = 1.0 / (2.0 * sigma - rho_old);
         st = oracle_apply_A_bc(n, h, bc, blocks, y, Av);
         if (st) goto done;
+        ORACLE_PAR_FOR
         for (int64_t q = 0; q < N; ++q)
             w[q] = rho_cur * (2.0 * sigma * y[q] + 2.0 / delta * (rhs[q] - Av[q]) - rho_old * z[q]);
         double *tmp = z; /* z <- y, y <- w */
@@ -453,7 +519,30 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
                        const oracle_pc *pc, int32_t half_step_check, int32_t rr_every,
                        oracle_result *res, double *hist_s, double *hist_r)
 {
+    return oracle_bicgstab_snap(n, h, bvec, x, use_x0, rtol, maxit, pc, half_step_check, rr_every, res, hist_s,
+                                hist_r, 0, NULL, NULL);
+}
+
+/* Copy of x after outer iteration i into the snapshot slots that ask for it. */
+static void snapshot(int64_t N, const double *x, int32_t i, int32_t nsnap, const int32_t *snap_at,
+                     double *snap_x)
+{
+    for (int32_t j = 0; j < nsnap; ++j)
+        if (snap_at[j] == i) memcpy(snap_x + (size_t)j * (size_t)N, x, sizeof(double) * (size_t)N);
+}
+
+/* oracle_bicgstab_rr that also copies x after the outer iterations listed in
+ * snap_at[0..nsnap) into snap_x (nsnap vectors of N doubles): the iterate a
+ * run with maxit = snap_at[j] would return.  Slots of iterations the solve
+ * does not reach are left untouched.  Records only; no arithmetic changes. */
+int oracle_bicgstab_snap(const int64_t n[3], const double h[3], const double *bvec,
+                         double *x, int32_t use_x0, double rtol, int32_t maxit,
+                         const oracle_pc *pc, int32_t half_step_check, int32_t rr_every,
+                         oracle_result *res, double *hist_s, double *hist_r,
+                         int32_t nsnap, const int32_t *snap_at, double *snap_x)
+{
     memset(res, 0, sizeof(*res));
+    if (nsnap < 0 || (nsnap > 0 && (!snap_at || !snap_x))) return res->status = ORACLE_E_ARG;
     if (rr_every < 0) return res->status = ORACLE_E_ARG;
     for (int d = 0; d < 3; ++d)
         if (n[d] < 1 || !(h[d] > 0.0)) return res->status = ORACLE_E_ARG;
@@ -478,6 +567,7 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
     if (use_x0) {
         st = oracle_apply_A_bc(n, h, pc->bc, NULL, x, t);
         if (st) goto out;
+        ORACLE_PAR_FOR
         for (int64_t q = 0; q < N; ++q) r[q] = bvec[q] - t[q];
     } else {
         memset(x, 0, bytes);
@@ -501,12 +591,15 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
         if (!finite(sig1)) { st = ORACLE_NONFINITE; break; }
         if (sig1 == 0.0) { st = ORACLE_BREAKDOWN; break; }
         const double alpha = rho / sig1;
+        ORACLE_PAR_FOR
         for (int64_t q = 0; q < N; ++q) s[q] = r[q] - alpha * w[q];
         const double snorm = sqrt(oracle_dot(N, s, s));
         if (hist_s) hist_s[i - 1] = snorm / nb;
         if (!finite(snorm)) { st = ORACLE_NONFINITE; break; }
         if (half_step_check && snorm / nb <= rtol) {
+            ORACLE_PAR_FOR
             for (int64_t q = 0; q < N; ++q) x[q] = x[q] + alpha * ph[q];
+            snapshot(N, x, i, nsnap, snap_at, snap_x);
             res->half_step_exit = 1;
             res->rel_res_recursive = snorm / nb;
             st = ORACLE_OK;
@@ -522,10 +615,12 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
         if (tt == 0.0) { st = ORACLE_BREAKDOWN; break; }
         const double omega = ts / tt;
         if (omega == 0.0) { st = ORACLE_BREAKDOWN; break; }
+        ORACLE_PAR_FOR
         for (int64_t q = 0; q < N; ++q) {
             x[q] = x[q] + alpha * ph[q] + omega * rh[q];
             r[q] = s[q] - omega * t[q];
         }
+        snapshot(N, x, i, nsnap, snap_at, snap_x);
         rnorm = sqrt(oracle_dot(N, r, r));
         res->rel_res_recursive = rnorm / nb;
         if (hist_r) hist_r[i - 1] = rnorm / nb;
@@ -538,6 +633,7 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
             /* residual replacement (see above) */
             e = oracle_apply_A_bc(n, h, pc->bc, NULL, x, t);
             if (e) { st = e; break; }
+            ORACLE_PAR_FOR
             for (int64_t q = 0; q < N; ++q) r[q] = bvec[q] - t[q];
             rnorm = sqrt(oracle_dot(N, r, r));
             const double rho_true = oracle_dot(N, rt, r);
@@ -550,6 +646,7 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *bvec
             rho_new = rho_true;
         }
         rho = rho_new;
+        ORACLE_PAR_FOR
         for (int64_t q = 0; q < N; ++q) p[q] = r[q] + beta * (p[q] - omega * w[q]);
     }
 
@@ -557,6 +654,7 @@ out:
     if (st != ORACLE_E_ARG && st != ORACLE_E_OOM && N > 0 && r && t) {
         /* true residual ||b - A x|| / ||b|| of the returned x */
         if (oracle_apply_A_bc(n, h, pc->bc, NULL, x, t) == ORACLE_OK) {
+            ORACLE_PAR_FOR
             for (int64_t q = 0; q < N; ++q) r[q] = bvec[q] - t[q];
             const double nbb = sqrt(oracle_dot(N, bvec, bvec));
             res->rel_res_true = nbb > 0.0 ? sqrt(oracle_dot(N, r, r)) / nbb : 0.0;

@@ -58,6 +58,9 @@ typedef struct {
 } oracle_result;
 
 double oracle_dot(int64_t N, const double *a, const double *b);
+/* Threads the OpenMP build uses from now on (n > 0 sets it); returns the
+ * count in force (always 1 for the serial build). */
+int oracle_threads(int32_t n);
 int oracle_apply_A(const int64_t n[3], const double h[3], const int32_t blocks[3],
                    const double *u, double *out);
 int oracle_eig_bounds(const int64_t n[3], const double h[3], double *lmin, double *lmax);
@@ -88,6 +91,13 @@ int oracle_bicgstab_rr(const int64_t n[3], const double h[3], const double *b,
                        double *x, int32_t use_x0, double rtol, int32_t maxit,
                        const oracle_pc *pc, int32_t half_step_check, int32_t rr_every,
                        oracle_result *res, double *hist_s, double *hist_r);
+/* oracle_bicgstab_rr that also copies x after the outer iterations snap_at[j]
+ * (j < nsnap) into snap_x + j*N (record only; see psolve_oracle.c). */
+int oracle_bicgstab_snap(const int64_t n[3], const double h[3], const double *b,
+                         double *x, int32_t use_x0, double rtol, int32_t maxit,
+                         const oracle_pc *pc, int32_t half_step_check, int32_t rr_every,
+                         oracle_result *res, double *hist_s, double *hist_r,
+                         int32_t nsnap, const int32_t *snap_at, double *snap_x);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ EXPORTS = [
     "psolve_apply_A", "psolve_precond_apply", "psolve_dot", "psolve_cheb_interval", "psolve_solve_batch",
     "psolve_server_create", "psolve_submit", "psolve_poll", "psolve_server_destroy", "psolve_last_error",
     "psolve_version", "psolve_dot_noalloc", "psolve_selfcheck_conversions", "psolve_selfcheck_wait_timeout",
-    "psolve_selfcheck_grid_timeout",
+    "psolve_selfcheck_grid_timeout", "psolve_history",
 ]
 
 
@@ -52,7 +52,7 @@ class Opts(ctypes.Structure):
         ("persistent", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("inner_maxit", ctypes.c_int32),
-        ("reserved_", ctypes.c_int32),
+        ("record_history", ctypes.c_int32),
         ("inner_rtol", ctypes.c_double),
     ]
 
@@ -114,10 +114,10 @@ def lib():
         L.psolve_solve_batch.argtypes = [ctypes.c_int32, I64P, DP, ctypes.POINTER(P), ctypes.POINTER(P),
                                          ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(Opts), ctypes.c_void_p, ctypes.POINTER(Result)]
-        L.psolve_server_create.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                           ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(P)]
-        L.psolve_submit.argtypes = [P, I64P, DP, P, P, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(Opts),
-                                    ctypes.POINTER(ctypes.c_uint64)]
+        L.psolve_server_create.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(P)]
+        L.psolve_submit.argtypes = [P, I64P, DP, P, P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_uint64)]
+        L.psolve_history.argtypes = [P, ctypes.c_int32, DP, DP, I32P]
         L.psolve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(Result)]
         L.psolve_server_destroy.argtypes = [P]
         L.psolve_server_destroy.restype = None
@@ -136,7 +136,7 @@ def lib():
         L.psolve_version.argtypes = []
         for name in ("psolve_create", "psolve_solve", "psolve_solve_host", "psolve_apply_A",
                      "psolve_precond_apply", "psolve_dot", "psolve_cheb_interval", "psolve_solve_batch",
-                     "psolve_server_create", "psolve_submit", "psolve_poll"):
+                     "psolve_server_create", "psolve_submit", "psolve_poll", "psolve_history"):
             getattr(L, name).restype = ctypes.c_int32
         _lib = L
     return _lib
@@ -274,6 +274,24 @@ class Solver:
             raise PsolveError(st, "psolve_solve_host")
         return _info(r)
 
+    def history(self):
+        """(rel_s, rel_r): ||s_i||/||b|| and ||r_i||/||b|| of each outer iteration of
+        the last solve (psolve_history; needs record_history=1), numpy arrays with
+        NaN where an iteration did not produce the value."""
+        import numpy as np
+        cnt = ctypes.c_int32()
+        st = lib().psolve_history(self.ctx, 0, None, None, ctypes.byref(cnt))
+        if st != OK:
+            raise PsolveError(st, "psolve_history")
+        n = cnt.value
+        rs = np.full(max(n, 1), np.nan)
+        rr = np.full(max(n, 1), np.nan)
+        st = lib().psolve_history(self.ctx, n, rs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(cnt))
+        if st != OK:
+            raise PsolveError(st, "psolve_history")
+        return rs[:n], rr[:n]
+
     def apply_A(self, u, out, block_restricted=False):
         _check_vec(u, self.shape)
         _check_vec(out, self.shape)
@@ -384,18 +402,20 @@ class Server:
     Requests of different grid sizes share every kernel launch; they are
     admitted at round boundaries while slots and the memory budget allow.
     The caller keeps b and x alive until the request's poll is final, and must
-    make b ready on the server's stream before submitting."""
+    make b ready on the server's stream before submitting.  Each request names
+    its preconditioner (precond, degree, and opts.cheb_prec); requests that
+    share one share every launch."""
 
-    def __init__(self, budget_bytes, max_slots=64, precond=PC_CHEB, degree=8, cheb_prec=FP64, stream=None):
+    def __init__(self, budget_bytes, max_slots=64, stream=None):
         srv = ctypes.c_void_p()
         self._stream = _stream_handle(stream)
-        st = lib().psolve_server_create(float(budget_bytes), int(max_slots), int(precond), int(degree),
-                                        int(cheb_prec), self._stream, ctypes.byref(srv))
+        st = lib().psolve_server_create(float(budget_bytes), int(max_slots), self._stream, ctypes.byref(srv))
         if st != OK:
             raise PsolveError(st, "psolve_server_create")
         self.srv = srv
 
-    def submit(self, b, x, h=None, rtol=1e-10, maxit=2000, opts: Opts | None = None, **opt_kw) -> int:
+    def submit(self, b, x, h=None, rtol=1e-10, maxit=2000, precond=PC_CHEB, degree=8, opts: Opts | None = None,
+               **opt_kw) -> int:
         nz, ny, nx = b.shape
         _check_vec(b, b.shape)
         _check_vec(x, b.shape)
@@ -405,8 +425,8 @@ class Server:
         hh = (ctypes.c_double * 3)(*[float(v) for v in h])
         o = opts if opts is not None else default_opts(**opt_kw)
         t = ctypes.c_uint64()
-        st = lib().psolve_submit(self.srv, grid, hh, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(o),
-                                 ctypes.byref(t))
+        st = lib().psolve_submit(self.srv, grid, hh, _ptr(b), _ptr(x), float(rtol), int(maxit), int(precond),
+                                 int(degree), ctypes.byref(o), ctypes.byref(t))
         if st != OK:
             raise PsolveError(st, "psolve_submit")
         return t.value

@@ -465,6 +465,9 @@ struct psolve_ctx {
     double *d_hb = nullptr, *d_hx = nullptr; // device copies for psolve_solve_host
     bool tma_ok = true; // false: the autotuner chose the general engine
     FlexInner flex;     // G(BiCGS) / BJ(BiCGS) inner solver, built on first use
+    double *d_hist = nullptr; // residual history (opts.record_history), 2 doubles per iteration
+    int hist_cap = 0;         // iterations d_hist holds
+    bool solved = false;      // a solve has run (its scalars are in P.d_sc)
 };
 
 extern "C" {
@@ -510,6 +513,7 @@ void psolve_destroy(psolve_ctx *c)
     if (c->d_list) cudaFree(c->d_list);
     if (c->d_hb) cudaFree(c->d_hb);
     if (c->d_hx) cudaFree(c->d_hx);
+    if (c->d_hist) cudaFree(c->d_hist);
     if (c->h_desc) cudaFreeHost(c->h_desc);
     if (c->d_tmap) cudaFree(c->d_tmap);
     if (c->h_tmap) cudaFreeHost(c->h_tmap);
@@ -950,6 +954,35 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     if (st != PSOLVE_OK) return st;
     const bool use_x0 = c->opts.use_x0 != 0;
     Desc &D = P.desc;
+    D.hist = nullptr;
+    D.hist_cap = 0;
+    if (c->opts.record_history) {
+        const int need = std::max(maxit, 1);
+        if (need > c->hist_cap) {
+            if (c->d_hist) cudaFree(c->d_hist);
+            c->d_hist = nullptr;
+            c->hist_cap = 0;
+            cudaError_t e = cudaMalloc(&c->d_hist, sizeof(double) * 2 * (size_t)need);
+            if (e != cudaSuccess) {
+                set_error("residual history buffer: %s", cudaGetErrorString(e));
+                return PSOLVE_E_OOM;
+            }
+            c->hist_cap = need;
+        }
+        // all-ones bytes are a NaN: entries a solve does not reach read as NaN
+        PS_CK(cudaMemsetAsync(c->d_hist, 0xff, sizeof(double) * 2 * (size_t)c->hist_cap, c->stream));
+        D.hist = c->d_hist;
+        D.hist_cap = c->hist_cap;
+    }
+    c->solved = true;
+    if (precond == PSOLVE_PC_GNOCOMM_CHEB) {
+        // the paper's upper bound on useful GNoComm(CI) degrees: N_s / 2
+        long long ns = P.n[0] / P.blocks[0];
+        for (int d = 1; d < 3; ++d) ns = std::min<long long>(ns, P.n[d] / P.blocks[d]);
+        if (2LL * degree > ns)
+            set_error("warning: GNoComm(CI) degree %d exceeds half the smallest block side (%lld / 2): the "
+                      "frozen block ghosts have reached every point after N_s/2 sweeps", degree, ns);
+    }
     D.rtol = rtol;
     D.maxit = maxit;
     D.half_check = c->opts.half_step_check ? 1 : 0;
@@ -1064,6 +1097,36 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     fill_result(s, P, R.plan, use_x0, tr, t0, R.launches, &tmp);
     if (res) *res = tmp;
     return (psolve_status)s.status;
+}
+
+psolve_status psolve_history(psolve_ctx *c, int32_t capacity, double *rel_s, double *rel_r, int32_t *count)
+{
+    clear_error();
+    if (!c || !count || capacity < 0) {
+        set_error("bad argument");
+        return PSOLVE_E_ARG;
+    }
+    if (!c->opts.record_history || !c->d_hist || !c->solved) {
+        set_error("no residual history: create the context with opts.record_history = 1 and solve first");
+        return PSOLVE_E_ARG;
+    }
+    PS_CK(cudaSetDevice(c->di.dev));
+    Scal s;
+    PS_CK(cudaMemcpyAsync(&s, c->P.d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, c->stream));
+    const int n = std::min(std::min((int)s.iter, c->hist_cap), (int)capacity);
+    std::vector<double> raw(2 * (size_t)std::max(n, 1));
+    if (n > 0)
+        PS_CK(cudaMemcpyAsync(raw.data(), c->d_hist, sizeof(double) * 2 * (size_t)n, cudaMemcpyDeviceToHost,
+                              c->stream));
+    PS_CK(cudaStreamSynchronize(c->stream));
+    // squared norms -> ||v|| / ||b||, the form Algorithm 1 tests
+    const double nb = std::sqrt(s.nb2);
+    for (int i = 0; i < n; ++i) {
+        if (rel_s) rel_s[i] = std::sqrt(raw[2 * (size_t)i]) / nb;
+        if (rel_r) rel_r[i] = std::sqrt(raw[2 * (size_t)i + 1]) / nb;
+    }
+    *count = s.iter;
+    return PSOLVE_OK;
 }
 
 psolve_status psolve_solve_host(psolve_ctx *c, const double *rhs_host, double *x_host, double rtol,
@@ -1181,6 +1244,8 @@ psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, 
     P.desc.vec[ROLE_R] = saved_r;
     if (st != PSOLVE_OK) return st;
     // first-iteration state: the direction update reads v as "r" and copies it
+    // (this overwrites the last solve's scalars, and with them its history count)
+    c->solved = false;
     Scal *init = c->h_sc + 2;
     std::memset(init, 0, sizeof(Scal));
     init->first = 1;

@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 
 namespace psolve {
 
@@ -47,22 +48,31 @@ cudaEvent_t Launcher::next_event()
     return (*event_pool)[(*event_next)++];
 }
 
-// Per-kernel launch set-up, done once per process: the dynamic shared memory
-// of the TMA ring and the resident CTAs per SM that size the grid.
+// Per-kernel launch set-up, done once per device: the dynamic shared memory
+// of the TMA ring (a per-device attribute of the kernel) and the resident
+// CTAs per SM that size the grid.  Several host threads may race to set it
+// up; each does the same idempotent calls and stores the same value.
+constexpr int MAX_CONFIG_DEVICES = 64;
 template <class Op>
 static cudaError_t op_config(int *occ_out)
 {
-    static int occ = 0;
-    if (!occ) {
+    static std::atomic<int> occ[MAX_CONFIG_DEVICES];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_CONFIG_DEVICES) return cudaErrorInvalidDevice;
+    int o = occ[dev].load(std::memory_order_acquire);
+    if (!o) {
         const int dyn = engine_dyn_smem<Op>();
-        cudaError_t e = cudaFuncSetAttribute(k_engine<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        e = cudaFuncSetAttribute(k_engine<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
         int n = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_engine<Op>, NTHREADS, dyn);
         if (e != cudaSuccess) return e;
-        occ = n < 1 ? 1 : n;
+        o = n < 1 ? 1 : n;
+        occ[dev].store(o, std::memory_order_release);
     }
-    *occ_out = occ;
+    *occ_out = o;
     return cudaSuccess;
 }
 

@@ -269,6 +269,7 @@ __device__ void epilogue(const Desc &D, Scal *sc_mem, const double (&v)[ND])
     } else if constexpr (EPI == EPI_SNORM) {
         const double ss = v[0];
         sc->ss = ss;
+        if (D.hist && sc->iter < D.hist_cap) D.hist[2 * sc->iter] = ss; // iteration iter + 1
         sc->half = 0;
         if (!isfinite(ss)) stop_with(sc, ST_NONFINITE);
         else if (D.half_check && ss <= sc->thr2) sc->half = 1;
@@ -290,6 +291,7 @@ __device__ void epilogue(const Desc &D, Scal *sc_mem, const double (&v)[ND])
         } else {
             const double rho_new = v[0], rr = v[1];
             sc->rr = rr;
+            if (D.hist && sc->iter <= D.hist_cap) D.hist[2 * sc->iter - 1] = rr;
             if (!isfinite(rr) || !isfinite(rho_new)) stop_with(sc, ST_NONFINITE);
             else if (rr <= sc->thr2) stop_with(sc, ST_OK);
             else if (rr > 1e16 * sc->nb2) stop_with(sc, ST_NOT_CONVERGED); // diverged: ||r|| > 1e8 ||b||
@@ -306,6 +308,7 @@ __device__ void epilogue(const Desc &D, Scal *sc_mem, const double (&v)[ND])
         // rescale it to rho_i = r~ . r of the replaced residual
         const double rho_new = v[0], rr = v[1];
         sc->rr = rr;
+        if (D.hist && sc->iter <= D.hist_cap) D.hist[2 * sc->iter - 1] = rr; // replaces the recursive norm
         if (!isfinite(rr) || !isfinite(rho_new)) stop_with(sc, ST_NONFINITE);
         else if (rr <= sc->thr2) stop_with(sc, ST_OK);
         else if (rho_new == 0.0) stop_with(sc, ST_BREAKDOWN);

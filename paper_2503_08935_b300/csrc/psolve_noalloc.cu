@@ -12,14 +12,14 @@
 // launch list, scalar block and per-unit partial sums placed in one
 // file-scope __device__ array of NOALLOC_SCRATCH_BYTES bytes, which every GPU
 // that loads the library keeps until the process exits.  In host code the
-// array's name is only a host-side stand-in, so its device address is looked
-// up once per device with cudaGetSymbolAddress (that device current) on the
-// first call made on it; make that first call before any stream capture.
-// Every call shares the array: the scalar block (whose ticket must start at
-// zero) is cleared on each call, and calls that overlap on the GPU (on
-// different streams, or from several host threads) race on it.
-#include <mutex>
-
+// array's name is only a host-side stand-in, so every call looks its device
+// address up with cudaGetSymbolAddress on the current device (cheap once the
+// module is loaded, and never stale after a device reset).  Every call also
+// stages the descriptor from host stack memory and waits for its result, so
+// no call can run inside a stream capture.  Every call shares the array: the
+// scalar block (whose ticket must start at zero) is cleared on each call, and
+// calls that overlap on the GPU (on different streams, or from several host
+// threads) race on it.
 #include "psolve_engine.cuh"
 
 using namespace psolve;
@@ -27,12 +27,8 @@ using namespace psolve;
 namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = 4u << 20; // 4 MiB
-constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
-
-std::mutex g_noalloc_mu;
-unsigned char *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -42,23 +38,16 @@ constexpr size_t OFF_LIST = align256(sizeof(Desc));
 constexpr size_t OFF_SCAL = OFF_LIST + align256((LIST_HDR_INTS + 2) * sizeof(int32_t));
 constexpr size_t OFF_PART = OFF_SCAL + align256(sizeof(Scal));
 
+// Device address of the scratch array on the current device.
 psolve_status scratch_for_device(int dev, unsigned char **out)
 {
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
-        set_error("device %d: psolve_dot_noalloc supports devices 0..%d", dev, NOALLOC_MAX_DEVICES - 1);
-        return PSOLVE_E_ARG;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("cudaGetSymbolAddress(scratch) on device %d: %s", dev, cudaGetErrorString(e));
+        return PSOLVE_E_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress(scratch) on device %d: %s", dev, cudaGetErrorString(e));
-            return PSOLVE_E_CUDA;
-        }
-        g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_noalloc_addr[dev];
+    *out = static_cast<unsigned char *>(p);
     return PSOLVE_OK;
 }
 
@@ -89,7 +78,9 @@ extern "C" PSOLVE_API psolve_status psolve_dot_noalloc(const int64_t grid[3], co
     psolve_status st = device_info(&di);
     if (st != PSOLVE_OK) return st;
 
-    // The same unit decomposition as a context for this grid on this GPU.
+    // The same unit decomposition as a context for this grid on this GPU
+    // created without the autotuner (a tuned slab depth changes the units,
+    // and with them the summation order).
     Problem P;
     for (int d = 0; d < 3; ++d) {
         P.n[d] = grid[d];

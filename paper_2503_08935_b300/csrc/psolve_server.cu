@@ -6,12 +6,16 @@
 //   1. admit queued requests (FIFO) while a slot and a block of the device
 //      memory pool are free; set up their descriptors and launch the
 //      initial-residual kernel over the newcomers only;
-//   2. replay one captured CUDA graph of `round_iters` outer iterations over
-//      the device-side launch list of all active problems (kernels skip a
-//      problem whose `stop` flag is set, so problems finish independently);
+//   2. for each launch group (the active requests that share a
+//      preconditioner: precond, degree, Chebyshev precision), replay that
+//      group's captured CUDA graph of `round_iters` outer iterations over
+//      the group's device-side launch list (kernels skip a problem whose
+//      `stop` flag is set, so problems finish independently);
 //   3. copy the active problems' scalar blocks to pinned memory, and retire
 //      the stopped ones: true residual, result record, memory back to the
 //      pool, slot freed.
+// The initial residual and the true residual do not depend on the
+// preconditioner, so they run over mixed lists of every group.
 // Each problem keeps its own unit decomposition and reduction order, so a
 // served result is bitwise the one psolve_solve gives for the same problem
 // and options, whatever else is in the mix.
@@ -92,6 +96,7 @@ class Pool {
 
 struct Request {
     uint64_t ticket = 0;
+    int group = 0;               // launch group (the request's preconditioner)
     Problem prob;
     const double *rhs = nullptr; // caller's b (device)
     double *x = nullptr;         // caller's x (device)
@@ -108,13 +113,27 @@ struct Active {
     Request req;
 };
 
+constexpr int MAX_GROUPS = 32; // distinct preconditioners per server
+
+// The requests that share one preconditioner share every launch of a round:
+// one device launch list and one captured graph per group, created by the
+// worker thread when the group first has an active request.
+struct Group {
+    Plan plan;
+    int32_t *d_list = nullptr;
+    int32_t *h_list = nullptr; // pinned; a list of its own per group, so the
+                               // uploads of one round never share a buffer
+    cudaGraphExec_t graph = nullptr;
+};
+
 } // namespace
 
 struct psolve_server {
     DevInfo di;
     cudaStream_t stream = 0, cap = 0;
     int max_slots = 0;
-    Plan plan;
+    std::vector<Plan> plans; // plans[g]: launch group g (guarded by mu)
+    Group groups[MAX_GROUPS];
     double budget = 0;
     int round_iters = 2;
     char *pool_mem = nullptr;
@@ -124,10 +143,9 @@ struct psolve_server {
     Desc *d_desc = nullptr, *h_desc = nullptr;
     Scal *d_sc = nullptr, *h_sc = nullptr;
     CUtensorMap *d_tmap = nullptr, *h_tmap = nullptr;
-    int32_t *d_list_all = nullptr, *d_list_new = nullptr, *d_list_fin = nullptr;
-    int32_t *h_lists = nullptr; // three pinned lists back to back
+    int32_t *d_list_new = nullptr, *d_list_fin = nullptr;
+    int32_t *h_lists = nullptr; // two pinned lists back to back (new, finished)
     cudaEvent_t ev = nullptr;
-    cudaGraphExec_t graph = nullptr;
     // requests
     std::mutex mu;
     std::condition_variable cv;
@@ -145,17 +163,12 @@ struct psolve_server {
 namespace {
 
 // Lists are [n, total, next, done, (slot, first unit) x n]; capacity
-// max_slots entries.
-int32_t *list_host(psolve_server *s, int which)
-{
-    return s->h_lists + (size_t)which * (LIST_HDR_INTS + 2 * s->max_slots);
-}
-
+// max_slots entries.  Pinned host copies: a group's own, or h_lists for the
+// newcomers' (which = 1) and finished requests' (which = 2) lists.
 size_t list_bytes(int n) { return sizeof(int32_t) * (LIST_HDR_INTS + 2 * (size_t)n); }
 
-cudaError_t upload_list(psolve_server *s, int which, const std::vector<int> &slots)
+cudaError_t upload_list(psolve_server *s, int32_t *h, int32_t *d, const std::vector<int> &slots)
 {
-    int32_t *h = list_host(s, which);
     h[0] = (int32_t)slots.size();
     h[2] = h[3] = 0; // the list's work counters start at zero
     int32_t ub = 0;
@@ -165,8 +178,13 @@ cudaError_t upload_list(psolve_server *s, int which, const std::vector<int> &slo
         ub += s->slots[slots[q]].req.prob.desc.units;
     }
     h[1] = ub;
-    int32_t *d = which == 0 ? s->d_list_all : (which == 1 ? s->d_list_new : s->d_list_fin);
     return cudaMemcpyAsync(d, h, list_bytes((int)slots.size()), cudaMemcpyHostToDevice, s->stream);
+}
+
+cudaError_t upload_list(psolve_server *s, int which, const std::vector<int> &slots)
+{
+    int32_t *h = s->h_lists + (size_t)(which - 1) * (LIST_HDR_INTS + 2 * s->max_slots);
+    return upload_list(s, h, which == 1 ? s->d_list_new : s->d_list_fin, slots);
 }
 
 Launcher server_launcher(psolve_server *s, const int32_t *d_list)
@@ -180,33 +198,44 @@ Launcher server_launcher(psolve_server *s, const int32_t *d_list)
     return L;
 }
 
-cudaError_t ensure_graph(psolve_server *s)
+// Device list, pinned list and captured round graph of group gi (worker
+// thread, on first use).
+cudaError_t ensure_group(psolve_server *s, int gi)
 {
-    if (s->graph) return cudaSuccess;
-    Launcher C = server_launcher(s, s->d_list_all);
+    Group &G = s->groups[gi];
+    if (G.graph) return cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        G.plan = s->plans[gi];
+    }
+    cudaError_t e;
+    if (!G.d_list && (e = cudaMalloc(&G.d_list, list_bytes(s->max_slots))) != cudaSuccess) return e;
+    if (!G.h_list && (e = cudaHostAlloc(&G.h_list, list_bytes(s->max_slots), cudaHostAllocDefault)) != cudaSuccess)
+        return e;
+    Launcher C = server_launcher(s, G.d_list);
     C.stream = s->cap;
     C.iter = 2;
     Launcher cfg = C;
     cfg.configure = true;
-    enqueue_iteration(cfg, s->plan);
+    enqueue_iteration(cfg, G.plan);
     enqueue_init(cfg, false);
     enqueue_true_residual(cfg);
     if (cfg.err != cudaSuccess) return cfg.err;
-    cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+    e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    for (int j = 0; j < s->round_iters; ++j) enqueue_iteration(C, s->plan);
+    for (int j = 0; j < s->round_iters; ++j) enqueue_iteration(C, G.plan);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s->cap, &g);
     if (C.err != cudaSuccess || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return C.err != cudaSuccess ? C.err : e;
     }
-    e = cudaGraphInstantiate(&s->graph, g, 0);
+    e = cudaGraphInstantiate(&G.graph, g, 0);
     cudaGraphDestroy(g);
     return e;
 }
 
-void finish(psolve_server *s, const Request &r, const Scal &sc, double t)
+void finish(psolve_server *s, const Request &r, const Scal &sc, double t, const Plan &plan)
 {
     psolve_result res;
     std::memset(&res, 0, sizeof res);
@@ -227,7 +256,7 @@ void finish(psolve_server *s, const Request &r, const Scal &sc, double t)
     enqueue_init(D, false);
     for (int it = 1; it <= sc.iter; ++it) {
         D.iter = it;
-        enqueue_iteration(D, s->plan);
+        enqueue_iteration(D, plan);
     }
     D.iter = -1;
     enqueue_true_residual(D);
@@ -273,6 +302,7 @@ void worker_main(psolve_server *s)
 {
     cudaSetDevice(s->di.dev);
     std::vector<int> active, fresh, fin;
+    std::vector<int> by_group[MAX_GROUPS];
     for (;;) {
         // ---- admission
         fresh.clear();
@@ -323,11 +353,16 @@ void worker_main(psolve_server *s)
             P.desc.vec[ROLE_RT] = (void *)r.rhs; // x0 = 0: r~ = r0 = b
             P.desc.sc = s->d_sc + slot;
             P.desc.tmap = s->d_tmap + (size_t)TMAPS_PER_PROBLEM * slot;
-            if (problem_set_cheb(P, s->plan.precond, s->plan.degree, r.lmin_scale, r.lmax_scale) != PSOLVE_OK) {
+            Plan plan;
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                plan = s->plans[r.group];
+            }
+            if (problem_set_cheb(P, plan.precond, plan.degree, r.lmin_scale, r.lmax_scale) != PSOLVE_OK) {
                 Scal sc{};
                 sc.status = PSOLVE_E_ARG;
                 sc.stop = 1;
-                finish(s, r, sc, now_s());
+                finish(s, r, sc, now_s(), plan);
                 s->pool.release(r.off, r.bytes);
                 s->slots[slot].used = false;
                 continue;
@@ -354,10 +389,16 @@ void worker_main(psolve_server *s)
             if (s->slots[q].used) active.push_back(q);
         if (active.empty()) continue;
 
-        // ---- one round over every active problem
-        W_CK(upload_list(s, 0, active));
-        W_CK(ensure_graph(s));
-        W_CK(cudaGraphLaunch(s->graph, s->stream));
+        // ---- one round over every active problem, group by group
+        for (auto &v : by_group) v.clear();
+        for (int q : active) by_group[s->slots[q].req.group].push_back(q);
+        for (int gi = 0; gi < MAX_GROUPS; ++gi) {
+            if (by_group[gi].empty()) continue;
+            W_CK(ensure_group(s, gi));
+            Group &G = s->groups[gi];
+            W_CK(upload_list(s, G.h_list, G.d_list, by_group[gi]));
+            W_CK(cudaGraphLaunch(G.graph, s->stream));
+        }
         W_CK(cudaMemcpyAsync(s->h_sc, s->d_sc, sizeof(Scal) * s->max_slots, cudaMemcpyDeviceToHost, s->stream));
         W_CK(cudaEventRecord(s->ev, s->stream));
         W_CK(cudaEventSynchronize(s->ev));
@@ -378,7 +419,7 @@ void worker_main(psolve_server *s)
         for (int q : fin) {
             Active &a = s->slots[q];
             const Scal sc = s->h_sc[q];
-            finish(s, a.req, sc, t);
+            finish(s, a.req, sc, t, s->groups[a.req.group].plan);
             {
                 std::lock_guard<std::mutex> lock(s->mu);
                 s->pool.release(a.req.off, a.req.bytes);
@@ -396,13 +437,10 @@ void worker_main(psolve_server *s)
 
 extern "C" {
 
-psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, int32_t precond, int32_t degree,
-                                   int32_t cheb_prec, uintptr_t stream, psolve_server **out)
+psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, uintptr_t stream, psolve_server **out)
 {
     clear_error();
-    if (!out || !(hbm_budget_bytes > 0) || max_slots < 1 || max_slots > 4096 || precond < PSOLVE_PC_NONE ||
-        precond > PSOLVE_PC_GNOCOMM_CHEB || degree < 0 || degree > MAX_DEGREE || cheb_prec < PSOLVE_FP64 ||
-        cheb_prec > PSOLVE_BF16) {
+    if (!out || !(hbm_budget_bytes > 0) || max_slots < 1 || max_slots > 4096) {
         set_error("bad server argument");
         return PSOLVE_E_ARG;
     }
@@ -414,10 +452,6 @@ psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, i
     }
     s->stream = (cudaStream_t)stream;
     s->max_slots = max_slots;
-    s->plan.precond = precond;
-    s->plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
-    s->plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : cheb_prec;
-    s->plan.exact_bounds = true; // requests use the exact closed-form bounds (checked at submit)
     s->budget = hbm_budget_bytes;
     s->pool_bytes = (size_t)hbm_budget_bytes;
     s->slots.resize(max_slots);
@@ -434,7 +468,6 @@ psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, i
     if ((e = cudaMemset(s->d_sc, 0, sizeof(Scal) * max_slots)) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->d_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * max_slots)) != cudaSuccess)
         return bail(e);
-    if ((e = cudaMalloc(&s->d_list_all, list_bytes(max_slots))) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->d_list_new, list_bytes(max_slots))) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->d_list_fin, list_bytes(max_slots))) != cudaSuccess) return bail(e);
     if ((e = cudaHostAlloc(&s->h_desc, sizeof(Desc) * max_slots, cudaHostAllocDefault)) != cudaSuccess)
@@ -444,7 +477,7 @@ psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, i
     if ((e = cudaHostAlloc(&s->h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM * max_slots,
                            cudaHostAllocDefault)) != cudaSuccess)
         return bail(e);
-    if ((e = cudaHostAlloc(&s->h_lists, 3 * list_bytes(max_slots), cudaHostAllocDefault)) != cudaSuccess)
+    if ((e = cudaHostAlloc(&s->h_lists, 2 * list_bytes(max_slots), cudaHostAllocDefault)) != cudaSuccess)
         return bail(e);
     if ((e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
     if ((e = cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming)) != cudaSuccess) return bail(e);
@@ -454,11 +487,16 @@ psolve_status psolve_server_create(double hbm_budget_bytes, int32_t max_slots, i
 }
 
 psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const double h[3], const double *rhs_dev,
-                            double *x_dev, double rtol, int32_t maxit, const psolve_opts *opts, uint64_t *ticket)
+                            double *x_dev, double rtol, int32_t maxit, int32_t precond, int32_t degree,
+                            const psolve_opts *opts, uint64_t *ticket)
 {
     clear_error();
     if (!s || !grid || !h || !rhs_dev || !x_dev || !ticket || !(rtol >= 0.0) || !std::isfinite(rtol) || maxit < 0) {
         set_error("bad argument");
+        return PSOLVE_E_ARG;
+    }
+    if (precond < PSOLVE_PC_NONE || precond > PSOLVE_PC_GNOCOMM_CHEB || degree < 0 || degree > MAX_DEGREE) {
+        set_error("served requests take PSOLVE_PC_NONE or a Chebyshev form with degree in [0, %d]", MAX_DEGREE);
         return PSOLVE_E_ARG;
     }
     long long n = 1;
@@ -480,18 +518,27 @@ psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const doubl
         set_error("served requests use the exact closed-form Chebyshev bounds (scales 1, 1)");
         return PSOLVE_E_ARG;
     }
+    if (o.cheb_prec < PSOLVE_FP64 || o.cheb_prec > PSOLVE_BF16) {
+        set_error("unknown Chebyshev precision %d", o.cheb_prec);
+        return PSOLVE_E_ARG;
+    }
+    Plan plan;
+    plan.precond = precond;
+    plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
+    plan.prec = precond == PSOLVE_PC_NONE ? PSOLVE_FP64 : o.cheb_prec;
+    plan.exact_bounds = true; // scales 1, 1 (checked above)
     Request r;
     Problem &P = r.prob;
     for (int d = 0; d < 3; ++d) {
         P.n[d] = grid[d];
         P.h[d] = h[d];
         P.blocks[d] = o.blocks[d];
-        if (o.blocks[d] < 1 || (s->plan.precond >= PSOLVE_PC_BJ_CHEB && grid[d] % o.blocks[d] != 0)) {
+        if (o.blocks[d] < 1 || (precond >= PSOLVE_PC_BJ_CHEB && grid[d] % o.blocks[d] != 0)) {
             set_error("blocks[%d] = %d does not divide the grid", d, o.blocks[d]);
             return PSOLVE_E_ARG;
         }
     }
-    P.prec = s->plan.prec;
+    P.prec = plan.prec;
     P.have_rt = false;
     problem_geometry(P, s->di.sms);
     P.desc.rtol = rtol;
@@ -510,8 +557,7 @@ psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const doubl
     }
     {
         double a, b;
-        if (s->plan.precond != PSOLVE_PC_NONE &&
-            cheb_interval(P, s->plan.precond, o.lmin_scale, o.lmax_scale, &a, &b) != PSOLVE_OK)
+        if (precond != PSOLVE_PC_NONE && cheb_interval(P, precond, o.lmin_scale, o.lmax_scale, &a, &b) != PSOLVE_OK)
             return PSOLVE_E_ARG;
     }
     r.t_submit = now_s();
@@ -521,6 +567,18 @@ psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const doubl
             set_error("server failed: %s", s->fail_msg.c_str());
             return PSOLVE_E_CUDA;
         }
+        int gi = -1;
+        for (size_t q = 0; q < s->plans.size(); ++q)
+            if (s->plans[q] == plan) gi = (int)q;
+        if (gi < 0) {
+            if ((int)s->plans.size() >= MAX_GROUPS) {
+                set_error("the server already serves %d distinct preconditioners", MAX_GROUPS);
+                return PSOLVE_E_ARG;
+            }
+            gi = (int)s->plans.size();
+            s->plans.push_back(plan);
+        }
+        r.group = gi;
         r.ticket = s->next_ticket++;
         s->state[r.ticket] = 0;
         s->queue.push_back(r);
@@ -558,14 +616,17 @@ void psolve_server_destroy(psolve_server *s)
     if (s->worker.joinable()) s->worker.join();
     cudaSetDevice(s->di.dev);
     if (s->stream) cudaStreamSynchronize(s->stream);
-    if (s->graph) cudaGraphExecDestroy(s->graph);
+    for (Group &G : s->groups) {
+        if (G.graph) cudaGraphExecDestroy(G.graph);
+        cudaFree(G.d_list);
+        if (G.h_list) cudaFreeHost(G.h_list);
+    }
     if (s->ev) cudaEventDestroy(s->ev);
     if (s->cap) cudaStreamDestroy(s->cap);
     cudaFree(s->pool_mem);
     cudaFree(s->d_desc);
     cudaFree(s->d_sc);
     cudaFree(s->d_tmap);
-    cudaFree(s->d_list_all);
     cudaFree(s->d_list_new);
     cudaFree(s->d_list_fin);
     if (s->h_desc) cudaFreeHost(s->h_desc);

@@ -108,8 +108,12 @@ struct Desc {
     int32_t tma;
     int32_t rr_every;   // residual replacement every rr_every outer iterations (0: never)
     int32_t bcm;        // zero-flux Neumann faces: bit f for face f (x-, x+, y-, y+, z-, z+)
-    int32_t pad2_;
+    int32_t hist_cap;   // outer iterations the history buffer holds
     const CUtensorMap *tmap;
+    // residual history (nullptr: not recorded): hist[2 (i-1)] = ||s_i||^2 and
+    // hist[2 (i-1) + 1] = ||r_i||^2 of outer iteration i (Algorithm 1), for
+    // i <= hist_cap; written by the epilogues of the reductions that produce them
+    double *hist;
 };
 
 // Header of a device-side launch list: `n` entries of (problem, first unit)

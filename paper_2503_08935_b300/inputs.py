@@ -152,3 +152,10 @@ def serving_stream(count: int = 2000, seed: int = 3, lo: int = 16, hi: int = 256
     g = uniform(seed + 1000, count, 0.0, 1.0)
     gaps = -np.log1p(-g)  # Exp(1)
     return shapes, gaps
+
+
+def perturb_relative(v: np.ndarray, seed: int, eps: float) -> np.ndarray:
+    """v * (1 + eps * u) with u i.i.d. uniform[-1, 1) from the splitmix64 stream
+    ``seed``: a right-hand side that differs from v by rounding-sized noise."""
+    u = uniform(seed, v.size).reshape(v.shape)
+    return v * (1.0 + eps * u)

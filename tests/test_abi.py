@@ -49,14 +49,16 @@ def test_struct_layout_matches_c(tmp_path):
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(psolve_opts), sizeof(psolve_result),"
         " offsetof(psolve_result, kernel_launches), offsetof(psolve_result, kclass_bytes),"
         " offsetof(psolve_opts, engine), offsetof(psolve_opts, autotune), offsetof(psolve_result, tuned));"
+        " printf(\"%zu %zu\\n\", offsetof(psolve_opts, record_history), offsetof(psolve_opts, inner_rtol));"
         " return 0;}\n")
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
-    so, sr, okl, okb, orr, oat, otu = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
-                                                              check=True).stdout.split())
+    so, sr, okl, okb, orr, oat, otu, orh, oir = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                                                        check=True).stdout.split())
     assert so == ctypes.sizeof(B.Opts) and sr == ctypes.sizeof(B.Result)
     assert okl == B.Result.kernel_launches.offset and okb == B.Result.kclass_bytes.offset
     assert orr == B.Opts.engine.offset and oat == B.Opts.autotune.offset and otu == B.Result.tuned.offset
+    assert orh == B.Opts.record_history.offset and oir == B.Opts.inner_rtol.offset
 
 
 def test_default_opts(L):
@@ -65,6 +67,7 @@ def test_default_opts(L):
     assert list(o.blocks) == [1, 1, 1]
     assert o.cheb_prec == B.FP64 and o.half_step_check == 1 and o.use_x0 == 0
     assert o.use_graph == 1 and o.true_residual == 1 and o.timing == 0
+    assert o.record_history == 0
 
 
 def _create(L, grid, h, bc=None, opts=None):
@@ -102,4 +105,12 @@ def test_null_arguments_are_rejected(L):
     assert L.psolve_solve(None, None, None, 1e-10, 10, 0, 0, ctypes.byref(r)) == B.E_ARG
     assert L.psolve_apply_A(None, None, None, 0) == B.E_ARG
     assert L.psolve_solve_batch(0, None, None, None, None, 1e-10, 10, 1, 8, None, None, None) == B.E_ARG
+    cnt = ctypes.c_int32()
+    assert L.psolve_history(None, 0, None, None, ctypes.byref(cnt)) == B.E_ARG
+    t = ctypes.c_uint64()
+    g = (ctypes.c_int64 * 3)(4, 4, 4)
+    hh = (ctypes.c_double * 3)(1, 1, 1)
+    assert L.psolve_submit(None, g, hh, None, None, 1e-10, 10, 1, 8, None, ctypes.byref(t)) == B.E_ARG
+    srv = ctypes.c_void_p()
+    assert L.psolve_server_create(0.0, 4, None, ctypes.byref(srv)) == B.E_ARG and not srv.value
     L.psolve_destroy(None)  # no-op

@@ -34,8 +34,9 @@ def test_served_results_bitwise_equal_alone(prec):
     bs = [torch.from_numpy(I.rhs_uniform(sh, seed=50 + q)).to(DEV) for q, sh in enumerate(shapes)]
     xs = [torch.zeros(sh, dtype=torch.float64, device=DEV) for sh in shapes]
     torch.cuda.synchronize()
-    with B.Server(budget_bytes=2 << 30, max_slots=4, precond=B.PC_CHEB, degree=6, cheb_prec=prec) as srv:
-        tickets = [srv.submit(b, x, rtol=1e-10, maxit=500) for b, x in zip(bs, xs)]
+    with B.Server(budget_bytes=2 << 30, max_slots=4) as srv:
+        tickets = [srv.submit(b, x, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=6, cheb_prec=prec)
+                   for b, x in zip(bs, xs)]
         infos = [srv.wait(t) for t in tickets]
     torch.cuda.synchronize()
     for q, sh in enumerate(shapes):
@@ -51,14 +52,17 @@ def test_server_admits_under_a_tight_budget_and_rejects_oversized():
     xs = [torch.zeros(sh, dtype=torch.float64, device=DEV) for sh in shapes]
     torch.cuda.synchronize()
     one = 12 * 8 * 32 * 32 * 40  # roughly one 32x32x40 workspace: forces one-at-a-time admission
-    with B.Server(budget_bytes=1.6 * one, max_slots=8, precond=B.PC_CHEB, degree=4) as srv:
-        tickets = [srv.submit(b, x, rtol=1e-10) for b, x in zip(bs, xs)]
+    with B.Server(budget_bytes=1.6 * one, max_slots=8) as srv:
+        tickets = [srv.submit(b, x, rtol=1e-10, precond=B.PC_CHEB, degree=4) for b, x in zip(bs, xs)]
         big = torch.zeros((64, 64, 64), dtype=torch.float64, device=DEV)
         with pytest.raises(B.PsolveError) as e:
-            srv.submit(big, big)
+            srv.submit(big, big, precond=B.PC_CHEB, degree=4)
         assert e.value.status == B.REJECTED
         with pytest.raises(B.PsolveError) as e:  # served requests share the exact bounds
-            srv.submit(bs[0], xs[0], lmin_scale=100.0, lmax_scale=1 - 1e-4)
+            srv.submit(bs[0], xs[0], precond=B.PC_CHEB, degree=4, lmin_scale=100.0, lmax_scale=1 - 1e-4)
+        assert e.value.status == B.E_ARG
+        with pytest.raises(B.PsolveError) as e:  # the flexible forms are not served
+            srv.submit(bs[0], xs[0], precond=B.PC_G_BICGS, degree=0)
         assert e.value.status == B.E_ARG
         infos = [srv.wait(t) for t in tickets]
     for q, sh in enumerate(shapes):
@@ -77,11 +81,11 @@ def test_served_requests_join_while_others_run():
     bsm = torch.from_numpy(I.rhs_uniform(small_shape, seed=71)).to(DEV)
     xsm = torch.zeros(small_shape, dtype=torch.float64, device=DEV)
     torch.cuda.synchronize()
-    with B.Server(budget_bytes=4 << 30, max_slots=8, precond=B.PC_CHEB, degree=8) as srv:
-        tb = srv.submit(bb, xb, rtol=1e-12, maxit=2000)
+    with B.Server(budget_bytes=4 << 30, max_slots=8) as srv:
+        tb = srv.submit(bb, xb, rtol=1e-12, maxit=2000, precond=B.PC_CHEB, degree=8)
         import time
         time.sleep(0.02)
-        ts = srv.submit(bsm, xsm, rtol=1e-10)
+        ts = srv.submit(bsm, xsm, rtol=1e-10, precond=B.PC_CHEB, degree=8)
         ism = srv.wait(ts)
         st_big, _ = srv.poll(tb)
         ib = srv.wait(tb)
@@ -89,6 +93,46 @@ def test_served_requests_join_while_others_run():
     assert st_big == B.PENDING  # the small one completed while the big one was still running
     xa, ia = solo(small_shape, bsm, B.PC_CHEB, 8, B.FP64)
     assert np.array_equal(xsm.cpu().numpy(), xa)
+
+
+# (precond, degree, Chebyshev precision, blocks) of the mixed-preconditioner stream
+MIXED_REQUESTS = [
+    ((24, 16, 40), B.PC_CHEB, 8, B.FP64, (1, 1, 1)),
+    ((32, 32, 32), B.PC_CHEB, 8, B.FP32, (1, 1, 1)),
+    ((20, 24, 16), B.PC_BJ_CHEB, 6, B.FP64, (2, 2, 2)),
+    ((17, 9, 33), B.PC_NONE, 0, B.FP64, (1, 1, 1)),
+    ((32, 16, 24), B.PC_GNOCOMM_CHEB, 4, B.FP64, (2, 2, 2)),
+    ((40, 24, 16), B.PC_CHEB, 8, B.FP64, (1, 1, 1)),
+    ((16, 32, 24), B.PC_CHEB, 4, B.FP32, (1, 1, 1)),
+    ((24, 24, 24), B.PC_BJ_CHEB, 6, B.FP64, (2, 2, 2)),
+]
+
+
+def test_served_mixed_preconditioners_bitwise_equal_alone():
+    """Requests with different preconditioners (G(CI), BJ(CI), GNoComm(CI), none;
+    FP64 and FP32 Chebyshev vectors; several degrees) in one server: each
+    preconditioner is a launch group of its own in every round, and every
+    result is bitwise the result of solving the request alone."""
+    bs, xs = [], []
+    for q, (sh, *_rest) in enumerate(MIXED_REQUESTS):
+        bs.append(torch.from_numpy(I.rhs_uniform(sh, seed=80 + q)).to(DEV))
+        xs.append(torch.zeros(sh, dtype=torch.float64, device=DEV))
+    torch.cuda.synchronize()
+    with B.Server(budget_bytes=2 << 30, max_slots=5) as srv:
+        tickets = [srv.submit(bs[q], xs[q], rtol=1e-10, maxit=1000, precond=pc, degree=d, cheb_prec=prec,
+                              blocks=blk)
+                   for q, (sh, pc, d, prec, blk) in enumerate(MIXED_REQUESTS)]
+        infos = [srv.wait(t) for t in tickets]
+    torch.cuda.synchronize()
+    for q, (sh, pc, d, prec, blk) in enumerate(MIXED_REQUESTS):
+        x = torch.zeros(sh, dtype=torch.float64, device=DEV)
+        with B.Solver(sh, cheb_prec=prec, blocks=blk) as s:
+            ia = s.solve(bs[q], x, rtol=1e-10, maxit=1000, precond=pc, degree=d)
+        torch.cuda.synchronize()
+        assert infos[q].status == B.OK and ia.status == B.OK
+        assert infos[q].iterations == ia.iterations, (q, infos[q].iterations, ia.iterations)
+        assert np.array_equal(xs[q].cpu().numpy(), x.cpu().numpy()), q
+        assert infos[q].rel_res_true <= 2e-10
 
 
 def test_batch_of_mixed_sizes_config_shapes():

@@ -27,8 +27,8 @@ MUTANTS = {
                                        "x[q] = x[q] + alpha * ph[q];"),
     "bicg_p_update_sign": ("p[q] = r[q] + beta * (p[q] - omega * w[q]);",
                            "p[q] = r[q] + beta * (p[q] + omega * w[q]);"),
-    "bicg_half_step_skips_x_update": ("x[q] = x[q] + alpha * ph[q];\n            res->half_step_exit",
-                                      "x[q] = x[q];\n            res->half_step_exit"),
+    "bicg_half_step_skips_x_update": ("x[q] = x[q] + alpha * ph[q];\n            snapshot(",
+                                      "x[q] = x[q];\n            snapshot("),
     "bicg_alpha_uses_r_not_rtilde": ("const double sig1 = oracle_dot(N, rt, w);",
                                      "const double sig1 = oracle_dot(N, r, w);"),
     "dot2_drops_product_error": ("s = s + (q + r);", "s = s + q;"),

@@ -607,3 +607,72 @@ def test_flexible_bicgstab_matches_dense_solve(pc, blocks, tol, bc):
     P = dense_P_bc(shape, h, bcs)
     assert res.status == O.OK and res.rel_res_true <= 1.1e-10
     assert rel(x, np.linalg.solve(P, b.ravel())) <= 10 * np.linalg.cond(P) * 1e-10
+
+
+# ------------------------------------------------- the OpenMP build ---------
+# The same source compiled with -fopenmp: loops spread over threads, dot
+# products as the Dot2 recurrence over 64 fixed index ranges joined in order.
+# It runs the long stored 256^3 reference solves and the timed CPU baseline;
+# these pins hold it to the same facts as the serial build and to the serial
+# build itself.
+@pytest.fixture
+def omp_build():
+    prev = O.use_build("omp")
+    yield
+    O.use_build(prev)
+
+
+@pytest.mark.parametrize("cond", ["plain", "cancelling"])
+def test_omp_dot2_near_correctly_rounded(omp_build, cond):
+    test_dot2_near_correctly_rounded(cond)
+    test_dot_empty_and_single()
+
+
+def test_omp_dot_does_not_depend_on_thread_count(omp_build):
+    rng = np.random.default_rng(8)
+    a, b = rng.standard_normal(100_003), rng.standard_normal(100_003)
+    vals = []
+    for t in (1, 3, 8):
+        O.threads(t)
+        vals.append(O.dot(a, b))
+    O.threads(os.cpu_count() or 1)
+    assert vals[0] == vals[1] == vals[2]
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 4), (6, 6, 6)])
+@pytest.mark.parametrize("pc", PCS[:3])
+def test_omp_bicgstab_matches_dense_solve(omp_build, shape, pc):
+    test_bicgstab_matches_dense_solve(shape, pc, False)
+
+
+def test_omp_build_follows_the_serial_build():
+    """G(CI) d=8 on 40x36x44 (three threads): the OpenMP build's solve agrees
+    with the serial build's to rounding (same iteration count, solutions and
+    residual histories within 1e-12)."""
+    shape = (44, 36, 40)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=5)
+    xs, rs = O.bicgstab(b, h, rtol=1e-10, maxit=300, precond=O.PC_CHEB, degree=8)
+    prev = O.use_build("omp")
+    try:
+        O.threads(3)
+        xo, ro = O.bicgstab(b, h, rtol=1e-10, maxit=300, precond=O.PC_CHEB, degree=8)
+        O.threads(os.cpu_count() or 1)
+    finally:
+        O.use_build(prev)
+    assert rs.status == ro.status == O.OK and rs.iterations == ro.iterations
+    assert rel(xo, xs) <= 1e-12
+    np.testing.assert_allclose(ro.hist_s, rs.hist_s, rtol=1e-12)
+
+
+def test_snapshots_equal_runs_stopped_there():
+    """x copied out after iteration k of a longer solve is the iterate of a
+    solve with maxit = k; slots past the exit stay NaN."""
+    shape = (12, 10, 14)
+    h = I.default_h(shape)
+    b = I.rhs_uniform(shape, seed=3)
+    x, r = O.bicgstab(b, h, rtol=1e-10, maxit=100, precond=O.PC_CHEB, degree=4, snapshots=(2, 5, 1000))
+    for k in (2, 5):
+        xk, rk = O.bicgstab(b, h, rtol=0.0, maxit=k, precond=O.PC_CHEB, degree=4)
+        assert rk.iterations == k and np.array_equal(xk, r.snapshots[k])
+    assert np.isnan(r.snapshots[1000]).all()

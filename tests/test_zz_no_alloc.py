@@ -35,6 +35,8 @@ def test_noalloc_dot_matches_context_dot_twice(shape):
     first = B.dot_noalloc(a, b)
     second = B.dot_noalloc(a, b)
     assert abs(first - ref) <= tol and abs(second - ref) <= tol
+    # same units, same summation order as a context without the autotuner
+    assert first == ref and second == ref
     assert abs(first - O.dot(a_np, b_np)) <= tol
     # a different pair right after: the shared scratch must not leak state
     c = torch.from_numpy(I.rhs_uniform(shape, seed=33)).cuda()
