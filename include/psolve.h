@@ -340,6 +340,19 @@ PSOLVE_API psolve_status psolve_selfcheck_wait_timeout(int64_t limit_cycles, int
 PSOLVE_API psolve_status psolve_selfcheck_grid_timeout(int64_t limit_ns, int32_t absent_cta, int32_t *ctas,
                                                        int32_t *passed, int32_t *gave_up, int32_t *error_word);
 
+/* Measured FP64 instruction throughput of this GPU: a kernel in which every
+ * thread of 8 CTAs of 256 threads per SM runs 8 independent chains of
+ * `iters` (1 .. 2^24) dependent FP64 instructions, fused multiply-adds (kind
+ * 0) or adds (kind 1), timed with CUDA events on `stream` after one warm-up
+ * run.  *instr_per_s receives the FP64 instructions (thread level) executed
+ * per second, *ms_out (may be NULL) the timed run's duration and *sm_mhz (may
+ * be NULL) the SM clock one CTA saw (clock cycles over global-timer time).
+ * The FP64 kernels of the solver are bound by this rate rather than by HBM
+ * bandwidth, so it is the roofline their achieved rate is divided by.  No
+ * counterpart in the paper (a measurement of the hardware). */
+PSOLVE_API psolve_status psolve_measure_fp64_rate(int32_t kind, int64_t iters, uintptr_t stream,
+                                                  double *instr_per_s, double *ms_out, double *sm_mhz);
+
 /* ---- many independent grids at once ----------------------------------- */
 
 /* Solve `count` independent problems of (possibly) different sizes together:

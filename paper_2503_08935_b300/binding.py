@@ -31,7 +31,7 @@ EXPORTS = [
     "psolve_apply_A", "psolve_precond_apply", "psolve_dot", "psolve_cheb_interval", "psolve_solve_batch",
     "psolve_server_create", "psolve_submit", "psolve_poll", "psolve_server_destroy", "psolve_last_error",
     "psolve_version", "psolve_dot_noalloc", "psolve_selfcheck_conversions", "psolve_selfcheck_wait_timeout",
-    "psolve_selfcheck_grid_timeout", "psolve_history",
+    "psolve_selfcheck_grid_timeout", "psolve_history", "psolve_measure_fp64_rate",
 ]
 
 
@@ -128,6 +128,8 @@ def lib():
         I32P = ctypes.POINTER(ctypes.c_int32)
         L.psolve_selfcheck_grid_timeout.argtypes = [ctypes.c_int64, ctypes.c_int32, I32P, I32P, I32P, I32P]
         L.psolve_selfcheck_grid_timeout.restype = ctypes.c_int32
+        L.psolve_measure_fp64_rate.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, DP, DP, DP]
+        L.psolve_measure_fp64_rate.restype = ctypes.c_int32
         L.psolve_dot_noalloc.argtypes = [I64P, P, P, ctypes.c_void_p, DP]
         L.psolve_dot_noalloc.restype = ctypes.c_int32
         L.psolve_last_error.restype = ctypes.c_char_p
@@ -379,6 +381,17 @@ def selfcheck_grid_timeout(limit_ns=20_000_000, absent_cta=0) -> dict:
     if st != OK:
         raise PsolveError(st, "psolve_selfcheck_grid_timeout")
     return dict(zip(("ctas", "passed", "gave_up", "error_word"), (x.value for x in v)))
+
+
+def measure_fp64_rate(kind=0, iters=4096, stream=None) -> dict:
+    """psolve_measure_fp64_rate: FP64 instructions per second of this GPU
+    (kind 0: fused multiply-add, 1: add), the timed run's ms and SM clock."""
+    rate, ms, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = lib().psolve_measure_fp64_rate(int(kind), int(iters), _stream_handle(stream), ctypes.byref(rate),
+                                        ctypes.byref(ms), ctypes.byref(mhz))
+    if st != OK:
+        raise PsolveError(st, "psolve_measure_fp64_rate")
+    return {"instr_per_s": rate.value, "ms": ms.value, "sm_mhz": mhz.value}
 
 
 def dot_noalloc(a, b, stream=None) -> float:

@@ -1013,6 +1013,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     R.plan.rr_every = c->opts.rr_every;
     R.plan.neumann = P.desc.bcm != 0;
     R.plan.split = sweep_split(R.plan.prec, P.desc.zc);
+    R.plan.wide = wide_sweeps(R.plan, P.desc.tma != 0);
     R.use_graph = c->opts.use_graph != 0;
     R.timing = c->opts.timing != 0;
     R.npts = (double)P.npts();
@@ -1257,6 +1258,7 @@ psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, 
     plan.exact_bounds = c->opts.lmin_scale == 1.0 && c->opts.lmax_scale == 1.0;
     plan.neumann = P.desc.bcm != 0;
     plan.split = sweep_split(plan.prec, P.desc.zc);
+    plan.wide = wide_sweeps(plan, P.desc.tma != 0);
     Launcher L = ctx_launcher(c);
     enqueue_precond(L, plan);
     PS_CK(L.err);
@@ -1469,6 +1471,9 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         int min_zc = 1 << 30;
         for (const Problem &P : probs) min_zc = std::min(min_zc, (int)P.desc.zc);
         R.plan.split = sweep_split(R.plan.prec, min_zc);
+        bool all_tma = true;
+        for (const Problem &P : probs) all_tma = all_tma && P.desc.tma != 0;
+        R.plan.wide = wide_sweeps(R.plan, all_tma);
     }
     R.use_graph = o.use_graph != 0;
     R.timing = o.timing != 0;

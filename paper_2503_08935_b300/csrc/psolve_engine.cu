@@ -67,7 +67,7 @@ static cudaError_t op_config(int *occ_out)
         e = cudaFuncSetAttribute(k_engine<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
         if (e != cudaSuccess) return e;
         int n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_engine<Op>, NTHREADS, dyn);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_engine<Op>, op_threads<Op>(), dyn);
         if (e != cudaSuccess) return e;
         o = n < 1 ? 1 : n;
         occ[dev].store(o, std::memory_order_release);
@@ -110,7 +110,7 @@ void Launcher::go(int cls, int side, KArgs a, double bytes_per_pt, double half_b
         if (err != cudaSuccess) return;
         cudaEventRecord(rec.ev0, stream);
     }
-    k_engine<Op><<<(int)g, NTHREADS, engine_dyn_smem<Op>(), stream>>>(a);
+    k_engine<Op><<<(int)g, op_threads<Op>(), engine_dyn_smem<Op>(), stream>>>(a);
     st = cudaGetLastError();
     if (st != cudaSuccess && err == cudaSuccess) err = st;
     if (timing) cudaEventRecord(rec.ev1, stream);
@@ -176,10 +176,11 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
 
 // --------------------------------------------------- per-iteration kernels --
 template <class T, bool BLK>
-static void iteration_cheb(Launcher &L, int d, bool eb, bool rr, bool neu, int split)
+static void iteration_cheb(Launcher &L, const Plan &p)
 {
-    if (eb) prog_iteration_cheb<T, BLK, false>(L, d, L.iter, rr, neu, split);
-    else prog_iteration_cheb<T, BLK, true>(L, d, L.iter, rr, neu, split);
+    const bool rr = p.rr_every > 0;
+    if (p.exact_bounds) prog_iteration_cheb<T, BLK, false>(L, p.degree, L.iter, rr, p.neumann, p.split, p.wide);
+    else prog_iteration_cheb<T, BLK, true>(L, p.degree, L.iter, rr, p.neumann, p.split, p.wide);
 }
 
 void enqueue_iteration(Launcher &L, const Plan &plan)
@@ -193,16 +194,16 @@ void enqueue_iteration(Launcher &L, const Plan &plan)
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
     switch (plan.prec) {
     case PSOLVE_FP32:
-        if (blk) iteration_cheb<float, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
-        else iteration_cheb<float, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
+        if (blk) iteration_cheb<float, true>(L, plan);
+        else iteration_cheb<float, false>(L, plan);
         break;
     case PSOLVE_BF16:
-        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
-        else iteration_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
+        if (blk) iteration_cheb<__nv_bfloat16, true>(L, plan);
+        else iteration_cheb<__nv_bfloat16, false>(L, plan);
         break;
     default:
-        if (blk) iteration_cheb<double, true>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
-        else iteration_cheb<double, false>(L, plan.degree, plan.exact_bounds, rr, plan.neumann, plan.split);
+        if (blk) iteration_cheb<double, true>(L, plan);
+        else iteration_cheb<double, false>(L, plan);
         break;
     }
 }
@@ -233,8 +234,11 @@ void enqueue_dot(Launcher &L)
 // reads v through ROLE_R (the caller points ROLE_R at v and sets first = 1,
 // iter = 0), then the sweeps, then a widening copy of p^ into ROLE_V.
 template <class T, bool BLK>
-static void precond_cheb(Launcher &L, int d, bool eb, bool neu, int split)
+static void precond_cheb(Launcher &L, const Plan &p)
 {
+    const int d = p.degree;
+    const bool eb = p.exact_bounds, neu = p.neumann, wide = p.wide;
+    const int split = p.split;
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
     KArgs a{};
@@ -244,8 +248,8 @@ static void precond_cheb(Launcher &L, int d, bool eb, bool neu, int split)
     constexpr bool U = !MIX; // y_1 stored scaled (FP64, d >= 2)
     if (U && d >= 2) L.go<OpCiFirst<T, BLK, SIDE_P, U>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
     else L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
-    if (eb) prog_sweeps<T, TB, BLK, false>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split);
-    else prog_sweeps<T, TB, BLK, true>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split);
+    if (eb) prog_sweeps<T, TB, BLK, false>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split, wide);
+    else prog_sweeps<T, TB, BLK, true>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split, wide);
     KArgs w{};
     w.in = ROLE_PH;
     w.out = ROLE_V;
@@ -257,16 +261,16 @@ void enqueue_precond(Launcher &L, const Plan &plan)
     const bool blk = plan.precond != PSOLVE_PC_CHEB;
     switch (plan.prec) {
     case PSOLVE_FP32:
-        if (blk) precond_cheb<float, true>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
-        else precond_cheb<float, false>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
+        if (blk) precond_cheb<float, true>(L, plan);
+        else precond_cheb<float, false>(L, plan);
         break;
     case PSOLVE_BF16:
-        if (blk) precond_cheb<__nv_bfloat16, true>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
-        else precond_cheb<__nv_bfloat16, false>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
+        if (blk) precond_cheb<__nv_bfloat16, true>(L, plan);
+        else precond_cheb<__nv_bfloat16, false>(L, plan);
         break;
     default:
-        if (blk) precond_cheb<double, true>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
-        else precond_cheb<double, false>(L, plan.degree, plan.exact_bounds, plan.neumann, plan.split);
+        if (blk) precond_cheb<double, true>(L, plan);
+        else precond_cheb<double, false>(L, plan);
         break;
     }
 }

@@ -48,12 +48,23 @@ struct Plan {
     int rr_every = 0;          // residual replacement period (0: none)
     bool neumann = false;      // the grid has zero-flux Neumann faces
     int split = 1;             // sub-units per work unit for the Chebyshev sweeps (see sweep_split)
+    bool wide = false;         // Chebyshev sweeps in the two-points-per-thread form (see wide_sweeps)
     bool operator==(const Plan &o) const
     {
         return precond == o.precond && degree == o.degree && prec == o.prec && exact_bounds == o.exact_bounds &&
-               rr_every == o.rr_every && neumann == o.neumann && split == o.split;
+               rr_every == o.rr_every && neumann == o.neumann && split == o.split && wide == o.wide;
     }
 };
+
+// Whether the Chebyshev sweeps of `plan` run two x-adjacent points per thread
+// (OpCiSweepW): FP32 or BF16 vectors, G(CI) (no block restriction), no
+// Neumann face, and every problem of the launch list on the TMA ring
+// (all_tma).  The FP32 sweeps are limited by instruction issue at one point
+// per thread; the FP64 sweeps are bound by the FP64 pipe and keep one.
+inline bool wide_sweeps(const Plan &p, bool all_tma)
+{
+    return all_tma && p.prec != PSOLVE_FP64 && p.precond == PSOLVE_PC_CHEB && !p.neumann;
+}
 
 // Sub-units per work unit for the Chebyshev sweeps of a launch list whose
 // smallest slab is min_zc planes.  The FP64 sweeps are bound by the FP64
@@ -79,6 +90,7 @@ struct LaunchRec {
 
 // Issues kernels (or only records what it would issue, dry = true).
 struct Launcher {
+    static constexpr bool WIDE_SWEEPS = true; // runs the wide sweeps of a plan that allows them
     cudaStream_t stream = 0;
     int sms = 1;               // SMs of the device
     long long units = 1;       // units of the launch list (upper bound)

@@ -215,7 +215,8 @@ enum Epi {
     EPI_REPLACE  // v0 = r~ . r, v1 = ||r||^2 of r = b - A x -> rescale beta, rho; test
 };
 
-constexpr int ST_OK = 0, ST_NOT_CONVERGED = 4, ST_BREAKDOWN = 5, ST_NONFINITE = 6;
+constexpr int ST_OK = 0, ST_INTERNAL = 3 /* PSOLVE_E_CUDA */, ST_NOT_CONVERGED = 4, ST_BREAKDOWN = 5,
+              ST_NONFINITE = 6;
 
 __device__ __forceinline__ void stop_with(volatile Scal *sc, int status)
 {
@@ -593,6 +594,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 
 constexpr int align128(int b) { return (b + 127) & ~127; }
 
+// Ring stages an operation asks for (0: as many as fit in 48 KB, 4..8).
+template <class Op, class = void>
+struct RingStages {
+    static constexpr int value = 0;
+};
+template <class Op>
+struct RingStages<Op, std::void_t<decltype(Op::RING_STAGES)>> {
+    static constexpr int value = Op::RING_STAGES;
+};
+
 // Shared-memory geometry of one ring stage for an operation.
 template <class Op>
 struct Ring {
@@ -612,7 +623,8 @@ struct Ring {
     static constexpr bool UX = Op::XFORM && !std::is_same<U, C>::value;
     static constexpr int XBYTES = Op::XFORM ? align128(HBOX * (int)sizeof(C)) + (UX ? align128(HBOX * (int)sizeof(U)) : 0) : 0;
     static constexpr int STAGES_RAW = (48 * 1024 - 3 * XBYTES) / (STAGE > 0 ? STAGE : 1);
-    static constexpr int STAGES = STAGES_RAW < 4 ? 4 : (STAGES_RAW > 8 ? 8 : STAGES_RAW); // <= MAX_STAGES
+    static constexpr int STAGES_FIT = STAGES_RAW < 4 ? 4 : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+    static constexpr int STAGES = RingStages<Op>::value > 0 ? RingStages<Op>::value : STAGES_FIT; // <= MAX_STAGES
     static constexpr int BYTES = STAGES * STAGE + 3 * XBYTES; // dynamic shared memory
 };
 
@@ -850,6 +862,140 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
 }
 
 // ------------------------------------------------------------------------
+// Wide Chebyshev sweeps (OpCiSweepW): the same TMA ring, with each of
+// TILE_X * TILE_Y / 2 threads computing two x-adjacent points of a plane.
+// Per plane a thread reads its centre pair from the z-queue, the two outer x
+// neighbours as single values, the y neighbours, the next plane's centre and
+// the pointwise operands b and y_{k-2} as pairs, and stores one pair: seven
+// shared-memory reads and one store for two points, where the one-point march
+// spends seven reads and one store per point, and the per-plane work (ring
+// waits, stage bookkeeping, barriers) is shared by two points.  The sweep is
+// limited by instruction issue at one point per thread; the arithmetic and
+// its order are those of the one-point sweep (OpCiSweep::combine), so the
+// results are bitwise the same.  Needs the TMA ring (nx % 8 == 0): a pair
+// never straddles the grid's x end and pair addresses are 2-element aligned.
+// ------------------------------------------------------------------------
+template <class Op>
+__device__ __forceinline__ void march_tma_wide(Op &op, const Desc &D, int tile, int kb, int ke,
+                                               unsigned char *ring, uint64_t *bars, uint32_t &seq, int *s_dead)
+{
+    using R = Ring<Op>;
+    constexpr int S = R::STAGES;
+    constexpr int W = R::W;
+    constexpr int PX = TILE_X / 2; // point pairs along x
+    static_assert(S >= 6, "one CTA barrier per two planes needs six or more stages");
+    static_assert(Op::NH == 1 && Op::NP == 2 && (R::HX % 2) == 0 && (W % 2) == 0, "pair alignment");
+
+    const int nx = D.nx, ny = D.ny;
+    const int plane = nx * ny;
+    const int tid = threadIdx.x, tx = tid % PX, ty = tid / PX;
+    const int i0 = (tile % D.tiles_x) * TILE_X, j0 = (tile / D.tiles_x) * TILE_Y;
+    const int i = i0 + 2 * tx, j = j0 + ty;
+    const bool in = (i < nx) && (j < ny); // nx even: then i + 1 < nx too
+    const int col = in ? j * nx + i : 0;
+    const int me = (ty + 1) * W + R::HX + 2 * tx; // left point of the pair in a halo box (even)
+    const int mp = ty * TILE_X + 2 * tx;          // the same in a plain box (even)
+    const int q0 = kb - 1, q1 = ke;
+    const int nplanes = q1 - q0 + 1;
+    const uint32_t seq0 = seq;
+
+    struct Slot {
+        int st;
+        uint32_t par;
+        __device__ __forceinline__ void next()
+        {
+            if (++st == S) {
+                st = 0;
+                par ^= 1u;
+            }
+        }
+    };
+    Slot sm{(int)(seq0 % S), (seq0 / S) & 1u}; // plane k-1
+    Slot smm = sm;                              // plane k-2
+    Slot sc = sm;
+    sc.next(); // plane k
+    Slot sn = sc;
+    sn.next(); // plane k+1
+    auto stage = [&](int st) { return ring + st * R::STAGE; };
+    auto wait = [&](const Slot &sl) {
+        if (*s_dead) return;
+        if (!mbar_wait(bars + sl.st, sl.par)) {
+            *s_dead = 1;
+            D.sc->status = ST_TIMEOUT;
+            D.sc->stop = 1;
+        }
+    };
+
+    __syncthreads(); // the previous run's readers of the ring are done
+    if (tid == 0) {
+        Slot si = sm;
+        for (int n = 0; n < S && n < nplanes; ++n) {
+            const int q = q0 + n;
+            ring_issue<Op>(op, D, stage(si.st), bars + si.st, i0, j0, q, q >= kb && q < ke);
+            si.next();
+        }
+    }
+    wait(sm);
+    wait(sc);
+    float2 zdn = in ? op.ld2(stage(sm.st), me) : make_float2(0.f, 0.f); // centre pairs of planes k-1, k
+    float2 zc = in ? op.ld2(stage(sc.st), me) : make_float2(0.f, 0.f);
+
+    for (int k = kb; k < ke; ++k) {
+        wait(sn);
+        float2 zup = make_float2(0.f, 0.f);
+        if (in && !*s_dead) {
+            const unsigned char *hs = stage(sc.st);
+            const unsigned char *ps = hs + R::HSTRIDE;
+            zup = op.ld2(stage(sn.st), me);
+            const float w = op.ld1(hs, me - 1), e = op.ld1(hs, me + 2);
+            const float2 so = op.ld2(hs, me - W), no = op.ld2(hs, me + W);
+            const float2 b = op.ld2(ps, mp);
+            const float2 z = op.k >= 3 ? op.ld2(ps + R::PSTRIDE, mp) : make_float2(0.f, 0.f);
+            op.emit2(col + k * plane, zc, make_float2(w + zc.y, zc.x + e), make_float2(so.x + no.x, so.y + no.y),
+                     make_float2(zdn.x + zup.x, zdn.y + zup.y), b, z);
+        }
+        if ((k - kb) & 1) {
+            // one CTA barrier per two planes: the stages of planes k-2 and k-1
+            // are free and both refills go out in plane order (plane k+1 went
+            // out at least three planes ahead, as in the one-point sweep)
+            __syncthreads();
+            if (tid == 0 && !*s_dead) {
+                if (k - 2 + S <= q1) {
+                    const int q = k - 2 + S;
+                    ring_issue<Op>(op, D, stage(smm.st), bars + smm.st, i0, j0, q, q >= kb && q < ke);
+                }
+                if (k - 1 + S <= q1) {
+                    const int q = k - 1 + S;
+                    ring_issue<Op>(op, D, stage(sm.st), bars + sm.st, i0, j0, q, q >= kb && q < ke);
+                }
+            }
+        }
+        smm = sm;
+        sm = sc;
+        sc = sn;
+        sn.next();
+        zdn = zc;
+        zc = zup;
+    }
+    seq = seq0 + nplanes;
+}
+
+// Whether an operation is a wide sweep, and the CTA size of its kernel.
+template <class Op, class = void>
+struct IsWide {
+    static constexpr bool value = false;
+};
+template <class Op>
+struct IsWide<Op, std::void_t<decltype(Op::WIDE)>> {
+    static constexpr bool value = Op::WIDE;
+};
+template <class Op>
+constexpr int op_threads()
+{
+    return IsWide<Op>::value ? NTHREADS / 2 : NTHREADS;
+}
+
+// ------------------------------------------------------------------------
 // The generic kernel: take units from the launch list until it is exhausted.
 // ------------------------------------------------------------------------
 // Shared-memory state of a CTA, reused by every phase a CTA runs.
@@ -925,8 +1071,15 @@ __device__ __forceinline__ void engine_body(const KArgs &a, EngineShared &sh)
                     ke = min(ke, kb + part);
                 }
                 if (kb < ke) {
-                    if (D.tma) march_tma<Op>(op, D, tile, c0, kb, ke, sh.dyn, sh.bars, sh.seq, sh.sred, sh.s_dead);
-                    else march_stencil<Op>(op, D, tile, c0, kb, ke, sp, sh.sred);
+                    if constexpr (IsWide<Op>::value) {
+                        // the host runs wide sweeps only on lists of TMA problems
+                        if (D.tma) march_tma_wide<Op>(op, D, tile, kb, ke, sh.dyn, sh.bars, sh.seq, sh.s_dead);
+                        else if (threadIdx.x == 0) stop_with(sc, ST_INTERNAL);
+                    } else if (D.tma) {
+                        march_tma<Op>(op, D, tile, c0, kb, ke, sh.dyn, sh.bars, sh.seq, sh.sred, sh.s_dead);
+                    } else {
+                        march_stencil<Op>(op, D, tile, c0, kb, ke, sp, sh.sred);
+                    }
                 }
             } else {
                 march_point<Op>(op, D, tile, c0, c0 + 1, sh.sred);
@@ -1009,7 +1162,7 @@ struct MinBlocks<Op, std::void_t<decltype(Op::MIN_BLOCKS)>> {
 };
 
 template <class Op>
-__global__ void __launch_bounds__(NTHREADS, MinBlocks<Op>::value) k_engine(KArgs a)
+__global__ void __launch_bounds__(op_threads<Op>(), MinBlocks<Op>::value) k_engine(KArgs a)
 {
     __shared__ double sred[(NTHREADS / 32) * MAX_DOTS];
     __shared__ alignas(8) uint64_t bars[MAX_STAGES];
@@ -1026,7 +1179,9 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<Op>::value) k_engine(KArgs
 template <class Op>
 constexpr int engine_dyn_smem()
 {
-    if constexpr (Op::STENCIL) {
+    if constexpr (IsWide<Op>::value) {
+        return Ring<Op>::BYTES; // TMA ring only
+    } else if constexpr (Op::STENCIL) {
         constexpr int lsu = 2 * (TILE_X + 2) * (TILE_Y + 2) * (int)sizeof(typename Op::C);
         return Ring<Op>::BYTES > lsu ? Ring<Op>::BYTES : lsu;
     } else {
@@ -1248,16 +1403,77 @@ struct OpCiSweep {
         if (k >= 3) v.z = E::lds(p[1], x);
         return v;
     }
+    // the new iterate at one point from its centre value, neighbour-pair sums,
+    // b and z
+    __device__ __forceinline__ C combine(C yc, C sx, C sy, C sz, C b, C z) const
+    {
+        C v;
+        if constexpr (UNIT && WITH_Y) v = fma(c_y, yc, b);
+        else if constexpr (UNIT) v = b;
+        else if constexpr (WITH_Y) v = fma(c_b, b, c_y * yc);
+        else v = c_b * b;
+        if (k >= 3) v = fma(c_z, z, v);
+        return fma(c_zz, sz, fma(c_yy, sy, fma(c_x, sx, v)));
+    }
     template <int NA>
     __device__ __forceinline__ void emit(int idx, C yc, C sx, C sy, C sz, C, const PW &p, double (&)[NA]) const
     {
-        C v;
-        if constexpr (UNIT && WITH_Y) v = fma(c_y, yc, p.b);
-        else if constexpr (UNIT) v = p.b;
-        else if constexpr (WITH_Y) v = fma(c_b, p.b, c_y * yc);
-        else v = c_b * p.b;
-        if (k >= 3) v = fma(c_z, p.z, v);
-        E::st(out, idx, fma(c_zz, sz, fma(c_yy, sy, fma(c_x, sx, v))));
+        E::st(out, idx, combine(yc, sx, sy, sz, p.b, p.z));
+    }
+};
+
+// Pairs of x-adjacent Chebyshev-vector elements (wide sweeps): FP32 math on
+// FP32 or BF16 storage, element index even.
+template <class T> struct Pair;
+template <> struct Pair<float> {
+    static __device__ __forceinline__ float2 lds(const void *p, int x)
+    {
+        return *reinterpret_cast<const float2 *>(reinterpret_cast<const float *>(p) + x);
+    }
+    static __device__ __forceinline__ float lds1(const void *p, int x) { return reinterpret_cast<const float *>(p)[x]; }
+    static __device__ __forceinline__ void st(void *p, int x, float2 v)
+    {
+        *reinterpret_cast<float2 *>(reinterpret_cast<float *>(p) + x) = v;
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 lds(const void *p, int x)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(reinterpret_cast<const __nv_bfloat16 *>(p) + x));
+    }
+    static __device__ __forceinline__ float lds1(const void *p, int x)
+    {
+        return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[x]);
+    }
+    static __device__ __forceinline__ void st(void *p, int x, float2 v)
+    {
+        // each element rounded to nearest even, as Elem<__nv_bfloat16>::st does
+        *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(p) + x) = __floats2bfloat162_rn(v.x, v.y);
+    }
+};
+
+// Chebyshev sweep k >= 2 with FP32 or BF16 vectors on the whole grid (no block
+// restriction, no Neumann face), two x-adjacent points per thread
+// (march_tma_wide; 128 threads per CTA).  Same coefficients, arithmetic and
+// results as OpCiSweep<T, T, false, WY, false>.
+template <class T, bool WY>
+struct OpCiSweepW : OpCiSweep<T, T, false, WY, false, false> {
+    using Base = OpCiSweep<T, T, false, WY, false, false>;
+    static_assert(std::is_same<typename Base::C, float>::value, "wide sweeps are the FP32-math forms");
+    static constexpr bool WIDE = true;
+    // 64 registers a thread at 8 CTAs of 128 threads per SM; six ring stages
+    // (22 KB with FP32 vectors) let that many CTAs fit in shared memory
+    static constexpr int MIN_BLOCKS = 8;
+    static constexpr int RING_STAGES = 6;
+    __device__ OpCiSweepW(const Desc &D, const KArgs &a, Scal *sc) : Base(D, a, sc) {}
+    __device__ __forceinline__ float2 ld2(const void *p, int x) const { return Pair<T>::lds(p, x); }
+    __device__ __forceinline__ float ld1(const void *p, int x) const { return Pair<T>::lds1(p, x); }
+    __device__ __forceinline__ void emit2(int idx, float2 yc, float2 sx, float2 sy, float2 sz, float2 b,
+                                          float2 z) const
+    {
+        Pair<T>::st(this->out, idx,
+                    make_float2(this->combine(yc.x, sx.x, sy.x, sz.x, b.x, z.x),
+                                this->combine(yc.y, sx.y, sy.y, sz.y, b.y, z.y)));
     }
 };
 

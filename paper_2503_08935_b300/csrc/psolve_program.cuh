@@ -34,12 +34,33 @@ __host__ __device__ void prog_replace(V &v)
     v.template go<OpReplace>(PSOLVE_K_OTHER, 2, a, 32.0);
 }
 
-// One sweep of kind (NEU, UNIT) chosen at run time.
+// Whether a program runner V launches wide sweeps (OpCiSweepW, 128-thread
+// CTAs): the per-kernel launcher does; the persistent kernel, whose CTAs all
+// have 256 threads, does not.
+template <class V, class = void>
+struct RunsWide {
+    static constexpr bool value = false;
+};
+template <class V>
+struct RunsWide<V, std::void_t<decltype(V::WIDE_SWEEPS)>> {
+    static constexpr bool value = V::WIDE_SWEEPS;
+};
+
+// One sweep of kind (NEU, UNIT) chosen at run time; `wide`: the launch list
+// allows the two-points-per-thread form (FP32/BF16 vectors, whole grid, no
+// Neumann face, TMA ring), which computes the same values.
 #pragma nv_exec_check_disable
 template <class T, class TB, bool BLK, bool WY, class V>
-__host__ __device__ void prog_sweep(V &v, int cls, int side, const KArgs &a, double bytes, bool neu, bool unit)
+__host__ __device__ void prog_sweep(V &v, int cls, int side, const KArgs &a, double bytes, bool neu, bool unit,
+                                    bool wide = false)
 {
     constexpr bool U = !is_mixed<T>(); // the scaled-iterate form exists for FP64 vectors
+    if constexpr (RunsWide<V>::value && is_mixed<T>() && !BLK) {
+        if (wide && !neu) {
+            v.template go<OpCiSweepW<T, WY>>(cls, side, a, bytes);
+            return;
+        }
+    }
     if (neu && unit) v.template go<OpCiSweep<T, TB, BLK, WY, true, U>>(cls, side, a, bytes);
     else if (neu) v.template go<OpCiSweep<T, TB, BLK, WY, true, false>>(cls, side, a, bytes);
     else if (unit) v.template go<OpCiSweep<T, TB, BLK, WY, false, U>>(cls, side, a, bytes);
@@ -56,7 +77,7 @@ __host__ __device__ void prog_sweep(V &v, int cls, int side, const KArgs &a, dou
 #pragma nv_exec_check_disable
 template <class T, class TB, bool BLK, bool WY, class V>
 __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final_role, int skip, bool neu,
-                                     int split = 1)
+                                     int split = 1, bool wide = false)
 {
     const double c = sizeof(T), cb = sizeof(TB);
     for (int k = 2; k <= d; ++k) {
@@ -70,7 +91,7 @@ __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final
         a.b = brole;
         const int cls = (k == 2) ? PSOLVE_K_CI_SWEEP3 : PSOLVE_K_CI_SWEEP4;
         const double bytes = (k == 2) ? c + cb + c : c + cb + c + c;
-        prog_sweep<T, TB, BLK, WY>(v, cls, side, a, bytes, neu, !is_mixed<T>());
+        prog_sweep<T, TB, BLK, WY>(v, cls, side, a, bytes, neu, !is_mixed<T>(), wide);
     }
 }
 
@@ -80,7 +101,8 @@ __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final
 // then, when rr, the residual replacement.
 #pragma nv_exec_check_disable
 template <class T, bool BLK, bool WY, class V>
-__host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, bool neu, int split = 1)
+__host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, bool neu, int split = 1,
+                                             bool wide = false)
 {
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
     constexpr bool MIX = is_mixed<T>();
@@ -97,7 +119,7 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, boo
         if (U && d >= 2) v.template go<OpCiFirst<T, BLK, SIDE_P, U>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
         else v.template go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
     }
-    prog_sweeps<T, TB, BLK, WY>(v, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP, neu, split);
+    prog_sweeps<T, TB, BLK, WY>(v, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP, neu, split, wide);
     {
         KArgs a{};
         a.skip = SKIP_STOP;
@@ -114,7 +136,8 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, boo
         if (U && d >= 2) v.template go<OpCiFirst<T, BLK, SIDE_S, U>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
         else v.template go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
     }
-    prog_sweeps<T, TB, BLK, WY>(v, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF, neu, split);
+    prog_sweeps<T, TB, BLK, WY>(v, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF, neu, split,
+                                wide);
     {
         KArgs a{};
         a.skip = SKIP_STOP | SKIP_HALF;

@@ -183,3 +183,96 @@ extern "C" PSOLVE_API psolve_status psolve_selfcheck_grid_timeout(int64_t limit_
     *error_word = g.err;
     return PSOLVE_OK;
 }
+
+namespace {
+
+// FP64 instruction throughput: every thread runs FP64_CHAINS independent
+// chains of `iters` dependent FP64 instructions (kind 0: fused multiply-add,
+// kind 1: add), so the FP64 pipe, not latency, limits the loop.  Thread 0 of
+// CTA 0 records the SM clock and the global timer around its loop, which
+// gives the SM clock the run saw.  The chains' sum is stored only when it
+// equals an impossible value, which keeps them live without a store per
+// thread.
+constexpr int FP64_CHAINS = 8;
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_fp64_rate(long long iters, double a, double c, double *sink,
+                                                   long long *clk)
+{
+    double v[FP64_CHAINS];
+#pragma unroll
+    for (int q = 0; q < FP64_CHAINS; ++q) v[q] = 1e-3 * (double)(threadIdx.x + 8 * q + 1);
+    long long c0 = 0, t0 = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c0 = clock64();
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    }
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < FP64_CHAINS; ++q) v[q] = KIND == 0 ? fma(v[q], a, c) : v[q] + c;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long t1;
+        const long long c1 = clock64();
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        clk[0] = c1 - c0;
+        clk[1] = t1 - t0;
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < FP64_CHAINS; ++q) s += v[q];
+    if (s == -1.25e300) sink[0] = s;
+}
+
+} // namespace
+
+extern "C" PSOLVE_API psolve_status psolve_measure_fp64_rate(int32_t kind, int64_t iters, uintptr_t stream,
+                                                             double *instr_per_s, double *ms_out,
+                                                             double *sm_mhz)
+{
+    clear_error();
+    if (!instr_per_s || (kind != 0 && kind != 1) || iters < 1 || iters > (1LL << 24)) {
+        set_error("bad argument");
+        return PSOLVE_E_ARG;
+    }
+    DevInfo di;
+    psolve_status st = device_info(&di);
+    if (st != PSOLVE_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = 8 * di.sms; // 8 CTAs of 256 threads: every SM full
+    double *d_sink = nullptr;
+    long long *d_clk = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PS_CK(cudaMalloc(&d_sink, sizeof(double) + 2 * sizeof(long long)));
+    d_clk = reinterpret_cast<long long *>(d_sink + 1);
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // the multiplier is below 1 and the addend small, so the chains stay finite
+    const double a = 0.999999, c = 1e-7;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) { // the first run warms up
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) {
+            if (kind == 0) k_fp64_rate<0><<<grid, 256, 0, s>>>((long long)iters, a, c, d_sink, d_clk);
+            else k_fp64_rate<1><<<grid, 256, 0, s>>>((long long)iters, a, c, d_sink, d_clk);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    long long clk[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(clk, d_clk, sizeof clk, cudaMemcpyDeviceToHost);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d_sink);
+    if (e != cudaSuccess) {
+        set_error("FP64 rate measurement: %s", cudaGetErrorString(e));
+        return PSOLVE_E_CUDA;
+    }
+    const double instr = (double)grid * 256.0 * FP64_CHAINS * (double)iters;
+    *instr_per_s = instr / (ms * 1e-3);
+    if (ms_out) *ms_out = ms;
+    if (sm_mhz) *sm_mhz = clk[1] > 0 ? (double)clk[0] / (double)clk[1] * 1e3 : 0.0;
+    return PSOLVE_OK;
+}

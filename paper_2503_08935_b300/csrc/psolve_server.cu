@@ -117,7 +117,9 @@ constexpr int MAX_GROUPS = 32; // distinct preconditioners per server
 
 // The requests that share one preconditioner share every launch of a round:
 // one device launch list and one captured graph per group, created by the
-// worker thread when the group first has an active request.
+// worker thread when the group first has an active request.  Each
+// preconditioner has two launch groups: requests on the TMA ring, whose FP32
+// or BF16 G(CI) sweeps run two points per thread (wide_sweeps), and the rest.
 struct Group {
     Plan plan;
     int32_t *d_list = nullptr;
@@ -133,7 +135,7 @@ struct psolve_server {
     cudaStream_t stream = 0, cap = 0;
     int max_slots = 0;
     std::vector<Plan> plans; // plans[g]: launch group g (guarded by mu)
-    Group groups[MAX_GROUPS];
+    Group groups[2 * MAX_GROUPS]; // groups[2 g + tma]: preconditioner g, problems on the TMA ring or not
     double budget = 0;
     int round_iters = 2;
     char *pool_mem = nullptr;
@@ -198,16 +200,21 @@ Launcher server_launcher(psolve_server *s, const int32_t *d_list)
     return L;
 }
 
-// Device list, pinned list and captured round graph of group gi (worker
-// thread, on first use).
+// The launch group of an admitted request (its descriptor's TMA flag is set
+// at admission and kept).
+int launch_group(const Request &r) { return 2 * r.group + (r.prob.desc.tma ? 1 : 0); }
+
+// Device list, pinned list and captured round graph of launch group gi
+// (worker thread, on first use).
 cudaError_t ensure_group(psolve_server *s, int gi)
 {
     Group &G = s->groups[gi];
     if (G.graph) return cudaSuccess;
     {
         std::lock_guard<std::mutex> lock(s->mu);
-        G.plan = s->plans[gi];
+        G.plan = s->plans[gi / 2];
     }
+    G.plan.wide = wide_sweeps(G.plan, (gi & 1) != 0);
     cudaError_t e;
     if (!G.d_list && (e = cudaMalloc(&G.d_list, list_bytes(s->max_slots))) != cudaSuccess) return e;
     if (!G.h_list && (e = cudaHostAlloc(&G.h_list, list_bytes(s->max_slots), cudaHostAllocDefault)) != cudaSuccess)
@@ -302,7 +309,7 @@ void worker_main(psolve_server *s)
 {
     cudaSetDevice(s->di.dev);
     std::vector<int> active, fresh, fin;
-    std::vector<int> by_group[MAX_GROUPS];
+    std::vector<int> by_group[2 * MAX_GROUPS];
     for (;;) {
         // ---- admission
         fresh.clear();
@@ -391,8 +398,8 @@ void worker_main(psolve_server *s)
 
         // ---- one round over every active problem, group by group
         for (auto &v : by_group) v.clear();
-        for (int q : active) by_group[s->slots[q].req.group].push_back(q);
-        for (int gi = 0; gi < MAX_GROUPS; ++gi) {
+        for (int q : active) by_group[launch_group(s->slots[q].req)].push_back(q);
+        for (int gi = 0; gi < 2 * MAX_GROUPS; ++gi) {
             if (by_group[gi].empty()) continue;
             W_CK(ensure_group(s, gi));
             Group &G = s->groups[gi];
@@ -419,7 +426,7 @@ void worker_main(psolve_server *s)
         for (int q : fin) {
             Active &a = s->slots[q];
             const Scal sc = s->h_sc[q];
-            finish(s, a.req, sc, t, s->groups[a.req.group].plan);
+            finish(s, a.req, sc, t, s->groups[launch_group(a.req)].plan);
             {
                 std::lock_guard<std::mutex> lock(s->mu);
                 s->pool.release(a.req.off, a.req.bytes);

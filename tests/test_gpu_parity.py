@@ -70,6 +70,18 @@ def test_bounded_wait_gives_up_and_reports_timeout():
     assert B.selfcheck_wait_timeout(1 << 20) == B.TIMEOUT
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_measured_fp64_rate_is_plausible(kind):
+    """The FP64 roofline's denominator: a B300 SM runs a few FP64 instructions
+    per clock (the fma and add rates agree), so the measured rate per SM per
+    clock lies well inside (0.5, 64), and the run is long enough to time."""
+    r = B.measure_fp64_rate(kind=kind, iters=4096)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert r["ms"] > 1.0 and 500.0 < r["sm_mhz"] < 4000.0
+    per_clk_sm = r["instr_per_s"] / (sms * r["sm_mhz"] * 1e6)
+    assert 0.5 < per_clk_sm < 64.0, per_clk_sm
+
+
 # ---------------------------------------------------------------- stencil --
 @pytest.mark.parametrize("engine", [0, 1])
 @pytest.mark.parametrize("shape", SHAPES)
@@ -291,6 +303,35 @@ def test_engines_agree(prec, precond, blocks):
         outs.append((host(x), info.iterations))
     assert outs[0][1] == outs[1][1]
     assert np.max(np.abs(outs[0][0] - outs[1][0])) <= 1e-12 * np.max(np.abs(outs[1][0]))
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.BF16])
+@pytest.mark.parametrize("shape", [(37, 20, 40), (33, 16, 64), (5, 9, 8)])
+def test_wide_sweeps_bitwise_equal_to_one_point_sweeps(prec, shape):
+    """With FP32/BF16 Chebyshev vectors, G(CI) on the TMA ring runs its sweeps
+    two x-adjacent points per thread; the general engine runs them one point
+    per thread with the same expressions.  M^-1 v (degrees 2, 3, 8: sweep 2
+    without y_{k-2}, sweeps k >= 3 with it) and a whole solve agree bit for
+    bit, on grids with a partial x tile, ragged y tiles and odd plane counts."""
+    h = I.default_h(shape)
+    v = dev(I.rhs_uniform(shape, seed=21))
+    for deg in (2, 3, 8):
+        outs = []
+        for engine in (0, 1):
+            out = torch.empty_like(v)
+            with B.Solver(shape, h, engine=engine, cheb_prec=prec) as s:
+                s.precond_apply(v, out, B.PC_CHEB, deg)
+            outs.append(out)
+        assert torch.equal(outs[0], outs[1]), f"degree {deg}"
+    sols = []
+    for engine in (0, 1):
+        x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+        with B.Solver(shape, h, engine=engine, cheb_prec=prec) as s:
+            info = s.solve(v, x, rtol=1e-9, maxit=300, precond=B.PC_CHEB, degree=8, raise_on_error=False)
+        assert info.engine == (1 if engine == 0 else 0)
+        sols.append((x, info.iterations, info.status))
+    assert sols[0][1] == sols[1][1] and sols[0][2] == sols[1][2]
+    assert torch.equal(sols[0][0], sols[1][0])
 
 
 def test_solve_with_initial_guess():
