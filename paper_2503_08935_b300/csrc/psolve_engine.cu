@@ -246,8 +246,14 @@ static void precond_cheb(Launcher &L, const Plan &p)
     a.in = ROLE_PCUR;
     a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
     constexpr bool U = !MIX; // y_1 stored scaled (FP64, d >= 2)
-    if (U && d >= 2) L.go<OpCiFirst<T, BLK, SIDE_P, U>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
-    else L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
+    if constexpr (MIX) { // the solve's two-pass sweep 1 (OpDirUpdate, then sweep 1 on b_c)
+        L.go<OpDirUpdate<T>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
+        prog_sweep1<T, BLK>(L, 0, a, 0.0, neu, wide);
+    } else if (U && d >= 2) {
+        L.go<OpCiFirst<T, BLK, SIDE_P, U>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
+    } else {
+        L.go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, 0.0);
+    }
     if (eb) prog_sweeps<T, TB, BLK, false>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split, wide);
     else prog_sweeps<T, TB, BLK, true>(L, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, 0, neu, split, wide);
     KArgs w{};

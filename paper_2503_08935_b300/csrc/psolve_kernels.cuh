@@ -491,10 +491,27 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
     if constexpr (ND > 0) flush_unit<ND>(acc, sred, D.partials, unit);
 }
 
-// Pointwise march (no stencil) over chunks [c0, c1) of one tile.  Planes are
-// taken two at a time with both planes' loads issued before either is used
-// (different planes never alias), which doubles the loads in flight.
-// Op provides: struct In; In load(idx); void apply(idx, const In&, acc).
+// Planes a pointwise operation keeps in flight ahead of the one it computes
+// (2, or the operation's PREFETCH: 1 where three planes of inputs would not
+// fit in the registers; 0: load two planes, then compute both).
+template <class Op, class = void>
+struct PointDepth {
+    static constexpr int value = 2;
+};
+template <class Op>
+struct PointDepth<Op, std::void_t<decltype(Op::PREFETCH)>> {
+    static constexpr int value = Op::PREFETCH;
+};
+
+// Pointwise march (no stencil) over chunks [c0, c1) of one tile, software
+// pipelined: while plane k is computed, the loads of planes k+1 and k+2 are
+// in flight (different planes never alias).  A warp that has computed a plane
+// therefore finds the next one arriving instead of issuing its loads only
+// then, which keeps loads in flight during the FP64 work (the update with 6
+// inputs per point is bound by both).  Planes are applied in order, so the
+// per-thread partial sums are the same as with one plane at a time.
+// Op provides: struct In (raw loaded values; narrow types are widened in
+// apply); In load(idx); void apply(idx, const In&, acc).
 template <class Op>
 __device__ __forceinline__ void march_point(Op &op, const Desc &D, int tile, int c0, int c1, double *sred)
 {
@@ -513,13 +530,35 @@ __device__ __forceinline__ void march_point(Op &op, const Desc &D, int tile, int
     for (int q = 0; q < NDA; ++q) acc[q] = 0.0;
     for (int c = c0; c < c1; ++c) {
         const int kb = c * zc, ke = min(nz, (c + 1) * zc);
-        for (int k = kb; k < ke; k += 2) {
-            const bool two = k + 1 < ke;
-            In v0{}, v1{};
-            if (in) v0 = op.load(col + k * plane);
-            if (in && two) v1 = op.load(col + (k + 1) * plane);
-            if (in) op.apply(col + k * plane, v0, acc);
-            if (in && two) op.apply(col + (k + 1) * plane, v1, acc);
+        if constexpr (PointDepth<Op>::value >= 2) {
+            In a{}, b{};
+            if (in) a = op.load(col + kb * plane);
+            if (in && kb + 1 < ke) b = op.load(col + (kb + 1) * plane);
+            for (int k = kb; k < ke; ++k) {
+                In n{};
+                if (in && k + 2 < ke) n = op.load(col + (k + 2) * plane);
+                if (in) op.apply(col + k * plane, a, acc);
+                a = b;
+                b = n;
+            }
+        } else if constexpr (PointDepth<Op>::value == 1) { // one plane ahead (many inputs: registers)
+            In a{};
+            if (in) a = op.load(col + kb * plane);
+            for (int k = kb; k < ke; ++k) {
+                In n{};
+                if (in && k + 1 < ke) n = op.load(col + (k + 1) * plane);
+                if (in) op.apply(col + k * plane, a, acc);
+                a = n;
+            }
+        } else { // two planes loaded, then both computed
+            for (int k = kb; k < ke; k += 2) {
+                const bool two = k + 1 < ke;
+                In v0{}, v1{};
+                if (in) v0 = op.load(col + k * plane);
+                if (in && two) v1 = op.load(col + (k + 1) * plane);
+                if (in) op.apply(col + k * plane, v0, acc);
+                if (in && two) op.apply(col + (k + 1) * plane, v1, acc);
+            }
         }
         if constexpr (ND > 0) flush_unit<ND>(acc, sred, D.partials, c * ntiles + tile);
     }
@@ -884,7 +923,8 @@ __device__ __forceinline__ void march_tma_wide(Op &op, const Desc &D, int tile, 
     constexpr int W = R::W;
     constexpr int PX = TILE_X / 2; // point pairs along x
     static_assert(S >= 6, "one CTA barrier per two planes needs six or more stages");
-    static_assert(Op::NH == 1 && Op::NP == 2 && (R::HX % 2) == 0 && (W % 2) == 0, "pair alignment");
+    static_assert(Op::NH == 1 && (Op::NP == 0 || Op::NP == 2) && (R::HX % 2) == 0 && (W % 2) == 0,
+                  "one halo operand, pair alignment");
 
     const int nx = D.nx, ny = D.ny;
     const int plane = nx * ny;
@@ -962,8 +1002,11 @@ __device__ __forceinline__ void march_tma_wide(Op &op, const Desc &D, int tile, 
             zup = op.ld2(stage(sn.st), me);
             const float w = op.ld1(hs, me - 1), e = op.ld1(hs, me + 2);
             const float2 so = op.ld2(hs, me - W), no = op.ld2(hs, me + W);
-            const float2 b = op.ld2(ps, mp);
-            const float2 z = op.k >= 3 ? op.ld2(ps + R::PSTRIDE, mp) : make_float2(0.f, 0.f);
+            float2 b = make_float2(0.f, 0.f), z = b;
+            if constexpr (Op::NP == 2) { // sweeps k >= 2: b and y_(k-2)
+                b = op.ld2(ps, mp);
+                if (op.k >= 3) z = op.ld2(ps + R::PSTRIDE, mp);
+            }
             op.emit2(col + k * plane, zc, make_float2(w + zc.y, zc.x + e), make_float2(so.x + no.x, so.y + no.y),
                      make_float2(zdn.x + zup.x, zdn.y + zup.y), b, z);
         }
@@ -1312,6 +1355,148 @@ struct OpCiFirst {
     }
 };
 
+// Mixed precision (FP32 / BF16 Chebyshev vectors): CI sweep 1 in two passes.
+// The fused OpCiFirst forms the FP64 right-hand side u on every cell of its
+// halo box (40 % more FP64 work than points) and rounds it there; in the
+// mixed solve that FP64 work and the transform pass bound it.  Here a
+// pointwise pass forms u once per point in FP64 and stores it together with
+// its rounding to the Chebyshev type (the CI right-hand side b_c the sweeps
+// read anyway), and sweep 1 then reads b_c as its stencil input.  The values
+// are those of OpCiFirst: the same expression for u, the same rounding, and
+// the same FP32 expression for y_1 on the rounded values; the extra traffic is
+// one read of b_c.
+
+// p_{i-1} = r + beta (p_{i-2} - omega w)  (p = r on the first iteration) into
+// the current p buffer, and b_c = p_{i-1} rounded (Algorithm 1, last line).
+template <class T>
+struct OpDirUpdate {
+    using C = double;
+    using E = Elem<T>;
+    static constexpr int ND = 0, EPI = EPI_NONE;
+    static constexpr bool STENCIL = false;
+    const double *r, *pold, *w;
+    double *p;
+    void *bc;
+    double beta, omega;
+    int first;
+    __device__ OpDirUpdate(const Desc &D, const KArgs &a, Scal *sc)
+    {
+        const int iter = ld_flag(&sc->iter);
+        r = (const double *)D.vec[ROLE_R];
+        w = (const double *)D.vec[ROLE_W];
+        pold = (const double *)D.vec[resolve_role(ROLE_POLD, iter)];
+        p = (double *)D.vec[resolve_role(a.in, iter)];
+        bc = D.vec[ROLE_BC];
+        beta = ld_scal(&sc->beta);
+        omega = ld_scal(&sc->omega);
+        first = ld_flag(&sc->first);
+    }
+    struct In { double r, p, w; };
+    __device__ __forceinline__ In load(int idx) const
+    {
+        In v{};
+        v.r = gld(r + idx);
+        if (!first) {
+            v.p = gld(pold + idx);
+            v.w = gld(w + idx);
+        }
+        return v;
+    }
+    template <int NA>
+    __device__ __forceinline__ void apply(int idx, const In &v, double (&)[NA]) const
+    {
+        // the expression OpCiFirst<T, BLK, SIDE_P>::load evaluates
+        const double u = first ? v.r : v.r + beta * (v.p - omega * v.w);
+        p[idx] = u;
+        E::st(bc, idx, E::round(u));
+    }
+};
+
+// s = r - alpha w with ||s||^2 (Algorithm 1, half step) and b_c = s rounded.
+template <class T>
+struct OpHalfStep {
+    using C = double;
+    using E = Elem<T>;
+    static constexpr int ND = 1, EPI = EPI_SNORM;
+    static constexpr bool STENCIL = false;
+    const double *r, *w;
+    double *s;
+    void *bc;
+    double alpha;
+    __device__ OpHalfStep(const Desc &D, const KArgs &, Scal *sc)
+    {
+        r = (const double *)D.vec[ROLE_R];
+        w = (const double *)D.vec[ROLE_W];
+        s = (double *)D.vec[ROLE_S];
+        bc = D.vec[ROLE_BC];
+        alpha = ld_scal(&sc->alpha);
+    }
+    struct In { double r, w; };
+    __device__ __forceinline__ In load(int idx) const { return In{gld(r + idx), gld(w + idx)}; }
+    template <int NA>
+    __device__ __forceinline__ void apply(int idx, const In &v, double (&acc)[NA]) const
+    {
+        const double u = v.r - alpha * v.w; // as OpCiFirst<T, BLK, SIDE_S>::load
+        s[idx] = u;
+        acc[0] += u * u;
+        E::st(bc, idx, E::round(u));
+    }
+};
+
+// CI sweep 1 (Algorithm 2, first two steps) on the rounded right-hand side
+// b_c written by OpDirUpdate / OpHalfStep: y_1 = (2 rho_1/delta)(2u - A u/theta)
+// in the Chebyshev type's arithmetic, or z = u/theta for degree 0, with the
+// coefficients OpCiFirst uses (folded on the host).  One point per thread,
+// either engine, block restriction and Neumann faces as the sweeps.
+template <class T, bool BLK>
+struct OpCiFirstC {
+    using E = Elem<T>;
+    using C = typename E::C;
+    using U = C;
+    using PW = NoPW;
+    static constexpr int ND = 0, EPI = EPI_NONE;
+    static constexpr bool STENCIL = true, BLOCKED = BLK;
+    static_assert(!std::is_same<T, double>::value, "the two-pass sweep 1 is the mixed-precision form");
+    using TH = T;
+    using TP = T;
+    static constexpr int NH = 1, NP = 0;
+    static constexpr bool XFORM = false;
+    int nh = 1, np = 0, hrole[NH], prole[1];
+    const void *u;
+    void *out;
+    int degree;
+    C tinv, a_u, a_x, a_y, a_z;
+    __device__ OpCiFirstC(const Desc &D, const KArgs &a, Scal *)
+    {
+        u = D.vec[ROLE_BC];
+        out = D.vec[a.out];
+        hrole[0] = ROLE_BC;
+        prole[0] = 0;
+        degree = D.degree;
+        tinv = (C)D.theta_inv;
+        a_u = (C)D.ci1[0];
+        a_x = (C)D.ci1[1];
+        a_y = (C)D.ci1[2];
+        a_z = (C)D.ci1[3];
+    }
+    __device__ __forceinline__ C load(int idx) const { return E::ld(u, idx); }
+    __device__ __forceinline__ C load_s(const void *const *h, int x) const { return E::lds(h[0], x); }
+    __device__ __forceinline__ C sv(C v) const { return v; }
+    __device__ __forceinline__ PW pw(bool, int) const { return PW{}; }
+    __device__ __forceinline__ PW pw_s(const void *const *, int) const { return PW{}; }
+    // the expression of OpCiFirst::emit (non-scaled form)
+    __device__ __forceinline__ C combine(C b, C sx, C sy, C sz) const
+    {
+        if (degree == 0) return b * tinv;
+        return fma(a_z, sz, fma(a_y, sy, fma(a_x, sx, a_u * b)));
+    }
+    template <int NA>
+    __device__ __forceinline__ void emit(int idx, C b, C sx, C sy, C sz, C, const PW &, double (&)[NA]) const
+    {
+        E::st(out, idx, combine(b, sx, sy, sz));
+    }
+};
+
 // Chebyshev sweep k >= 2 (Algorithm 2 loop body):
 //   w = rho_k (2 sigma y + (2/delta)(b - A y) - rho_{k-1} z),
 // y = y_{k-1} (stencil input), z = y_{k-2} (z = b/theta when k = 2).
@@ -1481,6 +1666,27 @@ struct OpCiSweepW : OpCiSweep<T, T, false, WY, false, false> {
         Pair<T>::st(this->out, idx,
                     make_float2(this->combine(yc.x, sx.x, sy.x, sz.x, b.x, z.x),
                                 this->combine(yc.y, sx.y, sy.y, sz.y, b.y, z.y)));
+    }
+};
+
+// CI sweep 1 on b_c with two x-adjacent points per thread (march_tma_wide;
+// whole grid, no Neumann face, TMA ring): the values of OpCiFirstC.
+template <class T>
+struct OpCiFirstCW : OpCiFirstC<T, false> {
+    using Base = OpCiFirstC<T, false>;
+    static constexpr bool WIDE = true;
+    static constexpr bool NEUMANN = false;
+    // one FP32 halo box per stage (1.7 KB): eight stages, and 8 CTAs of 128
+    // threads per SM at 64 registers
+    static constexpr int MIN_BLOCKS = 8;
+    static constexpr int RING_STAGES = 8;
+    __device__ OpCiFirstCW(const Desc &D, const KArgs &a, Scal *sc) : Base(D, a, sc) {}
+    __device__ __forceinline__ float2 ld2(const void *p, int x) const { return Pair<T>::lds(p, x); }
+    __device__ __forceinline__ float ld1(const void *p, int x) const { return Pair<T>::lds1(p, x); }
+    __device__ __forceinline__ void emit2(int idx, float2 yc, float2 sx, float2 sy, float2 sz, float2, float2) const
+    {
+        Pair<T>::st(this->out, idx,
+                    make_float2(this->combine(yc.x, sx.x, sy.x, sz.x), this->combine(yc.y, sx.y, sy.y, sz.y)));
     }
 };
 
@@ -1769,28 +1975,40 @@ struct OpUpdate {
         alpha_h = alpha * D.inv_cc;
         omega_h = omega * D.inv_cc;
     }
-    struct In { double x, p, r, s, t, rt; };
+    // six inputs per point: one plane ahead with FP32/BF16 p^ and r^ (256^3
+    // update 289 -> 236 us); with FP64 ones the two-planes-then-compute loop
+    // measured faster (227 against 239 us)
+    static constexpr int PREFETCH = std::is_same<T, double>::value ? 0 : 1;
+    using Raw = typename std::conditional<std::is_same<T, double>::value, double, typename Elem<T>::C>::type;
+    struct In { double x; Raw p, r; double s, t, rt; };
     __device__ __forceinline__ In load(int idx) const
     {
         In v{};
         v.x = gld(x + idx);
-        v.p = Elem<T>::wide(ph, idx);
+        v.p = Elem<T>::ld(ph, idx);
         if (!half) {
-            v.r = Elem<T>::wide(rh, idx);
+            v.r = Elem<T>::ld(rh, idx);
             v.s = gld(s + idx);
             v.t = gld(t + idx);
             v.rt = gld(rt + idx);
         }
         return v;
     }
+    // narrow p^, r^ are widened here, when their loads have arrived
+    static __device__ __forceinline__ double widen(Raw v)
+    {
+        if constexpr (std::is_same<Raw, double>::value) return v;
+        else return f2d_exact(v);
+    }
     template <int NA>
     __device__ __forceinline__ void apply(int idx, const In &v, double (&acc)[NA]) const
     {
+        const double p = widen(v.p);
         if (half) {
-            x[idx] = v.x + alpha_h * v.p;
+            x[idx] = v.x + alpha_h * p;
             return;
         }
-        x[idx] = v.x + alpha_h * v.p + omega_h * v.r;
+        x[idx] = v.x + alpha_h * p + omega_h * widen(v.r);
         const double rn = v.s - omega * v.t;
         r[idx] = rn;
         acc[0] += v.rt * rn;
@@ -1897,12 +2115,14 @@ struct OpWiden {
         out = (double *)D.vec[k.out];
         hat = D.hat;
     }
-    struct In { double v; };
-    __device__ __forceinline__ In load(int idx) const { return In{Elem<T>::wide(in, idx)}; }
+    using Raw = typename std::conditional<std::is_same<T, double>::value, double, typename Elem<T>::C>::type;
+    struct In { Raw v; };
+    __device__ __forceinline__ In load(int idx) const { return In{Elem<T>::ld(in, idx)}; }
     template <int NA>
     __device__ __forceinline__ void apply(int idx, const In &v, double (&)[NA]) const
     {
-        out[idx] = v.v * hat;
+        if constexpr (std::is_same<Raw, double>::value) out[idx] = v.v * hat;
+        else out[idx] = f2d_exact(v.v) * hat;
     }
 };
 

@@ -126,15 +126,21 @@ struct Append<TypeList<Ops...>, Op> {
 template <int KIND, class T, bool BLK, bool WY>
 struct PersistOps { // Chebyshev-preconditioned iteration
     using TB = typename std::conditional<is_mixed<T>(), T, double>::type;
-    using Base = TypeList<OpInit0, OpResidual<true>, OpResidual<false>, OpCiFirst<T, BLK, SIDE_P>,
-                          OpCiSweep<T, TB, BLK, WY>, OpStencilDot<T>, OpCiFirst<T, BLK, SIDE_S>, OpStencil2Dot<T>,
-                          OpUpdate<T>, OpReplace>;
-    // FP64: sweep 1 and the sweeps before the last one run the scaled-iterate form
+    using Common = TypeList<OpInit0, OpResidual<true>, OpResidual<false>, OpCiSweep<T, TB, BLK, WY>,
+                            OpStencilDot<T>, OpStencil2Dot<T>, OpUpdate<T>, OpReplace>;
+    // FP64: CI sweep 1 fused with its right-hand side; sweep 1 and the sweeps
+    // before the last one in the scaled-iterate form
+    using Fused = typename Append<typename Append<Common, OpCiFirst<T, BLK, SIDE_P>>::type,
+                                  OpCiFirst<T, BLK, SIDE_S>>::type;
     using Scaled = typename Append<
-        typename Append<typename Append<Base, OpCiSweep<T, TB, BLK, WY, true, true>>::type,
+        typename Append<typename Append<Fused, OpCiSweep<T, TB, BLK, WY, true, true>>::type,
                         OpCiFirst<T, BLK, SIDE_P, true>>::type,
         OpCiFirst<T, BLK, SIDE_S, true>>::type;
-    using List = typename std::conditional<is_mixed<T>(), Base, Scaled>::type;
+    // mixed precision: the pointwise right-hand sides and sweep 1 on b_c
+    using Mixed = typename Append<typename Append<typename Append<Common, OpDirUpdate<T>>::type,
+                                                  OpHalfStep<T>>::type,
+                                  OpCiFirstC<T, BLK>>::type;
+    using List = typename std::conditional<is_mixed<T>(), Mixed, Scaled>::type;
 };
 template <class T, bool BLK, bool WY>
 struct PersistOps<0, T, BLK, WY> { // unpreconditioned iteration

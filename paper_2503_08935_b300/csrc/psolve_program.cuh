@@ -67,6 +67,21 @@ __host__ __device__ void prog_sweep(V &v, int cls, int side, const KArgs &a, dou
     else v.template go<OpCiSweep<T, TB, BLK, WY, false, false>>(cls, side, a, bytes);
 }
 
+// CI sweep 1 of the mixed-precision forms on the rounded right-hand side b_c
+// (OpCiFirstC; two points per thread where the launch list allows it).
+#pragma nv_exec_check_disable
+template <class T, bool BLK, class V>
+__host__ __device__ void prog_sweep1(V &v, int side, const KArgs &a, double bytes, bool neu, bool wide)
+{
+    if constexpr (RunsWide<V>::value && !BLK) {
+        if (wide && !neu) {
+            v.template go<OpCiFirstCW<T>>(PSOLVE_K_CI_FIRST, side, a, bytes);
+            return;
+        }
+    }
+    v.template go<OpCiFirstC<T, BLK>>(PSOLVE_K_CI_FIRST, side, a, bytes);
+}
+
 // Chebyshev sweeps k = 2..d (Algorithm 2 loop).  y_k overwrites y_{k-2}'s
 // buffer (read only at the same point), and the last sweep writes `final_role`.
 // neu: the grid has Neumann faces (else the sweeps compiled without them run).
@@ -109,15 +124,22 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, boo
     constexpr bool U = !MIX; // FP64 vectors: y_1 stored scaled when d >= 2 (OpCiFirst)
     const double c = sizeof(T);
     {
-        // p side: p_{i-1} = r + beta (p_{i-2} - omega w) fused with CI sweep 1
+        // p side: p_{i-1} = r + beta (p_{i-2} - omega w) and CI sweep 1 on it:
+        // fused (FP64, the stencil forms p stencil-wise), or a pointwise pass
+        // that also stores p rounded (b_c) and sweep 1 on b_c (mixed)
         KArgs a{};
         a.skip = SKIP_STOP;
         a.in = ROLE_PCUR;
         a.out = (d <= 1) ? ROLE_PH : ROLE_YA;
         const double rd = (iter == 1) ? 8.0 : 24.0;
-        const double bytes = rd + 8.0 + (MIX ? c : 0.0) + c;
-        if (U && d >= 2) v.template go<OpCiFirst<T, BLK, SIDE_P, U>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
-        else v.template go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
+        if constexpr (MIX) {
+            v.template go<OpDirUpdate<T>>(PSOLVE_K_CI_FIRST, 0, a, rd + 8.0 + c);
+            prog_sweep1<T, BLK>(v, 0, a, 2.0 * c, neu, wide);
+        } else {
+            const double bytes = rd + 8.0 + c;
+            if (U && d >= 2) v.template go<OpCiFirst<T, BLK, SIDE_P, U>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
+            else v.template go<OpCiFirst<T, BLK, SIDE_P>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
+        }
     }
     prog_sweeps<T, TB, BLK, WY>(v, d, 0, MIX ? ROLE_BC : ROLE_PCUR, ROLE_PH, SKIP_STOP, neu, split, wide);
     {
@@ -127,14 +149,23 @@ __host__ __device__ void prog_iteration_cheb(V &v, int d, int iter, bool rr, boo
         v.template go<OpStencilDot<T>>(PSOLVE_K_STENCIL_DOT, 0, a, c + 16.0);
     }
     {
-        // s side: s = r - alpha w fused with CI sweep 1 and ||s||^2
+        // s side: s = r - alpha w with ||s||^2 and CI sweep 1 on it (fused, or
+        // two passes as on the p side; sweep 1 is skipped after a passed
+        // half-step test, like the sweeps after it)
         KArgs a{};
         a.skip = SKIP_STOP;
         a.in = ROLE_S;
         a.out = (d <= 1) ? ROLE_RH : ROLE_YA;
-        const double bytes = 24.0 + (MIX ? c : 0.0) + c;
-        if (U && d >= 2) v.template go<OpCiFirst<T, BLK, SIDE_S, U>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
-        else v.template go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
+        if constexpr (MIX) {
+            v.template go<OpHalfStep<T>>(PSOLVE_K_CI_FIRST, 0, a, 24.0 + c);
+            KArgs b = a;
+            b.skip = SKIP_STOP | SKIP_HALF;
+            prog_sweep1<T, BLK>(v, 1, b, 2.0 * c, neu, wide);
+        } else {
+            const double bytes = 24.0 + c;
+            if (U && d >= 2) v.template go<OpCiFirst<T, BLK, SIDE_S, U>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
+            else v.template go<OpCiFirst<T, BLK, SIDE_S>>(PSOLVE_K_CI_FIRST, 0, a, bytes);
+        }
     }
     prog_sweeps<T, TB, BLK, WY>(v, d, 1, MIX ? ROLE_BC : ROLE_S, ROLE_RH, SKIP_STOP | SKIP_HALF, neu, split,
                                 wide);
