@@ -39,8 +39,8 @@ WORKLOAD = "poisson 256^3 FP64, Bi-CGSTAB + G(CI) Chebyshev degree 8, exact boun
 GOLDEN_256 = os.path.join(ROOT, "tests", "golden", "oracle_256_cheb8.json")
 # ncu summaries of the dominant kernel per Chebyshev precision (the FP32/BF16 sweeps run two points per thread)
 NCU_SUMMARY = {"fp64": os.path.join(ROOT, "profiles", "ncu_ci_sweep4_256_fp64.md"),
-               "fp32": os.path.join(ROOT, "profiles", "ncu_ci_sweep_wide_256_fp32.md"),
-               "bf16": os.path.join(ROOT, "profiles", "ncu_ci_sweep_wide_256_bf16.md")}
+               "fp32": os.path.join(ROOT, "profiles", "ncu_ci_sweep_pair_256_fp32.md"),
+               "bf16": os.path.join(ROOT, "profiles", "ncu_ci_sweep_pair_256_bf16.md")}
 KERNEL_SRC = os.path.join(ROOT, "paper_2503_08935_b300", "csrc", "psolve_kernels.cuh")
 # FP64 instructions per point of a Chebyshev sweep k >= 3 (exact bounds, where the
 # y coefficient vanishes; see OpCiSweep): b, y_{k-2} and the six neighbours of
@@ -105,8 +105,9 @@ def kernel_source_hash():
 
 
 def ncu_traffic_per_point(prec):
-    """DRAM bytes per grid point of one ci_sweep4 launch from the committed ncu
-    summary, or None if there is none or the kernel source changed since."""
+    """DRAM bytes per algorithmic byte of the captured ci_sweep4 launch in the
+    committed ncu summary, or None if there is none or the kernel source
+    changed since."""
     try:
         txt = open(NCU_SUMMARY[prec]).read()
     except OSError:
@@ -119,8 +120,8 @@ def ncu_traffic_per_point(prec):
     if vals.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_point"])
-    except (KeyError, ValueError):
+        return float(vals["dram_bytes_per_point"]) / float(vals["algorithmic_bytes_per_point"])
+    except (KeyError, ValueError, ZeroDivisionError):
         return None
 
 
@@ -389,13 +390,15 @@ def run_gpu(args):
         avg_ms = kms / max(kn, 1)
         per_launch = kbytes / max(kn, 1)
         gbs = per_launch / (avg_ms * 1e-3) / 1e9
-        tpp = ncu_traffic_per_point(args.prec)
+        ratio = ncu_traffic_per_point(args.prec)
         ctype = {"fp64": "double", "fp32": "float", "bf16": "__nv_bfloat16"}[args.prec]
         kname = ("k_engine<OpCiSweep<double,double,...>> (Chebyshev sweeps k>=3, scaled-iterate form)"
                  if args.prec == "fp64" else
-                 f"k_engine<OpCiSweepW<{ctype},...>> (Chebyshev sweeps k>=3, two points per thread)")
+                 f"k_engine<OpCiSweepPairW<{ctype},...>> (Chebyshev sweeps k>=4 two per pass, two points per "
+                 f"thread) with OpCiSweepW (an odd last sweep alone)")
         roof = {"kernel": kname,
-                "traffic": (tpp * npts) if tpp is not None else None,
+                # the captured launch's DRAM bytes per algorithmic byte times this class's algorithmic bytes
+                "traffic": (ratio * kbytes / max(kn, 1)) if ratio is not None else None,
                 "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms, "launches": kn,
                 "share_of_step": kms / ms if ms > 0 else None,
                 "hbm_view": {"achieved_GBps": gbs, "peak_GBps": peak, "frac": gbs / peak,

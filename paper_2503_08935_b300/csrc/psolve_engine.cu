@@ -137,7 +137,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 static bool role_is_ci(int r)
 {
-    return r == ROLE_PH || r == ROLE_RH || r == ROLE_YA || r == ROLE_YB || r == ROLE_BC;
+    return r == ROLE_PH || r == ROLE_RH || r == ROLE_YA || r == ROLE_YB || r == ROLE_BC || r == ROLE_YC ||
+           r == ROLE_YD;
 }
 
 void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
@@ -162,10 +163,12 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
         const cuuint32_t estr[3] = {1, 1, 1};
         const cuuint32_t halo[3] = {(cuuint32_t)(TILE_X + 2 * (16 / es)), (cuuint32_t)(TILE_Y + 2), 1};
         const cuuint32_t plain[3] = {(cuuint32_t)TILE_X, (cuuint32_t)TILE_Y, 1};
-        for (int v = 0; v < 2; ++v) {
+        const cuuint32_t halo2[3] = {(cuuint32_t)(TILE_X + 2 * (16 / es)), (cuuint32_t)(TILE_Y + 4), 1};
+        for (int v = 0; v < TMAPS_PER_ROLE; ++v) {
             // no L2 promotion: the halo boxes start 16 bytes before a line, and
             // promoting their sector reads to whole lines multiplied DRAM reads
-            CUresult e = fn(&maps[2 * r + v], dt, 3, D.vec[r], dims, strides, v == 0 ? halo : plain, estr,
+            const cuuint32_t *box = v == TMAP_HALO ? halo : (v == TMAP_PLAIN ? plain : halo2);
+            CUresult e = fn(&maps[TMAPS_PER_ROLE * r + v], dt, 3, D.vec[r], dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (e != CUDA_SUCCESS) return;
@@ -461,7 +464,9 @@ size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms)
 {
     const size_t N = (size_t)(n[0] * n[1] * n[2]);
     const size_t v64 = align_up(N * 8), vci = align_up(N * ci_elem_bytes(prec));
-    size_t b = v64 * (6 + (with_rt ? 1 : 0)) + vci * (4 + (prec != PSOLVE_FP64 ? 1 : 0));
+    // CI vectors p^, r^, y_a, y_b; mixed precision adds b_c and the paired
+    // sweeps' y_c, y_d
+    size_t b = v64 * (6 + (with_rt ? 1 : 0)) + vci * (4 + (prec != PSOLVE_FP64 ? 3 : 0));
     (void)sms;
     b += align_up(sizeof(Scal)) + align_up((size_t)units_max(n) * MAX_DOTS * sizeof(double));
     return b;
@@ -489,8 +494,10 @@ void problem_bind(Problem &P, char *base)
         q += vci;
     }
     if (P.prec != PSOLVE_FP64) {
-        D.vec[ROLE_BC] = q;
-        q += vci;
+        for (int r : {ROLE_BC, ROLE_YC, ROLE_YD}) {
+            D.vec[r] = q;
+            q += vci;
+        }
     }
     P.d_sc = reinterpret_cast<Scal *>(q);
     q += align_up(sizeof(Scal));
@@ -568,6 +575,16 @@ psolve_status cheb_interval(const Problem &P, int precond, double lmin_scale, do
     return PSOLVE_OK;
 }
 
+// FP32 copies of the folded coefficients, rounded to nearest as the device's
+// double-to-float conversion rounds.
+static void set_cheb_f32(Desc &D)
+{
+    for (int q = 0; q < 4; ++q) D.ci1f[q] = static_cast<float>(D.ci1[q]);
+    for (int k = 0; k <= MAX_DEGREE; ++k)
+        for (int q = 0; q < 6; ++q) D.cikf[k][q] = static_cast<float>(D.cik[k][q]);
+    D.theta_inv_f = static_cast<float>(D.theta_inv);
+}
+
 psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_scale, double lmax_scale)
 {
     Desc &D = P.desc;
@@ -575,6 +592,7 @@ psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_
     set_hat(D, 1.0);
     if (precond == PSOLVE_PC_NONE || precond == PSOLVE_PC_G_BICGS || precond == PSOLVE_PC_BJ_BICGS) {
         D.theta_inv = D.two_over_delta = D.two_sigma = 0.0; // no Chebyshev iteration
+        set_cheb_f32(D);
         return PSOLVE_OK;
     }
     double a, b;
@@ -623,6 +641,7 @@ psolve_status problem_set_cheb(Problem &P, int precond, int degree, double lmin_
         c[5] = rk * tod * D.cz * q1;
     }
     if (degree >= 2) set_hat(D, scale(degree));
+    set_cheb_f32(D);
     return PSOLVE_OK;
 }
 

@@ -676,10 +676,12 @@ __device__ __forceinline__ void ring_issue(const Op &op, const Desc &D, unsigned
     const uint32_t bytes = op.nh * R::HBYTES + (with_pw ? op.np * R::PBYTES : 0);
     mbar_expect_tx(bar, bytes);
     for (int a = 0; a < op.nh; ++a)
-        tma_load_3d(stage + a * R::HSTRIDE, D.tmap + 2 * op.hrole[a], i0 - R::HX, j0 - 1, q, bar);
+        tma_load_3d(stage + a * R::HSTRIDE, D.tmap + TMAPS_PER_ROLE * op.hrole[a] + TMAP_HALO, i0 - R::HX, j0 - 1, q,
+                    bar);
     if (with_pw)
         for (int a = 0; a < op.np; ++a)
-            tma_load_3d(stage + Op::NH * R::HSTRIDE + a * R::PSTRIDE, D.tmap + 2 * op.prole[a] + 1, i0, j0, q,
+            tma_load_3d(stage + Op::NH * R::HSTRIDE + a * R::PSTRIDE, D.tmap + TMAPS_PER_ROLE * op.prole[a] + TMAP_PLAIN,
+                        i0, j0, q,
                         bar);
 }
 
@@ -1045,6 +1047,20 @@ constexpr int op_threads()
     return IsWide<Op>::value ? NTHREADS / 2 : NTHREADS;
 }
 
+// Whether an operation is a pair of Chebyshev sweeps in one pass
+// (OpCiSweepPairW, march_pair_wide, defined with the operations below).
+template <class Op, class = void>
+struct IsPair {
+    static constexpr bool value = false;
+};
+template <class Op>
+struct IsPair<Op, std::void_t<decltype(Op::PAIR)>> {
+    static constexpr bool value = Op::PAIR;
+};
+template <class Op>
+__device__ __forceinline__ void march_pair_wide(Op &op, const Desc &D, int tile, int kb, int ke,
+                                                unsigned char *ring, uint64_t *bars, uint32_t &seq, int *s_dead);
+
 // ------------------------------------------------------------------------
 // The generic kernel: take units from the launch list until it is exhausted.
 // ------------------------------------------------------------------------
@@ -1121,7 +1137,11 @@ __device__ __forceinline__ void engine_body(const KArgs &a, EngineShared &sh)
                     ke = min(ke, kb + part);
                 }
                 if (kb < ke) {
-                    if constexpr (IsWide<Op>::value) {
+                    if constexpr (IsPair<Op>::value) {
+                        // the host runs paired sweeps only on lists of TMA problems
+                        if (D.tma) march_pair_wide<Op>(op, D, tile, kb, ke, sh.dyn, sh.bars, sh.seq, sh.s_dead);
+                        else if (threadIdx.x == 0) stop_with(sc, ST_INTERNAL);
+                    } else if constexpr (IsWide<Op>::value) {
                         // the host runs wide sweeps only on lists of TMA problems
                         if (D.tma) march_tma_wide<Op>(op, D, tile, kb, ke, sh.dyn, sh.bars, sh.seq, sh.s_dead);
                         else if (threadIdx.x == 0) stop_with(sc, ST_INTERNAL);
@@ -1229,7 +1249,9 @@ __global__ void __launch_bounds__(op_threads<Op>(), MinBlocks<Op>::value) k_engi
 template <class Op>
 constexpr int engine_dyn_smem()
 {
-    if constexpr (IsWide<Op>::value) {
+    if constexpr (IsPair<Op>::value) {
+        return Op::DYN_BYTES; // its stages and the y_k planes
+    } else if constexpr (IsWide<Op>::value) {
         return Ring<Op>::BYTES; // TMA ring only
     } else if constexpr (Op::STENCIL) {
         constexpr int lsu = 2 * (TILE_X + 2) * (TILE_Y + 2) * (int)sizeof(typename Op::C);
@@ -1473,11 +1495,11 @@ struct OpCiFirstC {
         hrole[0] = ROLE_BC;
         prole[0] = 0;
         degree = D.degree;
-        tinv = (C)D.theta_inv;
-        a_u = (C)D.ci1[0];
-        a_x = (C)D.ci1[1];
-        a_y = (C)D.ci1[2];
-        a_z = (C)D.ci1[3];
+        tinv = D.theta_inv_f; // FP32 copies rounded on the host
+        a_u = D.ci1f[0];
+        a_x = D.ci1f[1];
+        a_y = D.ci1f[2];
+        a_z = D.ci1f[3];
     }
     __device__ __forceinline__ C load(int idx) const { return E::ld(u, idx); }
     __device__ __forceinline__ C load_s(const void *const *h, int x) const { return E::lds(h[0], x); }
@@ -1569,13 +1591,23 @@ struct OpCiSweep {
         // (Eq. 9: sin^2 a + cos^2 a = 1 per axis, for the grid and for every
         // block), so theta = cc and the y coefficient vanishes; the kernel
         // then skips its multiply.
-        const double *ck = D.cik[a.k];
-        c_y = (C)ck[0];
-        c_b = (C)ck[1];
-        c_z = (C)ck[2];
-        c_x = (C)ck[3];
-        c_yy = (C)ck[4];
-        c_zz = (C)ck[5];
+        if constexpr (std::is_same<C, float>::value) { // rounded on the host (Desc::cikf)
+            const float *ck = D.cikf[a.k];
+            c_y = ck[0];
+            c_b = ck[1];
+            c_z = ck[2];
+            c_x = ck[3];
+            c_yy = ck[4];
+            c_zz = ck[5];
+        } else {
+            const double *ck = D.cik[a.k];
+            c_y = ck[0];
+            c_b = ck[1];
+            c_z = ck[2];
+            c_x = ck[3];
+            c_yy = ck[4];
+            c_zz = ck[5];
+        }
     }
     __device__ __forceinline__ C load(int idx) const { return E::ld(y, idx); }
     __device__ __forceinline__ C load_s(const void *const *h, int x) const { return E::lds(h[0], x); }
@@ -1689,6 +1721,273 @@ struct OpCiFirstCW : OpCiFirstC<T, false> {
                     make_float2(this->combine(yc.x, sx.x, sy.x, sz.x), this->combine(yc.y, sx.y, sy.y, sz.y)));
     }
 };
+
+// A value of FP32 arithmetic as the storage type T holds it (read back as FP32).
+template <class T>
+__device__ __forceinline__ float E_round(float v)
+{
+    if constexpr (std::is_same<T, float>::value) return v;
+    else return __bfloat162float(__float2bfloat16_rn(v));
+}
+// ------------------------------------------------------------------------
+// Temporal blocking of the Chebyshev sweeps (FP32/BF16 vectors, G(CI) on the
+// TMA ring): sweeps k and k+1 in one pass over the grid.  Algorithm 2's
+// recurrence is reduction-free, so sweep k+1 can follow sweep k plane by
+// plane: y_k is computed on the tile and a one-cell ring around it (34 x 10
+// cells), from y_{k-1} staged with a two-cell halo in y (and the aligned
+// four-cell halo in x), then y_{k+1} on the tile from the last three planes
+// of y_k held in shared memory.  One pass reads y_{k-1}, b and y_{k-2} and
+// writes y_k and y_{k+1}: 5 vector accesses for two sweeps instead of 8.  The
+// values are those of two single sweeps: each y_k is rounded to the storage
+// type before sweep k+1 reads it, outside-grid cells of y_k are the zero
+// ghosts, and every expression is OpCiSweep::combine.  y_k and y_{k+1} go to
+// buffers that neither input occupies (the inputs are read with a halo by
+// neighbouring tiles, so nothing is overwritten in place).
+// KArgs: k (the first sweep), in = y_{k-1}, z = y_{k-2} (k >= 3), b = b_c,
+// out = y_k, aux = y_{k+1}.
+// ------------------------------------------------------------------------
+template <class T, bool WY>
+struct OpCiSweepPairW {
+    using E = Elem<T>;
+    using C = float;
+    using U = C;
+    using PW = NoPW;
+    static_assert(!std::is_same<T, double>::value, "paired sweeps are the FP32-arithmetic forms");
+    static constexpr int ND = 0, EPI = EPI_NONE;
+    static constexpr bool STENCIL = true, BLOCKED = false, NEUMANN = false, WIDE = true, PAIR = true;
+    static constexpr int MIN_BLOCKS = 6;
+    // shared-memory geometry: per stage the y_{k-1} box (W x (TILE_Y + 4)),
+    // the b box and the y_{k-2} box (W x (TILE_Y + 2)); the y_k ring of four
+    // planes (W x (TILE_Y + 2) floats each); the same x origin i0 - HX
+    static constexpr int HX = 16 / (int)sizeof(T);
+    static constexpr int W = TILE_X + 2 * HX;
+    static constexpr int AROWS = TILE_Y + 4, BROWS = TILE_Y + 2;
+    static constexpr int ABYTES = W * AROWS * (int)sizeof(T), BBYTES = W * BROWS * (int)sizeof(T);
+    static constexpr int AST = align128(ABYTES), BST = align128(BBYTES);
+    static constexpr int STAGE = AST + 2 * BST;
+    static constexpr int STAGES = 6;
+    static constexpr int YPLANE = W * BROWS; // floats per y_k ring plane
+    static constexpr int DYN_BYTES = STAGES * STAGE + 4 * YPLANE * (int)sizeof(float);
+    static constexpr int EX = TILE_X + 2, EY = TILE_Y + 2; // the tile and its one-cell ring
+    const void *ym1, *bv, *zv;
+    void *out1, *out2;
+    int k, rin, rb, rz;
+    float c1[6], c2[6];
+    __device__ OpCiSweepPairW(const Desc &D, const KArgs &a, Scal *sc)
+    {
+        const int iter = ld_flag(&sc->iter);
+        k = a.k;
+        rin = a.in;
+        rb = resolve_role(a.b, iter);
+        rz = a.z;
+        ym1 = D.vec[rin];
+        bv = D.vec[rb];
+        zv = D.vec[rz];
+        out1 = D.vec[a.out];
+        out2 = D.vec[a.aux];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            c1[q] = D.cikf[a.k][q];
+            c2[q] = D.cikf[a.k + 1][q];
+        }
+    }
+    // OpCiSweep::combine with the coefficients of sweep kk
+    static __device__ __forceinline__ float combine(const float (&c)[6], int kk, float yc, float sx, float sy,
+                                                    float sz, float b, float z)
+    {
+        float v;
+        if constexpr (WY) v = fma(c[1], b, c[0] * yc);
+        else v = c[1] * b;
+        if (kk >= 3) v = fma(c[2], z, v);
+        return fma(c[5], sz, fma(c[4], sy, fma(c[3], sx, v)));
+    }
+    static __device__ __forceinline__ float lds(const unsigned char *p, int x) { return E::lds(p, x); }
+};
+
+// The march of a pair over output planes [kb, ke) of one tile.  Stencil
+// input planes q0 = kb - 2 .. q1 = ke + 1 are staged (b and y_{k-2} for kb - 1
+// .. ke); step p (kb - 2 <= p < ke) computes y_k on plane p+1 over the tile
+// and its ring, then, after one CTA barrier, y_{k+1} on plane p over the
+// tile.  Plane q's stage is last read in step q, so it is refilled (with
+// plane q + S) after the barrier of step q+1; the y_k ring keeps four planes,
+// so the plane written in step p+1 never overlaps one read in step p.
+template <class Op>
+__device__ __forceinline__ void march_pair_wide(Op &op, const Desc &D, int tile, int kb, int ke,
+                                                unsigned char *ring, uint64_t *bars, uint32_t &seq, int *s_dead)
+{
+    using T = typename std::conditional<Op::HX == 4, float, __nv_bfloat16>::type;
+    constexpr int S = Op::STAGES, W = Op::W, HX = Op::HX;
+    constexpr int PX = TILE_X / 2;
+    static_assert(S >= 5 && S <= MAX_STAGES, "stages");
+    const int nx = D.nx, ny = D.ny, nz = D.nz;
+    const int plane = nx * ny;
+    const int tid = threadIdx.x;
+    const int i0 = (tile % D.tiles_x) * TILE_X, j0 = (tile / D.tiles_x) * TILE_Y;
+    const int q0 = kb - 2, q1 = ke + 1;
+    const int nplanes = q1 - q0 + 1;
+    const uint32_t seq0 = seq;
+    float *yring = reinterpret_cast<float *>(ring + S * Op::STAGE);
+    const bool with_z = op.k >= 3;
+    const CUtensorMap *mA = D.tmap + TMAPS_PER_ROLE * op.rin + TMAP_HALO2;
+    const CUtensorMap *mB = D.tmap + TMAPS_PER_ROLE * op.rb + TMAP_HALO;
+    const CUtensorMap *mZ = D.tmap + TMAPS_PER_ROLE * op.rz + TMAP_HALO;
+    // rolling stage index and mbarrier parity of a plane (plane n of this
+    // march lives in stage (seq0 + n - q0) % S), advanced plane by plane
+    struct Slot {
+        int st;
+        uint32_t par;
+        __device__ __forceinline__ void next()
+        {
+            if (++st == S) {
+                st = 0;
+                par ^= 1u;
+            }
+        }
+    };
+    auto stage = [&](const Slot &sl) { return ring + sl.st * Op::STAGE; };
+    auto issue = [&](const Slot &sl, int q) { // thread 0: plane q into the stage of slot sl
+        unsigned char *st = stage(sl);
+        uint64_t *b = bars + sl.st;
+        const bool bz = q >= kb - 1 && q <= ke;
+        const uint32_t bytes = Op::ABYTES + (bz ? Op::BBYTES * (with_z ? 2 : 1) : 0);
+        mbar_expect_tx(b, bytes);
+        tma_load_3d(st, mA, i0 - HX, j0 - 2, q, b);
+        if (bz) {
+            tma_load_3d(st + Op::AST, mB, i0 - HX, j0 - 1, q, b);
+            if (with_z) tma_load_3d(st + Op::AST + Op::BST, mZ, i0 - HX, j0 - 1, q, b);
+        }
+    };
+    auto wait = [&](const Slot &sl) {
+        if (*s_dead) return;
+        if (!mbar_wait(bars + sl.st, sl.par)) {
+            *s_dead = 1;
+            D.sc->status = ST_TIMEOUT;
+            D.sc->stop = 1;
+        }
+    };
+    Slot s0{(int)(seq0 % S), (seq0 / S) & 1u}; // plane p
+    Slot s1 = s0;
+    s1.next(); // plane p + 1
+    Slot s2 = s1;
+    s2.next(); // plane p + 2
+    Slot sr = s0;   // thread 0: the stage of plane nref, the lowest not yet refilled
+    int nref = q0;
+
+    __syncthreads(); // the previous run's readers of the ring are done
+    if (tid == 0) {
+        Slot si = s0;
+        for (int n = 0; n < S && n < nplanes; ++n) {
+            issue(si, q0 + n);
+            si.next();
+        }
+    }
+    wait(s0);
+    wait(s1);
+    // the pair mapping of the tile for y_{k+1}
+    const int tx = tid % PX, ty = tid / PX;
+    const int gi = i0 + 2 * tx, gj = j0 + ty;
+    const bool tin = gi < nx && gj < ny; // nx even: gi + 1 < nx as well
+    const int col = tin ? gj * nx + gi : 0;
+    const int me = (ty + 1) * W + HX + 2 * tx;
+    // the ring cell of this thread (the first NRING threads): the rows above
+    // and below the tile (EX cells each), then the columns left and right of
+    // it (TILE_Y cells each), as an index into a W-wide, EY-row plane
+    constexpr int NRING = 2 * Op::EX + 2 * TILE_Y;
+    static_assert(NRING <= NTHREADS / 2, "one ring cell per thread");
+    int rcell = -1;
+    bool rin_grid = false;
+    if (tid < NRING) {
+        int ex, ey;
+        if (tid < Op::EX) {
+            ex = tid;
+            ey = 0;
+        } else if (tid < 2 * Op::EX) {
+            ex = tid - Op::EX;
+            ey = Op::EY - 1;
+        } else if (tid < 2 * Op::EX + TILE_Y) {
+            ex = 0;
+            ey = 1 + tid - 2 * Op::EX;
+        } else {
+            ex = Op::EX - 1;
+            ey = 1 + tid - 2 * Op::EX - TILE_Y;
+        }
+        rcell = ey * W + HX - 1 + ex;
+        const int ci = i0 - 1 + ex, cj = j0 - 1 + ey;
+        rin_grid = ci >= 0 && ci < nx && cj >= 0 && cj < ny;
+    }
+
+    for (int p = q0; p < ke; ++p) {
+        wait(s2);
+        const bool dead = *s_dead;
+        // y_k on plane p+1: the tile by the pair mapping, its one-cell ring by
+        // the first NRING threads
+        const int qk = p + 1;
+        if (!dead) {
+            const unsigned char *A0 = stage(s0), *A1 = stage(s1), *A2 = stage(s2);
+            const unsigned char *B1 = A1 + Op::AST, *Z1 = A1 + Op::AST + Op::BST;
+            float *Y = yring + (qk & 3) * Op::YPLANE;
+            const bool zin = qk >= 0 && qk < nz;
+            {
+                const int ia = me + W; // the y_{k-1} box has one more halo row on top
+                float2 v = make_float2(0.f, 0.f);
+                if (zin && tin) {
+                    const float2 yc = Pair<T>::lds(A1, ia);
+                    const float w = Op::lds(A1, ia - 1), e = Op::lds(A1, ia + 2);
+                    const float2 so = Pair<T>::lds(A1, ia - W), no = Pair<T>::lds(A1, ia + W);
+                    const float2 dn = Pair<T>::lds(A0, ia), up = Pair<T>::lds(A2, ia);
+                    const float2 b = Pair<T>::lds(B1, me);
+                    const float2 z = with_z ? Pair<T>::lds(Z1, me) : make_float2(0.f, 0.f);
+                    v.x = E_round<T>(Op::combine(op.c1, op.k, yc.x, w + yc.y, so.x + no.x, dn.x + up.x, b.x, z.x));
+                    v.y = E_round<T>(Op::combine(op.c1, op.k, yc.y, yc.x + e, so.y + no.y, dn.y + up.y, b.y, z.y));
+                    if (qk >= kb && qk < ke) Pair<T>::st(op.out1, col + qk * plane, v);
+                }
+                *reinterpret_cast<float2 *>(Y + me) = v;
+            }
+            if (rcell >= 0) {
+                float v = 0.f;
+                if (zin && rin_grid) {
+                    const int ia = rcell + W;
+                    const float yc = Op::lds(A1, ia);
+                    const float sx = Op::lds(A1, ia - 1) + Op::lds(A1, ia + 1);
+                    const float sy = Op::lds(A1, ia - W) + Op::lds(A1, ia + W);
+                    const float sz = Op::lds(A0, ia) + Op::lds(A2, ia);
+                    const float b = Op::lds(B1, rcell);
+                    const float z = with_z ? Op::lds(Z1, rcell) : 0.f;
+                    v = E_round<T>(Op::combine(op.c1, op.k, yc, sx, sy, sz, b, z));
+                }
+                Y[rcell] = v;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) // stages of the planes up to p - 1 are free
+            for (; nref <= p - 1; ++nref) {
+                if (nref + S <= q1 && !*s_dead) issue(sr, nref + S);
+                sr.next();
+            }
+        // y_{k+1} on plane p over the tile
+        if (p >= kb && tin && !dead) {
+            const float *Y0 = yring + ((p - 1) & 3) * Op::YPLANE, *Y1 = yring + (p & 3) * Op::YPLANE,
+                        *Y2 = yring + ((p + 1) & 3) * Op::YPLANE;
+            const unsigned char *Ap = stage(s0), *Bp = Ap + Op::AST;
+            const float2 yc = *reinterpret_cast<const float2 *>(Y1 + me);
+            const float w = Y1[me - 1], e = Y1[me + 2];
+            const float2 so = *reinterpret_cast<const float2 *>(Y1 + me - W);
+            const float2 no = *reinterpret_cast<const float2 *>(Y1 + me + W);
+            const float2 dn = *reinterpret_cast<const float2 *>(Y0 + me);
+            const float2 up = *reinterpret_cast<const float2 *>(Y2 + me);
+            const float2 b = Pair<T>::lds(Bp, me);
+            const float2 z = Pair<T>::lds(Ap, me + W); // y_{k-1} on plane p (rows shifted by the extra halo row)
+            const int kk = op.k + 1;
+            Pair<T>::st(op.out2, col + p * plane,
+                        make_float2(Op::combine(op.c2, kk, yc.x, w + yc.y, so.x + no.x, dn.x + up.x, b.x, z.x),
+                                    Op::combine(op.c2, kk, yc.y, yc.x + e, so.y + no.y, dn.y + up.y, b.y, z.y)));
+        }
+        s0 = s1; // plane p+1 becomes p, p+2 becomes p+1
+        s1 = s2;
+        s2.next();
+    }
+    seq = seq0 + nplanes;
+}
 
 // w = A p^ and r~ . w  (Algorithm 3, first stencil kernel); T = type of p^.
 // w is stored as w' = A q / cc, q = p^ as stored (p^ / Desc::hat): the centre

@@ -89,12 +89,60 @@ __host__ __device__ void prog_sweep1(V &v, int side, const KArgs &a, double byte
 // With FP64 vectors every sweep stores its iterate scaled (OpCiSweep; the
 // last one p^ or r^, divided by Desc::hat); the descriptor's coefficients
 // must be those of degree d.
+// Sweeps k = 2..d two per pass (OpCiSweepPairW) on a wide launch list; an odd
+// last sweep runs alone (OpCiSweepW).  y_1 is in y_a; a pair reads its inputs
+// with a halo, so its outputs go to two of the four work vectors y_a..y_d
+// that hold neither input (the last sweep writes final_role).
+#pragma nv_exec_check_disable
+template <class T, class TB, bool WY, class V>
+__host__ __device__ void prog_sweeps_paired(V &v, int d, int side, int brole, int final_role, int skip)
+{
+    const double c = sizeof(T), cb = sizeof(TB);
+    const int bufs[4] = {ROLE_YA, ROLE_YB, ROLE_YC, ROLE_YD};
+    auto pick = [&](int x0, int x1, int x2) -> int {
+        for (int q = 0; q < 4; ++q)
+            if (bufs[q] != x0 && bufs[q] != x1 && bufs[q] != x2) return bufs[q];
+        return ROLE_YD; // not reached: at most three of the four are excluded
+    };
+    int cur = ROLE_YA, prev = -1; // y_{k-1}, y_{k-2} (none before sweep 2)
+    int k = 2;
+    while (k <= d) {
+        KArgs a{};
+        a.k = k;
+        a.skip = skip;
+        a.in = cur;
+        a.z = prev >= 0 ? prev : ROLE_YB; // unused by sweep 2
+        a.b = brole;
+        const int cls = (k == 2) ? PSOLVE_K_CI_SWEEP3 : PSOLVE_K_CI_SWEEP4;
+        if (k + 1 <= d) {
+            a.out = pick(cur, prev, -1);
+            a.aux = (k + 1 == d) ? final_role : pick(cur, prev, a.out);
+            const double bytes = c + cb + (k >= 3 ? c : 0.0) + 2.0 * c;
+            v.template go<OpCiSweepPairW<T, WY>>(cls, side, a, bytes);
+            prev = a.out;
+            cur = a.aux;
+            k += 2;
+        } else {
+            a.out = final_role;
+            const double bytes = c + cb + (k >= 3 ? c : 0.0) + c;
+            v.template go<OpCiSweepW<T, WY>>(cls, side, a, bytes);
+            k += 1;
+        }
+    }
+}
+
 #pragma nv_exec_check_disable
 template <class T, class TB, bool BLK, bool WY, class V>
 __host__ __device__ void prog_sweeps(V &v, int d, int side, int brole, int final_role, int skip, bool neu,
                                      int split = 1, bool wide = false)
 {
     const double c = sizeof(T), cb = sizeof(TB);
+    if constexpr (RunsWide<V>::value && is_mixed<T>() && !BLK) {
+        if (wide && !neu) {
+            prog_sweeps_paired<T, TB, WY>(v, d, side, brole, final_role, skip);
+            return;
+        }
+    }
     for (int k = 2; k <= d; ++k) {
         KArgs a{};
         a.k = k;

@@ -39,6 +39,8 @@ enum Role : int {
     ROLE_YA,    // Chebyshev work vector (CI type)
     ROLE_YB,    // Chebyshev work vector (CI type)
     ROLE_BC,    // CI right-hand side rounded to the CI type (mixed only)
+    ROLE_YC,    // Chebyshev work vectors of the paired sweeps (CI type, mixed only):
+    ROLE_YD,    // two sweeps per pass read their inputs with a halo, so none is overwritten in place
     ROLE_U,     // input of the building-block entry points (FP64)
     ROLE_V,     // output of the building-block entry points (FP64)
     NROLES,
@@ -95,6 +97,11 @@ struct Desc {
     // a_z) and sweep k >= 2 (c_y, c_b, c_z, c_x, c_yy, c_zz)
     double ci1[4];
     double cik[MAX_DEGREE + 1][6];
+    // the same rounded to FP32 (nearest) for the FP32-arithmetic sweeps, which
+    // would otherwise convert them per work unit on the FP64 pipe
+    float ci1f[4];
+    float cikf[MAX_DEGREE + 1][6];
+    float theta_inv_f;
     // p^ and r^ are stored divided by hat (1 unless FP64 Chebyshev vectors and
     // degree >= 2); w and t are stored as A (stored vector) / cc, and
     // wcx.. = -(cx, cy, cz) / cc are that operator's neighbour coefficients
@@ -103,8 +110,8 @@ struct Desc {
     Scal *sc;
     double *partials;   // units * MAX_DOTS doubles
     // TMA engine: 1 if every stencil operand of this problem can be staged by
-    // tensor copies (nx % 8 == 0, 16-byte aligned vectors); tmap[2*role] is the
-    // role's halo-box map, tmap[2*role + 1] its plain-box map.
+    // tensor copies (nx % 8 == 0, 16-byte aligned vectors); tmap[TMAPS_PER_ROLE
+    // * role + TMAP_HALO / TMAP_PLAIN / TMAP_HALO2] are the role's maps.
     int32_t tma;
     int32_t rr_every;   // residual replacement every rr_every outer iterations (0: never)
     int32_t bcm;        // zero-flux Neumann faces: bit f for face f (x-, x+, y-, y+, z-, z+)
@@ -140,7 +147,11 @@ struct KArgs {
     int32_t split;       // stencil operations without dots: sub-units per work unit (0, 1: none)
 };
 
-constexpr int TMAPS_PER_PROBLEM = 2 * NROLES;
+// Tensor maps per role: the halo box (TILE_X + 2 HX) x (TILE_Y + 2), the
+// plain box TILE_X x TILE_Y and the two-row halo box (TILE_X + 2 HX) x
+// (TILE_Y + 4) that the paired Chebyshev sweeps read their stencil input with.
+constexpr int TMAP_HALO = 0, TMAP_PLAIN = 1, TMAP_HALO2 = 2, TMAPS_PER_ROLE = 3;
+constexpr int TMAPS_PER_PROBLEM = TMAPS_PER_ROLE * NROLES;
 constexpr int ST_TIMEOUT = 7; // a bounded wait of the TMA ring gave up
 
 constexpr int SKIP_STOP = 1; // skip problems whose `stop` is set

@@ -311,13 +311,16 @@ def test_engines_agree(prec, precond, blocks):
 @pytest.mark.parametrize("shape", [(37, 20, 40), (33, 16, 64), (5, 9, 8)])
 def test_wide_sweeps_bitwise_equal_to_one_point_sweeps(prec, shape):
     """With FP32/BF16 Chebyshev vectors, G(CI) on the TMA ring runs its sweeps
-    two x-adjacent points per thread; the general engine runs them one point
-    per thread with the same expressions.  M^-1 v (degrees 2, 3, 8: sweep 2
-    without y_{k-2}, sweeps k >= 3 with it) and a whole solve agree bit for
-    bit, on grids with a partial x tile, ragged y tiles and odd plane counts."""
+    two per pass and two x-adjacent points per thread (CI sweep 1 on the
+    rounded right-hand side, then pairs of sweeps, an odd last one alone); the
+    general engine runs them one sweep and one point at a time with the same
+    expressions.  M^-1 v (degrees 1..5, 8 and 16: sweep 2 without y_{k-2},
+    pairs ending on the last sweep or followed by a single one) and a whole
+    solve agree bit for bit, on grids with a partial x tile, ragged y tiles and
+    odd plane counts."""
     h = I.default_h(shape)
     v = dev(I.rhs_uniform(shape, seed=21))
-    for deg in (2, 3, 8):
+    for deg in (1, 2, 3, 4, 5, 8, 16):
         outs = []
         for engine in (0, 1):
             out = torch.empty_like(v)
