@@ -930,6 +930,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
                            int32_t precond, int32_t degree, psolve_result *res)
 {
     clear_error();
+    Range range("psolve_solve");
     const double t0 = now_s();
     if (!c || !rhs || !x) {
         set_error("null argument");
@@ -1134,6 +1135,7 @@ psolve_status psolve_solve_host(psolve_ctx *c, const double *rhs_host, double *x
                                 int32_t maxit, int32_t precond, int32_t degree, psolve_result *res)
 {
     clear_error();
+    Range range("psolve_solve_host");
     const double t0 = now_s();
     if (!c || !rhs_host || !x_host) {
         set_error("null argument");
@@ -1164,6 +1166,7 @@ psolve_status psolve_solve_host(psolve_ctx *c, const double *rhs_host, double *x
 psolve_status psolve_apply_A(psolve_ctx *c, const double *u, double *out, int32_t block_restricted)
 {
     clear_error();
+    Range range("psolve_apply_A");
     if (!c || !u || !out) {
         set_error("null argument");
         return PSOLVE_E_ARG;
@@ -1208,6 +1211,7 @@ psolve_status psolve_dot(psolve_ctx *c, const double *a, const double *b, double
 psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, int32_t precond, int32_t degree)
 {
     clear_error();
+    Range range("psolve_precond_apply");
     if (!c || !v || !out) {
         set_error("null argument");
         return PSOLVE_E_ARG;
@@ -1284,6 +1288,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
                                  int32_t precond, int32_t degree, const psolve_opts *opts, uintptr_t stream,
                                  psolve_result *results)
 {
+    Range range("psolve_solve_batch");
     clear_error();
     const double t0 = now_s();
     if (count < 1 || !grids || !h || !rhs || !x || !results) {

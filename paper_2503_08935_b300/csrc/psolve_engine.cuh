@@ -11,10 +11,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/psolve.h"
 #include "psolve_program.cuh"
 
 namespace psolve {
+
+// A named range on the calling host thread for profilers that read NVTX
+// annotations (ncu --nvtx, nsys); without such a tool attached it costs a
+// call that returns at once.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // ---------------------------------------------------------------- errors --
 void set_error(const char *fmt, ...);

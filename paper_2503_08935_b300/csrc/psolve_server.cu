@@ -397,6 +397,7 @@ void worker_main(psolve_server *s)
         if (active.empty()) continue;
 
         // ---- one round over every active problem, group by group
+        Range range("psolve_server round");
         for (auto &v : by_group) v.clear();
         for (int q : active) by_group[launch_group(s->slots[q].req)].push_back(q);
         for (int gi = 0; gi < 2 * MAX_GROUPS; ++gi) {
