@@ -468,6 +468,10 @@ struct psolve_ctx {
     double *d_hist = nullptr; // residual history (opts.record_history), 2 doubles per iteration
     int hist_cap = 0;         // iterations d_hist holds
     bool solved = false;      // a solve has run (its scalars are in P.d_sc)
+    TmapCache tmc;            // what h_tmap / d_tmap hold (upload_desc)
+    bool desc_valid = false;  // d_desc equals *h_desc
+    Plan poll_plan;           // the plan poll_K was computed for (poll_K < 0: none)
+    int poll_K = -1;
 };
 
 extern "C" {
@@ -627,14 +631,31 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
     return PSOLVE_OK;
 }
 
+// Brings d_desc and d_tmap up to date with c->P.desc.  Only the tensor maps of
+// vectors that changed since the last upload are encoded and copied, and the
+// descriptor is copied only when it differs from the one on the device: a
+// repeated solve on the same buffers (the small-grid latency case) pays for
+// neither.  Every entry point synchronizes its stream before returning, so
+// the pinned staging copies are never rewritten under a pending copy.
 static psolve_status upload_desc(psolve_ctx *c)
 {
-    problem_encode_tmaps(c->P, c->h_tmap, c->opts.engine != 1 && c->tma_ok);
-    *c->h_desc = c->P.desc;
-    if (c->P.desc.tma)
-        PS_CK(cudaMemcpyAsync(c->d_tmap, c->h_tmap, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM,
-                              cudaMemcpyHostToDevice, c->stream));
-    PS_CK(cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(Desc), cudaMemcpyHostToDevice, c->stream));
+    problem_encode_tmaps(c->P, c->h_tmap, c->opts.engine != 1 && c->tma_ok, &c->tmc);
+    const TmapCache &tc = c->tmc;
+    if (c->P.desc.tma && tc.hi > tc.lo) {
+        const size_t first = (size_t)TMAPS_PER_ROLE * tc.lo, count = (size_t)TMAPS_PER_ROLE * (tc.hi - tc.lo);
+        cudaError_t e = cudaMemcpyAsync(c->d_tmap + first, c->h_tmap + first, sizeof(CUtensorMap) * count,
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            c->tmc.valid = false;
+            PS_CK(e);
+        }
+    }
+    if (!c->desc_valid || std::memcmp(c->h_desc, &c->P.desc, sizeof(Desc)) != 0) {
+        *c->h_desc = c->P.desc;
+        c->desc_valid = false;
+        PS_CK(cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(Desc), cudaMemcpyHostToDevice, c->stream));
+        c->desc_valid = true;
+    }
     return PSOLVE_OK;
 }
 
@@ -1026,7 +1047,9 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     R.h_sc[1] = c->h_sc + 1;
     R.poll_ev[0] = c->poll_ev[0];
     R.poll_ev[1] = c->poll_ev[1];
-    {
+    if (c->poll_K < 0 || !(c->poll_plan == R.plan)) {
+        // the automatic poll period from one iteration's launches and bytes
+        // (a dry run of the sequence); it depends on the plan alone
         std::vector<LaunchRec> recs;
         Launcher Dry;
         Dry.dry = true;
@@ -1036,8 +1059,10 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
         enqueue_iteration(Dry, R.plan);
         double b = 0;
         for (const LaunchRec &r : recs) b += r.bytes;
-        R.K = c->opts.poll_every > 0 ? c->opts.poll_every : auto_poll(b, (int)recs.size());
+        c->poll_plan = R.plan;
+        c->poll_K = auto_poll(b, (int)recs.size());
     }
+    R.K = c->opts.poll_every > 0 ? c->opts.poll_every : c->poll_K;
 
     const bool tr = c->opts.true_residual != 0;
     if (c->opts.persistent) {

@@ -141,17 +141,40 @@ static bool role_is_ci(int r)
            r == ROLE_YD;
 }
 
-void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
+void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow, TmapCache *cache)
 {
     Desc &D = P.desc;
-    D.tma = 0;
-    if (!allow || D.nx % 8 != 0) return;
+    if (cache) {
+        cache->lo = cache->hi = 0;
+        if (cache->valid && cache->allow == allow && std::memcmp(cache->vec, D.vec, sizeof D.vec) == 0) {
+            D.tma = cache->tma;
+            return;
+        }
+    }
+    // a role keeps its maps when the cache holds valid maps of the same vector
+    const bool keep_any = cache && cache->valid && cache->tma;
+    auto finish = [&](int tma, int lo, int hi) {
+        D.tma = tma;
+        if (!cache) return;
+        cache->valid = true;
+        cache->allow = allow;
+        cache->tma = tma;
+        std::memcpy(cache->vec, D.vec, sizeof D.vec);
+        cache->lo = lo;
+        cache->hi = hi;
+    };
+    if (!allow || D.nx % 8 != 0) return finish(0, 0, 0);
     for (int r = 0; r < NROLES; ++r)
-        if (D.vec[r] && (reinterpret_cast<uintptr_t>(D.vec[r]) % 16) != 0) return;
+        if (D.vec[r] && (reinterpret_cast<uintptr_t>(D.vec[r]) % 16) != 0) return finish(0, 0, 0);
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (!fn) return;
-    std::memset(maps, 0, sizeof(CUtensorMap) * TMAPS_PER_PROBLEM);
+    if (!fn) return finish(0, 0, 0);
+    int lo = NROLES, hi = 0;
     for (int r = 0; r < NROLES; ++r) {
+        if (keep_any && cache->vec[r] == D.vec[r]) continue;
+        lo = std::min(lo, r);
+        hi = r + 1;
+        CUtensorMap *m = &maps[TMAPS_PER_ROLE * r];
+        std::memset(m, 0, sizeof(CUtensorMap) * TMAPS_PER_ROLE);
         if (!D.vec[r]) continue;
         const bool ci = role_is_ci(r);
         const size_t es = ci ? ci_elem_bytes(P.prec) : 8;
@@ -168,13 +191,18 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow)
             // no L2 promotion: the halo boxes start 16 bytes before a line, and
             // promoting their sector reads to whole lines multiplied DRAM reads
             const cuuint32_t *box = v == TMAP_HALO ? halo : (v == TMAP_PLAIN ? plain : halo2);
-            CUresult e = fn(&maps[TMAPS_PER_ROLE * r + v], dt, 3, D.vec[r], dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (e != CUDA_SUCCESS) return;
+            CUresult e = fn(&m[v], dt, 3, D.vec[r], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (e != CUDA_SUCCESS) {
+                if (cache) cache->valid = false;
+                D.tma = 0;
+                return;
+            }
         }
     }
-    D.tma = 1;
+    if (lo >= hi) lo = hi = 0;
+    finish(1, lo, hi);
 }
 
 // --------------------------------------------------- per-iteration kernels --

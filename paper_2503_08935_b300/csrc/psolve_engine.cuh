@@ -186,10 +186,24 @@ void enqueue_gather_blocks(cudaStream_t s, const double *src, double *dst, const
 // the sweep's sub-units per work unit (sweep_split).
 void enqueue_tune_probe(Launcher &L, int prec, bool blk, int split);
 
-// Encode the tensor maps of every bound vector of P into maps[0..2*NROLES)
-// and set P.desc.tma (1 when the TMA engine can run this problem: nx % 8 == 0,
-// every vector 16-byte aligned, and `allow`).
-void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow);
+// What problem_encode_tmaps last wrote into one maps array: the vectors it
+// encoded, `allow`, the resulting P.desc.tma, and the roles [lo, hi) whose
+// maps the last call rewrote (empty: the array is unchanged).
+struct TmapCache {
+    bool valid = false;
+    bool allow = false;
+    int tma = 0;
+    void *vec[NROLES] = {};
+    int lo = 0, hi = 0;
+};
+
+// Encode the tensor maps of every bound vector of P into
+// maps[0..TMAPS_PER_PROBLEM) and set P.desc.tma (1 when the TMA engine can run
+// this problem: nx % 8 == 0, every vector 16-byte aligned, and `allow`).  With
+// a cache, the maps of roles whose vector is the one encoded last time are
+// kept as they are (the grid and the precision of a Problem never change), and
+// cache->lo/hi name the roles rewritten.
+void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow, TmapCache *cache = nullptr);
 
 // Algorithmic bytes of the launches in `recs` that did work, given the exit
 // iteration and whether it was a half-step exit.

@@ -460,16 +460,38 @@ def test_argument_errors():
                     torch.zeros((4, 4, 4), dtype=torch.float64, device=DEV), precond=B.PC_CHEB, degree=2)
 
 
-def test_repeated_solves_reuse_context():
-    shape = (20, 20, 20)
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+def test_repeated_solves_reuse_context(prec):
+    """One context across solves on different buffers, with A u and M^-1 v
+    calls in between (they bind other vectors to the descriptor): every result
+    is bitwise that of a fresh context, so the tensor maps and the descriptor
+    a context keeps from one call to the next always describe the buffers of
+    the current call."""
+    shape = (20, 24, 32)  # nx % 8 == 0: the TMA engine, whose maps are cached
     h = I.default_h(shape)
-    with B.Solver(shape, h) as s:
-        res = []
-        for seed in (1, 2, 1):
-            x = torch.zeros(shape, dtype=torch.float64, device=DEV)
-            s.solve(dev(I.rhs_uniform(shape, seed=seed)), x, precond=B.PC_CHEB, degree=4)
-            res.append(host(x))
-    assert np.array_equal(res[0], res[2]) and not np.array_equal(res[0], res[1])
+    bs = [dev(I.rhs_uniform(shape, seed=seed)) for seed in (1, 2, 3)]  # all alive: distinct addresses
+    xs = [torch.zeros(shape, dtype=torch.float64, device=DEV) for _ in range(3)]
+    u = dev(I.rhs_uniform(shape, seed=9))
+    ref_x, outs = {}, {}
+    for q in range(3):
+        with B.Solver(shape, h, cheb_prec=prec) as f:
+            xr = torch.zeros(shape, dtype=torch.float64, device=DEV)
+            f.solve(bs[q], xr, precond=B.PC_CHEB, degree=4)
+            ref_x[q] = host(xr)
+    with B.Solver(shape, h, cheb_prec=prec) as f:
+        ref_au = host(f.apply_A(u, torch.empty_like(u)))
+        ref_mv = host(f.precond_apply(u, torch.empty_like(u), B.PC_CHEB, 4))
+    with B.Solver(shape, h, cheb_prec=prec) as s:
+        for k, (q, j) in enumerate([(0, 0), (1, 1), (0, 2), (2, 0), (0, 0), (1, 2)]):
+            xs[j].zero_()
+            s.solve(bs[q], xs[j], precond=B.PC_CHEB, degree=4)
+            assert np.array_equal(host(xs[j]), ref_x[q]), (k, q, j)
+            outs.setdefault(k % 2, torch.empty_like(u))
+            if k % 2 == 0:
+                assert np.array_equal(host(s.apply_A(u, outs[0])), ref_au), k
+            else:
+                assert np.array_equal(host(s.precond_apply(u, outs[1], B.PC_CHEB, 4)), ref_mv), k
+    assert not np.array_equal(ref_x[0], ref_x[1])
 
 
 # ------------------------------------------------------------------ batch --
