@@ -695,9 +695,21 @@ def extra_serve(B, I, torch, stream, n_req, factors=(0.8,), budget=120e9, max_sl
             infos = [srv.wait(t, timeout=600) for t in tickets]
             wall = time.perf_counter() - start
             lat = np.array([i.seconds for i in infos]) * 1e3
+            pts = np.array([b.numel() for b in bs], dtype=np.float64)
+            # latency by request size: thirds of the stream by grid points
+            cuts = np.percentile(pts, [100 / 3, 200 / 3])
+            thirds = {}
+            for name, sel in (("small", pts <= cuts[0]), ("medium", (pts > cuts[0]) & (pts <= cuts[1])),
+                              ("large", pts > cuts[1])):
+                if sel.any():
+                    thirds[name] = {"max_points": float(pts[sel].max()), "p50_ms": float(np.percentile(lat[sel], 50)),
+                                    "p99_ms": float(np.percentile(lat[sel], 99))}
             out[f"at_{f:.1f}_mu"] = {"offered_rate": lam, "solves_per_s": n_req / wall,
                                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                                      "mean_ms": float(lat.mean()),
+                                     "by_size": thirds,
+                                     # algorithmic bytes of every served solve over the wall time
+                                     "model_GBps": float(sum(i.model_bytes for i in infos) / wall / 1e9),
                                      "all_ok": all(i.status == B.OK for i in infos),
                                      "max_true_residual": max(i.rel_res_true for i in infos)}
     # the same requests solved one after another on the same GPU, same settings:
