@@ -109,9 +109,12 @@ typedef struct {
                                 (0 = never).  Meant for the mixed-precision
                                 forms; not part of the paper's method.       */
     int32_t engine;          /* stencil kernels: 0 = TMA ring where possible
-                                (nx % 8 == 0, 16-byte aligned vectors), else
-                                the general engine; 1 = always the general
-                                engine (no tensor copies)                     */
+                                (16-byte aligned vectors; when nx is not a
+                                multiple of 8 the context lays its vectors out
+                                with rows padded to one and copies b and x
+                                through padded staging vectors), else the
+                                general engine; 1 = always the general engine
+                                (no tensor copies, no padding)                */
     int32_t persistent;      /* 1: run the whole solve (r0, every outer
                                 iteration, the exit true residual) as ONE
                                 cooperative kernel launch whose phases are

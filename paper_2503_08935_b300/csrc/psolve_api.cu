@@ -588,8 +588,11 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
         for (int f = 0; f < 6; ++f) P.bc[f] = bc[f];
     P.prec = o.cheb_prec;
     P.have_rt = o.use_x0 != 0;
+    // rows padded to a multiple of 8 elements when nx is not one, so that the
+    // tensor copies can run on the grid (unless the general engine is forced)
+    P.px = (o.engine != 1 && P.n[0] % 8 != 0) ? padded_pitch(P.n[0]) : 0;
     problem_geometry(P, c->di.sms);
-    P.mem_bytes = problem_bytes(P.n, P.prec, P.have_rt, c->di.sms);
+    P.mem_bytes = problem_bytes(P.n, P.prec, P.have_rt, c->di.sms, P.px);
 #define CREATE_CK(call)                                                                          \
     do {                                                                                         \
         cudaError_t e_ = (call);                                                                 \
@@ -711,9 +714,13 @@ static psolve_status flex_setup(psolve_ctx *c, int precond)
             Q.bc[2 * d + 1] = B[d] == nb[d] - 1 ? P.bc[2 * d + 1] : 0;
         }
         Q.prec = PSOLVE_FP64;
+        if (!bj) { // G(BiCGS) binds the outer vectors: the same row pitch, nothing to stage
+            Q.px = P.px;
+            Q.no_stage = true;
+        }
         problem_geometry(Q, c->di.sms, 0, nblk); // the blocks share every launch
         offs[q] = total;
-        total += problem_bytes(Q.n, PSOLVE_FP64, false, c->di.sms);
+        total += problem_bytes(Q.n, PSOLVE_FP64, false, c->di.sms, Q.px, Q.no_stage);
     }
     const size_t M = (size_t)(m[0] * m[1] * m[2]);
     const size_t list_bytes = sizeof(int32_t) * (LIST_HDR_INTS + 2 * (size_t)nblk);
@@ -771,7 +778,7 @@ static psolve_status flex_inner(psolve_ctx *c, const double *v, double *out, dou
     const bool bj = F.precond == PSOLVE_PC_BJ_BICGS;
     const size_t M = (size_t)(F.probs[0].npts());
     if (bj) {
-        enqueue_gather_blocks(c->stream, v, F.bbuf, c->P.n, c->P.blocks, true);
+        enqueue_gather_blocks(c->stream, v, F.bbuf, c->P.n, c->P.pitch(), c->P.blocks, true);
         PS_CK(cudaGetLastError());
         ++*launches;
     }
@@ -830,7 +837,7 @@ static psolve_status flex_inner(psolve_ctx *c, const double *v, double *out, dou
     }
     *inner_iters += worst;
     if (bj) {
-        enqueue_gather_blocks(c->stream, F.xbuf, out, c->P.n, c->P.blocks, false);
+        enqueue_gather_blocks(c->stream, F.xbuf, out, c->P.n, c->P.pitch(), c->P.blocks, false);
         PS_CK(cudaGetLastError());
         ++*launches;
     }
@@ -909,7 +916,7 @@ static psolve_status flex_solve(psolve_ctx *c, int precond, int maxit, bool use_
         if (st != PSOLVE_OK) return st;
     }
     launches += L.launches;
-    if (hs->zero_x) PS_CK(cudaMemsetAsync(P.desc.vec[ROLE_X], 0, sizeof(double) * (size_t)P.npts(), c->stream));
+    if (hs->zero_x) PS_CK(cudaMemsetAsync(P.desc.vec[ROLE_X], 0, sizeof(double) * (size_t)P.nvec(), c->stream));
     if (tr) {
         Launcher T = ctx_launcher(c);
         T.iter = -1;
@@ -947,11 +954,11 @@ static psolve_status flex_solve(psolve_ctx *c, int precond, int maxit, bool use_
     return (psolve_status)hs->status;
 }
 
-psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double rtol, int32_t maxit,
-                           int32_t precond, int32_t degree, psolve_result *res)
+// psolve_solve without the final copy of x: *bound is set once a context with
+// a padded row pitch has staged b (and x) and runs on the copies.
+static psolve_status solve_impl(psolve_ctx *c, const double *rhs, double *x, double rtol, int32_t maxit,
+                                int32_t precond, int32_t degree, psolve_result *res, bool *bound)
 {
-    clear_error();
-    Range range("psolve_solve");
     const double t0 = now_s();
     if (!c || !rhs || !x) {
         set_error("null argument");
@@ -1009,13 +1016,20 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     D.maxit = maxit;
     D.half_check = c->opts.half_step_check ? 1 : 0;
     D.rr_every = c->opts.rr_every;
-    D.vec[ROLE_B] = (void *)rhs;
-    D.vec[ROLE_X] = x;
-    D.vec[ROLE_RT] = use_x0 ? P.desc.vec[ROLE_RT] : (void *)rhs;
     if (use_x0 && !P.have_rt) {
         set_error("use_x0 needs a context created with opts.use_x0 = 1");
         return PSOLVE_E_ARG;
     }
+    if (P.staged()) { // the caller's rows of nx into the padded copies
+        PS_CK(copy_to_pitched(P, P.d_bst, rhs, c->stream));
+        if (use_x0) PS_CK(copy_to_pitched(P, P.d_xst, x, c->stream));
+        rhs = P.d_bst;
+        x = P.d_xst;
+        *bound = true;
+    }
+    D.vec[ROLE_B] = (void *)rhs;
+    D.vec[ROLE_X] = x;
+    D.vec[ROLE_RT] = use_x0 ? P.desc.vec[ROLE_RT] : (void *)rhs;
     D.vec[ROLE_U] = D.vec[ROLE_V] = nullptr;
     st = upload_desc(c);
     if (st != PSOLVE_OK) return st;
@@ -1080,7 +1094,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
         Scal s = c->h_sc[2];
         if (s.zero_x) {
             // b = 0 with an initial guess: x = 0, and the residual of the zeroed x
-            PS_CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)P.npts(), c->stream));
+            PS_CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)P.nvec(), c->stream));
             if (tr) {
                 Launcher T = R.launcher();
                 T.iter = -1;
@@ -1107,7 +1121,7 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     st = run_loop(R, maxit);
     if (st != PSOLVE_OK) return st;
     Scal s = R.h_sc[R.last_slot][0];
-    if (s.zero_x) PS_CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)P.npts(), c->stream));
+    if (s.zero_x) PS_CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)P.nvec(), c->stream));
     if (tr) {
         Launcher T = R.launcher();
         T.iter = -1;
@@ -1124,6 +1138,24 @@ psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double r
     fill_result(s, P, R.plan, use_x0, tr, t0, R.launches, &tmp);
     if (res) *res = tmp;
     return (psolve_status)s.status;
+}
+
+psolve_status psolve_solve(psolve_ctx *c, const double *rhs, double *x, double rtol, int32_t maxit,
+                           int32_t precond, int32_t degree, psolve_result *res)
+{
+    clear_error();
+    Range range("psolve_solve");
+    bool bound = false;
+    const psolve_status st = solve_impl(c, rhs, x, rtol, maxit, precond, degree, res, &bound);
+    if (bound) { // the solve ran on the padded copies: x back into the caller's rows
+        cudaError_t e = copy_from_pitched(c->P, x, c->P.d_xst, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            set_error("copy of x from the padded layout: %s", cudaGetErrorString(e));
+            return PSOLVE_E_CUDA;
+        }
+    }
+    return st;
 }
 
 psolve_status psolve_history(psolve_ctx *c, int32_t capacity, double *rel_s, double *rel_r, int32_t *count)
@@ -1201,13 +1233,21 @@ psolve_status psolve_apply_A(psolve_ctx *c, const double *u, double *out, int32_
         if (st != PSOLVE_OK) return st;
     }
     PS_CK(cudaSetDevice(c->di.dev));
-    c->P.desc.vec[ROLE_U] = (void *)u;
-    c->P.desc.vec[ROLE_V] = out;
+    const Problem &P = c->P;
+    if (P.staged()) { // padded rows: run on the staging copies
+        PS_CK(copy_to_pitched(P, P.d_bst, u, c->stream));
+        c->P.desc.vec[ROLE_U] = P.d_bst;
+        c->P.desc.vec[ROLE_V] = P.d_xst;
+    } else {
+        c->P.desc.vec[ROLE_U] = (void *)u;
+        c->P.desc.vec[ROLE_V] = out;
+    }
     psolve_status st = upload_desc(c);
     if (st != PSOLVE_OK) return st;
     Launcher L = ctx_launcher(c);
     enqueue_apply_A(L, block_restricted != 0);
     PS_CK(L.err);
+    if (P.staged()) PS_CK(copy_from_pitched(P, out, P.d_xst, c->stream));
     PS_CK(cudaStreamSynchronize(c->stream));
     return PSOLVE_OK;
 }
@@ -1220,6 +1260,13 @@ psolve_status psolve_dot(psolve_ctx *c, const double *a, const double *b, double
         return PSOLVE_E_ARG;
     }
     PS_CK(cudaSetDevice(c->di.dev));
+    const Problem &P = c->P;
+    if (P.staged()) { // padded rows: run on the staging copies
+        PS_CK(copy_to_pitched(P, P.d_bst, a, c->stream));
+        PS_CK(copy_to_pitched(P, P.d_xst, b, c->stream));
+        a = P.d_bst;
+        b = P.d_xst;
+    }
     c->P.desc.vec[ROLE_U] = (void *)a;
     c->P.desc.vec[ROLE_V] = (void *)b;
     psolve_status st = upload_desc(c);
@@ -1258,18 +1305,27 @@ psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, 
         }
         st = flex_setup(c, precond);
         if (st != PSOLVE_OK) return st;
+        const Problem &Q = c->P;
+        if (Q.staged()) PS_CK(copy_to_pitched(Q, Q.d_bst, v, c->stream));
         int64_t iters = 0, launches = 0;
-        st = flex_inner(c, v, out, flex_rtol(c, precond), flex_maxit(c), &iters, &launches);
+        st = flex_inner(c, Q.staged() ? Q.d_bst : v, Q.staged() ? Q.d_xst : out, flex_rtol(c, precond),
+                        flex_maxit(c), &iters, &launches);
         if (st != PSOLVE_OK) return st;
+        if (Q.staged()) PS_CK(copy_from_pitched(Q, out, Q.d_xst, c->stream));
         PS_CK(cudaStreamSynchronize(c->stream));
         return PSOLVE_OK;
     }
     Problem &P = c->P;
     st = problem_set_cheb(P, precond, degree, c->opts.lmin_scale, c->opts.lmax_scale);
     if (st != PSOLVE_OK) return st;
+    if (P.staged()) { // padded rows: run on the staging copies
+        PS_CK(copy_to_pitched(P, P.d_bst, v, c->stream));
+        v = P.d_bst;
+    }
+    double *const out_run = P.staged() ? P.d_xst : out;
     void *saved_r = P.desc.vec[ROLE_R];
     P.desc.vec[ROLE_R] = (void *)v;
-    P.desc.vec[ROLE_V] = out;
+    P.desc.vec[ROLE_V] = out_run;
     st = upload_desc(c);
     P.desc.vec[ROLE_R] = saved_r;
     if (st != PSOLVE_OK) return st;
@@ -1291,6 +1347,7 @@ psolve_status psolve_precond_apply(psolve_ctx *c, const double *v, double *out, 
     Launcher L = ctx_launcher(c);
     enqueue_precond(L, plan);
     PS_CK(L.err);
+    if (P.staged()) PS_CK(copy_from_pitched(P, out, P.d_xst, c->stream));
     PS_CK(cudaStreamSynchronize(c->stream));
     return PSOLVE_OK;
 }
@@ -1367,9 +1424,10 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         P.prec = o.cheb_prec;
         st = check_blocks(P, precond);
         if (st != PSOLVE_OK) return st;
+        P.px = (o.engine != 1 && P.n[0] % 8 != 0) ? padded_pitch(P.n[0]) : 0; // as in psolve_create
         problem_geometry(P, di.sms);
         offs[q] = total_bytes;
-        total_bytes += problem_bytes(P.n, P.prec, false, di.sms);
+        total_bytes += problem_bytes(P.n, P.prec, false, di.sms, P.px);
         total_units += P.desc.units;
     }
     if (total_units >= (1LL << 31)) {
@@ -1463,9 +1521,16 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         P.desc.maxit = maxit;
         P.desc.half_check = o.half_step_check ? 1 : 0;
         P.desc.rr_every = o.rr_every;
-        P.desc.vec[ROLE_B] = (void *)rhs[q];
-        P.desc.vec[ROLE_X] = x[q];
-        P.desc.vec[ROLE_RT] = (void *)rhs[q];
+        const double *bq = rhs[q];
+        double *xq = x[q];
+        if (P.staged()) { // padded rows: the problem runs on its staging copies
+            BATCH_CK(copy_to_pitched(P, P.d_bst, bq, s));
+            bq = P.d_bst;
+            xq = P.d_xst;
+        }
+        P.desc.vec[ROLE_B] = (void *)bq;
+        P.desc.vec[ROLE_X] = xq;
+        P.desc.vec[ROLE_RT] = (void *)bq;
         P.desc.tmap = d_tmap + (size_t)TMAPS_PER_PROBLEM * q;
         problem_encode_tmaps(P, h_tmap + (size_t)TMAPS_PER_PROBLEM * q, o.engine != 1 && tma_ok);
         h_desc[q] = P.desc;
@@ -1555,6 +1620,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
             BATCH_CK(T.err);
         }
     }
+    for (int q = 0; q < count; ++q)
+        if (probs[q].staged()) BATCH_CK(copy_from_pitched(probs[q], x[q], probs[q].d_xst, s));
     BATCH_CK(cudaMemcpyAsync(h_sc, d_sc, sizeof(Scal) * count, cudaMemcpyDeviceToHost, s));
     BATCH_CK(cudaStreamSynchronize(s));
     psolve_status worst = PSOLVE_OK;

@@ -163,7 +163,7 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow, TmapCache *
         cache->lo = lo;
         cache->hi = hi;
     };
-    if (!allow || D.nx % 8 != 0) return finish(0, 0, 0);
+    if (!allow || D.px % 8 != 0) return finish(0, 0, 0);
     for (int r = 0; r < NROLES; ++r)
         if (D.vec[r] && (reinterpret_cast<uintptr_t>(D.vec[r]) % 16) != 0) return finish(0, 0, 0);
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
@@ -182,7 +182,7 @@ void problem_encode_tmaps(Problem &P, CUtensorMap *maps, bool allow, TmapCache *
                                        : P.prec == PSOLVE_FP32      ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
         const cuuint64_t dims[3] = {(cuuint64_t)D.nx, (cuuint64_t)D.ny, (cuuint64_t)D.nz};
-        const cuuint64_t strides[2] = {(cuuint64_t)D.nx * es, (cuuint64_t)D.nx * D.ny * es};
+        const cuuint64_t strides[2] = {(cuuint64_t)D.px * es, (cuuint64_t)D.px * D.ny * es};
         const cuuint32_t estr[3] = {1, 1, 1};
         const cuuint32_t halo[3] = {(cuuint32_t)(TILE_X + 2 * (16 / es)), (cuuint32_t)(TILE_Y + 2), 1};
         const cuuint32_t plain[3] = {(cuuint32_t)TILE_X, (cuuint32_t)TILE_Y, 1};
@@ -372,31 +372,47 @@ void enqueue_flex_phase(Launcher &L, int phase)
 
 // One thread per grid point: (i, j, k) -> block (i / mx, j / my, k / mz),
 // position inside the block; copies in the direction asked for.
-__global__ void k_gather_blocks(const double *src, double *dst, int nx, int ny, int nz, int mx, int my, int mz,
-                                int bx, int by, int to_blocks)
+// The grid side has rows of px elements (its row pitch).
+__global__ void k_gather_blocks(const double *src, double *dst, int nx, int ny, int nz, long long px, int mx, int my,
+                                int mz, int bx, int by, int to_blocks)
 {
     const long long N = (long long)nx * ny * nz;
     const long long M = (long long)mx * my * mz;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((long long)nx * ny));
+        const long long o = i + px * (j + (long long)ny * k);
         const int Bx = i / mx, By = j / my, Bz = k / mz;
         const long long q = Bx + (long long)bx * (By + (long long)by * Bz);
         const long long l = q * M + (i - Bx * mx) + (long long)mx * ((j - By * my) + (long long)my * (k - Bz * mz));
-        if (to_blocks) dst[l] = src[g];
-        else dst[g] = src[l];
+        if (to_blocks) dst[l] = src[o];
+        else dst[o] = src[l];
     }
 }
 
-void enqueue_gather_blocks(cudaStream_t s, const double *src, double *dst, const int64_t n[3], const int blocks[3],
-                           bool to_blocks)
+void enqueue_gather_blocks(cudaStream_t s, const double *src, double *dst, const int64_t n[3], int64_t px,
+                           const int blocks[3], bool to_blocks)
 {
     const long long N = n[0] * n[1] * n[2];
     const int threads = 256;
     const long long want = (N + threads - 1) / threads;
     const int grid = (int)(want < 65535 * 4 ? want : 65535 * 4);
-    k_gather_blocks<<<grid, threads, 0, s>>>(src, dst, (int)n[0], (int)n[1], (int)n[2], (int)(n[0] / blocks[0]),
-                                             (int)(n[1] / blocks[1]), (int)(n[2] / blocks[2]), blocks[0], blocks[1],
-                                             to_blocks ? 1 : 0);
+    k_gather_blocks<<<grid, threads, 0, s>>>(src, dst, (int)n[0], (int)n[1], (int)n[2], (long long)px,
+                                             (int)(n[0] / blocks[0]), (int)(n[1] / blocks[1]),
+                                             (int)(n[2] / blocks[2]), blocks[0], blocks[1], to_blocks ? 1 : 0);
+}
+
+cudaError_t copy_to_pitched(const Problem &P, double *dst, const double *src, cudaStream_t s, cudaMemcpyKind kind)
+{
+    const size_t w = sizeof(double) * (size_t)P.n[0];
+    return cudaMemcpy2DAsync(dst, sizeof(double) * (size_t)P.pitch(), src, w, w, (size_t)(P.n[1] * P.n[2]), kind,
+                             s);
+}
+
+cudaError_t copy_from_pitched(const Problem &P, double *dst, const double *src, cudaStream_t s, cudaMemcpyKind kind)
+{
+    const size_t w = sizeof(double) * (size_t)P.n[0];
+    return cudaMemcpy2DAsync(dst, w, src, sizeof(double) * (size_t)P.pitch(), w, (size_t)(P.n[1] * P.n[2]), kind,
+                             s);
 }
 
 bool launch_did_work(const LaunchRec &r, int final_iter, int half_exit)
@@ -431,6 +447,7 @@ void problem_geometry(Problem &P, int sms, int zc_choice, int copies)
     D.nx = (int)P.n[0];
     D.ny = (int)P.n[1];
     D.nz = (int)P.n[2];
+    D.px = (int)P.pitch();
     D.tiles_x = ceil_div(D.nx, TILE_X);
     D.tiles_y = ceil_div(D.ny, TILE_Y);
     const long long tiles = (long long)D.tiles_x * D.tiles_y;
@@ -488,13 +505,14 @@ static long long units_max(const int64_t n[3])
     return (long long)((n[0] + TILE_X - 1) / TILE_X) * ((n[1] + TILE_Y - 1) / TILE_Y) * n[2];
 }
 
-size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms)
+size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms, int64_t px, bool no_stage)
 {
-    const size_t N = (size_t)(n[0] * n[1] * n[2]);
+    const int64_t p = px ? px : n[0];
+    const size_t N = (size_t)(p * n[1] * n[2]);
     const size_t v64 = align_up(N * 8), vci = align_up(N * ci_elem_bytes(prec));
     // CI vectors p^, r^, y_a, y_b; mixed precision adds b_c and the paired
-    // sweeps' y_c, y_d
-    size_t b = v64 * (6 + (with_rt ? 1 : 0)) + vci * (4 + (prec != PSOLVE_FP64 ? 3 : 0));
+    // sweeps' y_c, y_d; a padded pitch adds the staging copies of b and x
+    size_t b = v64 * (6 + (with_rt ? 1 : 0) + (p != n[0] && !no_stage ? 2 : 0)) + vci * (4 + (prec != PSOLVE_FP64 ? 3 : 0));
     (void)sms;
     b += align_up(sizeof(Scal)) + align_up((size_t)units_max(n) * MAX_DOTS * sizeof(double));
     return b;
@@ -502,7 +520,7 @@ size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms)
 
 void problem_bind(Problem &P, char *base)
 {
-    const size_t N = (size_t)P.npts();
+    const size_t N = (size_t)P.nvec();
     const size_t v64 = align_up(N * 8), vci = align_up(N * ci_elem_bytes(P.prec));
     char *q = base;
     Desc &D = P.desc;
@@ -526,6 +544,13 @@ void problem_bind(Problem &P, char *base)
             D.vec[r] = q;
             q += vci;
         }
+    }
+    P.d_bst = P.d_xst = nullptr;
+    if (P.staged()) {
+        P.d_bst = reinterpret_cast<double *>(q);
+        q += v64;
+        P.d_xst = reinterpret_cast<double *>(q);
+        q += v64;
     }
     P.d_sc = reinterpret_cast<Scal *>(q);
     q += align_up(sizeof(Scal));

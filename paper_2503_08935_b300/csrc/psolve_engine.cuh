@@ -141,11 +141,35 @@ struct Problem {
     size_t mem_bytes = 0;
     Scal *d_sc = nullptr;
     double *d_partials = nullptr;
+    // Row pitch of the workspace vectors in elements (0: nx).  A problem
+    // whose nx is not a multiple of 8 can be laid out with rows padded to one
+    // (padded_pitch), so that the tensor copies run on it; the caller's b and
+    // x (rows of nx) are then copied into d_bst / d_xst (rows of px) before a
+    // solve and x back after it.
+    int64_t px = 0;
+    bool no_stage = false; // padded, but bound only to other padded vectors (no staging copies)
+    double *d_bst = nullptr, *d_xst = nullptr;
+    int64_t pitch() const { return px ? px : n[0]; }
+    bool staged() const { return pitch() != n[0] && !no_stage; }
     int64_t npts() const { return n[0] * n[1] * n[2]; }
+    int64_t nvec() const { return pitch() * n[1] * n[2]; } // elements one vector holds
 };
 
-// Bytes one problem's workspace needs (vectors + partials + scalars).
-size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms);
+// nx rounded up to a multiple of 8: rows of 8-, 4- and 2-byte elements then
+// all start on 16-byte boundaries.
+inline int64_t padded_pitch(int64_t nx) { return (nx + 7) / 8 * 8; }
+
+// Copy a vector with rows of nx (a caller's, `src`) into one with rows of
+// P.pitch() (`dst`), or back; `kind` says which sides are on the host.
+cudaError_t copy_to_pitched(const Problem &P, double *dst, const double *src, cudaStream_t s,
+                            cudaMemcpyKind kind = cudaMemcpyDeviceToDevice);
+cudaError_t copy_from_pitched(const Problem &P, double *dst, const double *src, cudaStream_t s,
+                              cudaMemcpyKind kind = cudaMemcpyDeviceToDevice);
+
+// Bytes one problem's workspace needs (vectors + partials + scalars), for
+// vectors with rows of px elements (0: n[0]); a padded pitch adds the two
+// staging vectors of b and x unless no_stage.
+size_t problem_bytes(const int64_t n[3], int prec, bool with_rt, int sms, int64_t px = 0, bool no_stage = false);
 // Fill the geometry fields of P.desc from P.n, P.h, P.blocks.  The slab depth
 // (planes per unit) is zc_choice when > 0 (a tuned value, at most nz), else
 // the built-in rule, applied to `copies` such problems sharing every launch.
@@ -178,8 +202,8 @@ enum FlexPhase {
 void enqueue_flex_phase(Launcher &L, int phase);
 // Gather a grid vector into block-contiguous storage (block q = Bx + bx (By +
 // by Bz), x fastest inside a block) and back.
-void enqueue_gather_blocks(cudaStream_t s, const double *src, double *dst, const int64_t n[3], const int blocks[3],
-                           bool to_blocks);
+void enqueue_gather_blocks(cudaStream_t s, const double *src, double *dst, const int64_t n[3], int64_t px,
+                           const int blocks[3], bool to_blocks);
 
 // The autotuner's probe kernels (a sweep, a stencil with two dots, an update)
 // for Chebyshev vectors of precision `prec`; needs every role bound.  split:
@@ -199,7 +223,9 @@ struct TmapCache {
 
 // Encode the tensor maps of every bound vector of P into
 // maps[0..TMAPS_PER_PROBLEM) and set P.desc.tma (1 when the TMA engine can run
-// this problem: nx % 8 == 0, every vector 16-byte aligned, and `allow`).  With
+// this problem: a row pitch that is a multiple of 8, every vector 16-byte
+// aligned, and `allow`; the maps span nx columns, so a copy reads zeros for
+// the padding columns as for any cell outside the grid).  With
 // a cache, the maps of roles whose vector is the one encoded last time are
 // kept as they are (the grid and the precision of a Problem never change), and
 // cache->lo/hi name the roles rewritten.

@@ -5,8 +5,8 @@
 // Engines.  A CTA of TILE_X x TILE_Y threads owns an xy tile; each thread owns
 // one z column and marches along z.  Two engines compute bitwise the same
 // values (same thread mapping, same expressions):
-//  * the TMA ring (march_tma, used when nx % 8 == 0 and the vectors are
-//    16-byte aligned): one thread stages whole plane tiles, halo included,
+//  * the TMA ring (march_tma, used when the row pitch is a multiple of 8 and
+//    the vectors are 16-byte aligned): one thread stages whole plane tiles, halo included,
 //    several planes ahead with cp.async.bulk.tensor into a shared-memory ring
 //    tracked by mbarriers, so the bytes in flight do not depend on registers;
 //  * the general engine (march_stencil, any size): u(k-1), u(k), u(k+1) in
@@ -402,13 +402,13 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
     constexpr int SW = TILE_X + 2;
     constexpr int SPL = SW * (TILE_Y + 2);
 
-    const int nx = D.nx, ny = D.ny, nz = D.nz;
-    const int plane = nx * ny;
+    const int nx = D.nx, ny = D.ny, nz = D.nz, px = D.px;
+    const int plane = px * ny;
     const int tid = threadIdx.x, tx = tid % TILE_X, ty = tid / TILE_X;
     const int i0 = (tile % D.tiles_x) * TILE_X, j0 = (tile / D.tiles_x) * TILE_Y;
     const int i = i0 + tx, j = j0 + ty;
     const bool in = (i < nx) && (j < ny);
-    const int col = in ? j * nx + i : 0;
+    const int col = in ? j * px + i : 0;
 
     // halo cell owned by this thread (rows above/below, columns left/right)
     int hs = -1, hi = 0, hj = 0;
@@ -424,7 +424,7 @@ __device__ __forceinline__ void march_stencil(Op &op, const Desc &D, int tile, i
         hs = (r + 1) * SW + TILE_X + 1; hi = i0 + TILE_X; hj = j0 + r;
     }
     const bool hv = hs >= 0 && hi >= 0 && hi < nx && hj >= 0 && hj < ny;
-    const int hcol = hv ? hj * nx + hi : 0;
+    const int hcol = hv ? hj * px + hi : 0;
     const int me = (ty + 1) * SW + tx + 1;
 
     bool okw = true, oke = true, oks = true, okn = true;
@@ -519,11 +519,11 @@ __device__ __forceinline__ void march_point(Op &op, const Desc &D, int tile, int
     constexpr int NDA = ND > 0 ? ND : 1;
     using In = typename Op::In;
     const int nx = D.nx, ny = D.ny, nz = D.nz, zc = D.zc;
-    const int plane = nx * ny;
+    const int plane = D.px * ny;
     const int tid = threadIdx.x, tx = tid % TILE_X, ty = tid / TILE_X;
     const int i = (tile % D.tiles_x) * TILE_X + tx, j = (tile / D.tiles_x) * TILE_Y + ty;
     const bool in = (i < nx) && (j < ny);
-    const int col = in ? j * nx + i : 0;
+    const int col = in ? j * D.px + i : 0;
     const int ntiles = D.tiles_x * D.tiles_y;
     double acc[NDA];
 #pragma unroll
@@ -719,13 +719,13 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
     constexpr int NHA = Op::NH > 0 ? Op::NH : 1;
     constexpr int NPA = Op::NP > 0 ? Op::NP : 1;
 
-    const int nx = D.nx, ny = D.ny, nz = D.nz;
-    const int plane = nx * ny;
+    const int nx = D.nx, ny = D.ny, nz = D.nz, px = D.px;
+    const int plane = px * ny;
     const int tid = threadIdx.x, tx = tid % TILE_X, ty = tid / TILE_X;
     const int i0 = (tile % D.tiles_x) * TILE_X, j0 = (tile / D.tiles_x) * TILE_Y;
     const int i = i0 + tx, j = j0 + ty;
     const bool in = (i < nx) && (j < ny);
-    const int col = in ? j * nx + i : 0;
+    const int col = in ? j * px + i : 0;
     const int me = (ty + 1) * W + tx + R::HX; // this point in a halo box
     const int mp = ty * TILE_X + tx;          // this point in a plain box
 
@@ -913,8 +913,9 @@ __device__ __forceinline__ void march_tma(Op &op, const Desc &D, int tile, int c
 // waits, stage bookkeeping, barriers) is shared by two points.  The sweep is
 // limited by instruction issue at one point per thread; the arithmetic and
 // its order are those of the one-point sweep (OpCiSweep::combine), so the
-// results are bitwise the same.  Needs the TMA ring (nx % 8 == 0): a pair
-// never straddles the grid's x end and pair addresses are 2-element aligned.
+// results are bitwise the same.  Needs the TMA ring (row pitch a multiple of
+// 8): pair addresses are 2-element aligned, and a pair that straddles the
+// grid's x end (nx odd) writes its right value into the row's padding.
 // ------------------------------------------------------------------------
 template <class Op>
 __device__ __forceinline__ void march_tma_wide(Op &op, const Desc &D, int tile, int kb, int ke,
@@ -929,12 +930,15 @@ __device__ __forceinline__ void march_tma_wide(Op &op, const Desc &D, int tile, 
                   "one halo operand, pair alignment");
 
     const int nx = D.nx, ny = D.ny;
-    const int plane = nx * ny;
+    const int plane = D.px * ny;
     const int tid = threadIdx.x, tx = tid % PX, ty = tid / PX;
     const int i0 = (tile % D.tiles_x) * TILE_X, j0 = (tile / D.tiles_x) * TILE_Y;
     const int i = i0 + 2 * tx, j = j0 + ty;
-    const bool in = (i < nx) && (j < ny); // nx even: then i + 1 < nx too
-    const int col = in ? j * nx + i : 0;
+    // with nx odd the pair (nx - 1, nx) stores its right value into column
+    // nx, which the pitch (a multiple of 8) holds as padding and no one reads
+    // as a grid value (the tensor maps end at nx and read zeros beyond it)
+    const bool in = (i < nx) && (j < ny);
+    const int col = in ? j * D.px + i : 0;
     const int me = (ty + 1) * W + R::HX + 2 * tx; // left point of the pair in a halo box (even)
     const int mp = ty * TILE_X + 2 * tx;          // the same in a plain box (even)
     const int q0 = kb - 1, q1 = ke;
@@ -1820,7 +1824,7 @@ __device__ __forceinline__ void march_pair_wide(Op &op, const Desc &D, int tile,
     constexpr int PX = TILE_X / 2;
     static_assert(S >= 5 && S <= MAX_STAGES, "stages");
     const int nx = D.nx, ny = D.ny, nz = D.nz;
-    const int plane = nx * ny;
+    const int plane = D.px * ny;
     const int tid = threadIdx.x;
     const int i0 = (tile % D.tiles_x) * TILE_X, j0 = (tile / D.tiles_x) * TILE_Y;
     const int q0 = kb - 2, q1 = ke + 1;
@@ -1886,8 +1890,8 @@ __device__ __forceinline__ void march_pair_wide(Op &op, const Desc &D, int tile,
     // the pair mapping of the tile for y_{k+1}
     const int tx = tid % PX, ty = tid / PX;
     const int gi = i0 + 2 * tx, gj = j0 + ty;
-    const bool tin = gi < nx && gj < ny; // nx even: gi + 1 < nx as well
-    const int col = tin ? gj * nx + gi : 0;
+    const bool tin = gi < nx && gj < ny; // nx odd: gi + 1 may be the padding column nx (above)
+    const int col = tin ? gj * D.px + gi : 0;
     const int me = (ty + 1) * W + HX + 2 * tx;
     // the ring cell of this thread (the first NRING threads): the rows above
     // and below the tile (EX cells each), then the columns left and right of
@@ -1939,6 +1943,9 @@ __device__ __forceinline__ void march_pair_wide(Op &op, const Desc &D, int tile,
                     const float2 z = with_z ? Pair<T>::lds(Z1, me) : make_float2(0.f, 0.f);
                     v.x = E_round<T>(Op::combine(op.c1, op.k, yc.x, w + yc.y, so.x + no.x, dn.x + up.x, b.x, z.x));
                     v.y = E_round<T>(Op::combine(op.c1, op.k, yc.y, yc.x + e, so.y + no.y, dn.y + up.y, b.y, z.y));
+                    // nx odd: the right point of the last pair is the ghost
+                    // column nx, which y_{k+1} reads as zero (Eq. 4)
+                    if (gi + 1 >= nx) v.y = 0.f;
                     if (qk >= kb && qk < ke) Pair<T>::st(op.out1, col + qk * plane, v);
                 }
                 *reinterpret_cast<float2 *>(Y + me) = v;

@@ -355,9 +355,16 @@ void worker_main(psolve_server *s)
             Request &r = s->slots[slot].req;
             Problem &P = r.prob;
             problem_bind(P, s->pool_mem + r.off); // lays out the workspace; clears every role pointer
-            P.desc.vec[ROLE_B] = (void *)r.rhs;
-            P.desc.vec[ROLE_X] = r.x;
-            P.desc.vec[ROLE_RT] = (void *)r.rhs; // x0 = 0: r~ = r0 = b
+            const double *bq = r.rhs;
+            double *xq = r.x;
+            if (P.staged()) { // padded rows: the request runs on its staging copies
+                W_CK(copy_to_pitched(P, P.d_bst, bq, s->stream));
+                bq = P.d_bst;
+                xq = P.d_xst;
+            }
+            P.desc.vec[ROLE_B] = (void *)bq;
+            P.desc.vec[ROLE_X] = xq;
+            P.desc.vec[ROLE_RT] = (void *)bq; // x0 = 0: r~ = r0 = b
             P.desc.sc = s->d_sc + slot;
             P.desc.tmap = s->d_tmap + (size_t)TMAPS_PER_PROBLEM * slot;
             Plan plan;
@@ -420,6 +427,10 @@ void worker_main(psolve_server *s)
         Launcher T = server_launcher(s, s->d_list_fin);
         enqueue_true_residual(T);
         W_CK(T.err);
+        for (int q : fin) {
+            const Request &r = s->slots[q].req;
+            if (r.prob.staged()) W_CK(copy_from_pitched(r.prob, r.x, r.prob.d_xst, s->stream));
+        }
         W_CK(cudaMemcpyAsync(s->h_sc, s->d_sc, sizeof(Scal) * s->max_slots, cudaMemcpyDeviceToHost, s->stream));
         W_CK(cudaEventRecord(s->ev, s->stream));
         W_CK(cudaEventSynchronize(s->ev));
@@ -548,6 +559,10 @@ psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const doubl
     }
     P.prec = plan.prec;
     P.have_rt = false;
+    // rows padded to a multiple of 8 elements when nx is not one, so that every
+    // request runs on the tensor copies (b is staged at admission, x copied back
+    // when the request retires)
+    P.px = P.n[0] % 8 != 0 ? padded_pitch(P.n[0]) : 0;
     problem_geometry(P, s->di.sms);
     P.desc.rtol = rtol;
     P.desc.maxit = maxit;
@@ -558,7 +573,7 @@ psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const doubl
     r.maxit = maxit;
     r.lmin_scale = o.lmin_scale;
     r.lmax_scale = o.lmax_scale;
-    r.bytes = problem_bytes(P.n, P.prec, false, s->di.sms);
+    r.bytes = problem_bytes(P.n, P.prec, false, s->di.sms, P.px);
     if ((double)r.bytes > s->budget) {
         set_error("request needs %zu bytes; the server's budget is %.0f", r.bytes, s->budget);
         return PSOLVE_REJECTED;

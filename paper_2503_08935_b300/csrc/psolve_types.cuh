@@ -79,6 +79,11 @@ struct Scal {
 struct Desc {
     // geometry
     int32_t nx, ny, nz;
+    // row pitch of every vector in elements (element (i, j, k) is at
+    // i + px (j + ny k)): nx, or nx rounded up to a multiple of 8 so that the
+    // rows of every precision start on 16-byte boundaries for the tensor maps;
+    // the columns i >= nx are never read as grid values
+    int32_t px;
     int32_t tiles_x, tiles_y;
     int32_t zc;         // planes per unit chunk
     int32_t nzc;        // chunks along z
@@ -110,7 +115,7 @@ struct Desc {
     Scal *sc;
     double *partials;   // units * MAX_DOTS doubles
     // TMA engine: 1 if every stencil operand of this problem can be staged by
-    // tensor copies (nx % 8 == 0, 16-byte aligned vectors); tmap[TMAPS_PER_ROLE
+    // tensor copies (px % 8 == 0, 16-byte aligned vectors); tmap[TMAPS_PER_ROLE
     // * role + TMAP_HALO / TMAP_PLAIN / TMAP_HALO2] are the role's maps.
     int32_t tma;
     int32_t rr_every;   // residual replacement every rr_every outer iterations (0: never)

@@ -47,8 +47,7 @@ def test_autotuned_solve_is_valid_and_matches_oracle(shape, prec):
     assert info.tuned in (1, 2)
     zc = info.slab_planes
     assert 1 <= zc <= min(32, shape[0]) and zc & (zc - 1) == 0
-    if shape[2] % 8 != 0:
-        assert info.engine == 0  # the TMA ring needs nx % 8 == 0
+    assert info.engine in (0, 1)  # nx = 37: padded rows, either engine may be chosen
     xo, ro = O.bicgstab(bn, I.default_h(shape), rtol=1e-10, maxit=500, precond=O.PC_CHEB, degree=8)
     assert info.status == B.OK and info.rel_res_true <= 1.1e-10
     if prec == B.FP64:

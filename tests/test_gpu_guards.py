@@ -39,7 +39,8 @@ def margins_intact(buf, n):
 
 CASES = [
     ((24, 20, 40), B.PC_CHEB, 8, (1, 1, 1), {}),                       # TMA ring engine
-    ((23, 19, 37), B.PC_CHEB, 6, (1, 1, 1), {}),                       # general engine (nx % 8 != 0)
+    ((23, 19, 37), B.PC_CHEB, 6, (1, 1, 1), {}),                       # padded rows, b and x staged
+    ((23, 19, 37), B.PC_CHEB, 6, (1, 1, 1), {"engine": 1}),            # general engine
     ((24, 20, 40), B.PC_BJ_CHEB, 4, (2, 2, 2), {}),
     ((24, 20, 40), B.PC_GNOCOMM_CHEB, 4, (2, 2, 2), {"cheb_prec": B.FP32}),
     ((24, 20, 40), B.PC_CHEB, 6, (1, 1, 1), {"cheb_prec": B.BF16}),

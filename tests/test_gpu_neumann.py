@@ -33,7 +33,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("bc", BCS)
-@pytest.mark.parametrize("shape", [(12, 16, 40), (11, 13, 21)])  # TMA ring (nx % 8 == 0), general engine
+@pytest.mark.parametrize("shape", [(12, 16, 40), (11, 13, 21)])  # TMA ring, unpadded and padded rows
 @pytest.mark.parametrize("blocked", [0, 1])
 def test_neumann_apply_A_matches_oracle(bc, shape, blocked):
     h = (0.07, 0.05, 0.09)

@@ -30,7 +30,8 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 # ragged shapes (nz, ny, nx): partial x tiles (32), partial y tiles (8), short z
-# nx % 8 == 0 runs the TMA ring engine (engine=0), other sizes the general engine
+# engine=0 runs the TMA ring on every size (rows padded to a multiple of 8 when
+# nx is not one); engine=1 forces the general engine
 SHAPES = [(1, 1, 1), (2, 3, 5), (7, 9, 33), (19, 24, 37), (16, 16, 16), (33, 18, 5), (5, 40, 70),
           (64, 64, 64), (3, 17, 40), (9, 5, 8), (13, 11, 72)]
 
@@ -308,7 +309,7 @@ def test_engines_agree(prec, precond, blocks):
 
 
 @pytest.mark.parametrize("prec", [B.FP32, B.BF16])
-@pytest.mark.parametrize("shape", [(37, 20, 40), (33, 16, 64), (5, 9, 8)])
+@pytest.mark.parametrize("shape", [(37, 20, 40), (33, 16, 64), (5, 9, 8), (21, 17, 37), (12, 9, 22)])
 def test_wide_sweeps_bitwise_equal_to_one_point_sweeps(prec, shape):
     """With FP32/BF16 Chebyshev vectors, G(CI) on the TMA ring runs its sweeps
     two per pass and two x-adjacent points per thread (CI sweep 1 on the
@@ -317,7 +318,8 @@ def test_wide_sweeps_bitwise_equal_to_one_point_sweeps(prec, shape):
     expressions.  M^-1 v (degrees 1..5, 8 and 16: sweep 2 without y_{k-2},
     pairs ending on the last sweep or followed by a single one) and a whole
     solve agree bit for bit, on grids with a partial x tile, ragged y tiles and
-    odd plane counts."""
+    odd plane counts, and on grids whose rows are padded for the tensor copies
+    (nx = 37: the last point pair straddles the grid edge; nx = 22)."""
     h = I.default_h(shape)
     v = dev(I.rhs_uniform(shape, seed=21))
     for deg in (1, 2, 3, 4, 5, 8, 16):
@@ -337,6 +339,62 @@ def test_wide_sweeps_bitwise_equal_to_one_point_sweeps(prec, shape):
         sols.append((x, info.iterations, info.status))
     assert sols[0][1] == sols[1][1] and sols[0][2] == sols[1][2]
     assert torch.equal(sols[0][0], sols[1][0])
+
+
+# ------------------------------------------------------------ padded rows --
+@pytest.mark.parametrize("shape", [(21, 17, 37), (12, 9, 22)])
+def test_padded_rows_every_entry_point(shape):
+    """A grid whose nx is not a multiple of 8 is laid out with its rows padded
+    to one, so that it runs on the TMA ring (info.engine == 1) while the
+    caller's b and x are copied through padded staging vectors.  Every entry
+    point gives bitwise the values of a context on the general engine with
+    unpadded rows (engine = 1): A u, M^-1 v, u . b, a solve from x0 = 0, from
+    host buffers and from an initial guess; a batch and a served request of
+    the grid give bitwise the solo solve (FP32 Chebyshev vectors for the
+    server, so its paired sweeps run over the padded rows too)."""
+    h = I.default_h(shape)
+    b = dev(I.rhs_uniform(shape, seed=31))
+    u = dev(I.rhs_uniform(shape, seed=32))
+    x0 = dev(I.rhs_uniform(shape, seed=33))
+    res = {}
+    for engine in (0, 1):
+        r = {}
+        with B.Solver(shape, h, engine=engine) as s:
+            r["Au"] = host(s.apply_A(u, torch.empty_like(u)))
+            r["Mv"] = host(s.precond_apply(u, torch.empty_like(u), B.PC_CHEB, 5))
+            r["dot"] = np.array([s.dot(u, b)])
+            x = torch.zeros_like(b)
+            info = s.solve(b, x, rtol=1e-10, maxit=300, precond=B.PC_CHEB, degree=4)
+            assert info.status == B.OK and info.engine == (1 if engine == 0 else 0)
+            r["x"], r["it"] = host(x), np.array([info.iterations])
+            xh = torch.zeros(shape, dtype=torch.float64).pin_memory()
+            s.solve_host(torch.from_numpy(host(b)).pin_memory(), xh, rtol=1e-10, maxit=300, precond=B.PC_CHEB,
+                         degree=4)
+            r["x_host"] = xh.numpy().copy()
+        with B.Solver(shape, h, engine=engine, use_x0=1) as s:
+            x = x0.clone()
+            info = s.solve(b, x, rtol=1e-10, maxit=300, precond=B.PC_CHEB, degree=4)
+            assert info.status == B.OK
+            r["x_from_x0"] = host(x)
+        res[engine] = r
+    for k in res[0]:
+        assert np.array_equal(res[0][k], res[1][k]), k
+    assert np.array_equal(res[0]["x"], res[0]["x_host"])
+    xo, ro = O.bicgstab(host(b), h, rtol=1e-10, maxit=300, precond=O.PC_CHEB, degree=4)
+    assert rel(res[0]["x"], xo) <= 1e-8
+    # a batch with the padded grid and an unpadded one, and a served request
+    xb = [torch.zeros_like(b), torch.zeros((8, 8, 16), dtype=torch.float64, device=DEV)]
+    infos = B.solve_batch([b, dev(I.rhs_uniform((8, 8, 16), seed=34))], xb, rtol=1e-10, maxit=300,
+                          precond=B.PC_CHEB, degree=4)
+    assert infos[0].engine == 1 and np.array_equal(host(xb[0]), res[0]["x"])
+    with B.Solver(shape, h, cheb_prec=B.FP32) as s:
+        xs = torch.zeros_like(b)
+        solo = s.solve(b, xs, rtol=1e-9, maxit=300, precond=B.PC_CHEB, degree=8)
+    with B.Server(4e9, max_slots=4) as srv:
+        xv = torch.zeros_like(b)
+        served = srv.wait(srv.submit(b, xv, rtol=1e-9, maxit=300, precond=B.PC_CHEB, degree=8, cheb_prec=B.FP32))
+    assert served.status == B.OK and served.iterations == solo.iterations and served.engine == 1
+    assert torch.equal(xv, xs)
 
 
 def test_solve_with_initial_guess():

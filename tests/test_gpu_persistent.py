@@ -33,7 +33,8 @@ def run(shape, b, precond, degree, rtol=1e-10, maxit=500, x0=None, **kw):
 CASES = [
     # (shape (nz, ny, nx), precond, degree, opts)
     ((24, 32, 40), B.PC_CHEB, 8, {}),                                   # TMA ring, exact bounds
-    ((23, 19, 37), B.PC_CHEB, 6, {}),                                   # general engine (nx % 8 != 0)
+    ((23, 19, 37), B.PC_CHEB, 6, {}),                                   # TMA ring on padded rows (nx % 8 != 0)
+    ((23, 19, 37), B.PC_CHEB, 6, dict(engine=1)),                       # general engine
     ((24, 32, 40), B.PC_CHEB, 8, dict(lmin_scale=100.0, lmax_scale=1 - 1e-4)),  # rescaled bounds (y term)
     ((24, 32, 40), B.PC_CHEB, 8, dict(cheb_prec=B.FP32)),
     ((32, 32, 32), B.PC_BJ_CHEB, 6, dict(cheb_prec=B.FP32, blocks=(2, 2, 2))),
