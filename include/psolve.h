@@ -144,6 +144,20 @@ typedef struct {
                                 context keeps a buffer of 2 * maxit doubles,
                                 grown when a solve asks for more iterations.
                                 Contexts only (not batch or server).         */
+    int32_t slab_share;      /* how many grids of this shape the slab-depth
+                                rule takes to share every launch: the more,
+                                the deeper the slabs (z planes per work unit)
+                                it picks, hence fewer units and less
+                                per-unit overhead when many grids fill the
+                                GPU together.  0 = the entry point's own: 1
+                                (a grid alone) for psolve_create and
+                                psolve_solve_batch, PSOLVE_SERVER_SLAB_SHARE
+                                for psolve_submit.  The decomposition fixes
+                                the order of every reduction, so a served
+                                request's result is bitwise that of a
+                                context created with the same slab_share (and
+                                otherwise the same options).  Ignored with
+                                autotune = 1.                                */
     double inner_rtol;       /* and inner relative tolerance; 0 = the
                                 experimental set-up's 1e-2 for G(BiCGS) and
                                 1e-6 for BJ(BiCGS)                           */
@@ -153,7 +167,7 @@ typedef struct {
  * on; x0 = 0; poll auto; graphs on; timing off; true residual on; rr off;
  * engine auto; per-kernel launches (persistent off); autotune off; inner
  * solves (G(BiCGS), BJ(BiCGS)) at the set-up's tolerances, 500 iterations;
- * no residual history. */
+ * no residual history; slab_share 0 (the entry point's own). */
 PSOLVE_API void psolve_opts_default(psolve_opts *o);
 
 /* Kernel classes reported by timing mode (psolve_result.kclass_*). */
@@ -376,6 +390,11 @@ PSOLVE_API psolve_status psolve_solve_batch(int32_t count, const int64_t *grids,
 /* ---- continuous-batching server ---------------------------------------- */
 
 typedef struct psolve_server psolve_server;
+
+/* The slab-depth rule's default share for served requests (opts.slab_share =
+ * 0 in psolve_submit): a served request shares its launches with the other
+ * admitted ones. */
+#define PSOLVE_SERVER_SLAB_SHARE 16
 
 /* A server owns a device memory pool of hbm_budget_bytes, a request queue
  * and a host thread that advances all admitted problems together, a few

@@ -570,6 +570,10 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
         set_error("unknown Chebyshev precision %d", o.cheb_prec);
         return PSOLVE_E_ARG;
     }
+    if (o.slab_share < 0 || o.slab_share > 4096) {
+        set_error("slab_share %d outside [0, 4096]", o.slab_share);
+        return PSOLVE_E_ARG;
+    }
     psolve_ctx *c = new psolve_ctx();
     c->opts = o;
     c->stream = (cudaStream_t)stream;
@@ -591,7 +595,7 @@ psolve_status psolve_create(const int64_t grid[3], const double h[3], const int3
     // rows padded to a multiple of 8 elements when nx is not one, so that the
     // tensor copies can run on the grid (unless the general engine is forced)
     P.px = (o.engine != 1 && P.n[0] % 8 != 0) ? padded_pitch(P.n[0]) : 0;
-    problem_geometry(P, c->di.sms);
+    problem_geometry(P, c->di.sms, 0, o.slab_share > 0 ? o.slab_share : 1);
     P.mem_bytes = problem_bytes(P.n, P.prec, P.have_rt, c->di.sms, P.px);
 #define CREATE_CK(call)                                                                          \
     do {                                                                                         \
@@ -1394,6 +1398,10 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         set_error("unknown Chebyshev precision %d", o.cheb_prec);
         return PSOLVE_E_ARG;
     }
+    if (o.slab_share < 0 || o.slab_share > 4096) {
+        set_error("slab_share %d outside [0, 4096]", o.slab_share);
+        return PSOLVE_E_ARG;
+    }
     if (o.persistent && o.timing) {
         set_error("timing mode times separate kernel launches; it cannot run with persistent = 1");
         return PSOLVE_E_ARG;
@@ -1425,7 +1433,7 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         st = check_blocks(P, precond);
         if (st != PSOLVE_OK) return st;
         P.px = (o.engine != 1 && P.n[0] % 8 != 0) ? padded_pitch(P.n[0]) : 0; // as in psolve_create
-        problem_geometry(P, di.sms);
+        problem_geometry(P, di.sms, 0, o.slab_share > 0 ? o.slab_share : 1);
         offs[q] = total_bytes;
         total_bytes += problem_bytes(P.n, P.prec, false, di.sms, P.px);
         total_units += P.desc.units;

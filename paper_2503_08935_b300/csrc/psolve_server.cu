@@ -541,6 +541,10 @@ psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const doubl
         set_error("unknown Chebyshev precision %d", o.cheb_prec);
         return PSOLVE_E_ARG;
     }
+    if (o.slab_share < 0 || o.slab_share > 4096) {
+        set_error("slab_share %d outside [0, 4096]", o.slab_share);
+        return PSOLVE_E_ARG;
+    }
     Plan plan;
     plan.precond = precond;
     plan.degree = precond == PSOLVE_PC_NONE ? 0 : degree;
@@ -563,7 +567,9 @@ psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const doubl
     // request runs on the tensor copies (b is staged at admission, x copied back
     // when the request retires)
     P.px = P.n[0] % 8 != 0 ? padded_pitch(P.n[0]) : 0;
-    problem_geometry(P, s->di.sms);
+    // deeper slabs than for a grid alone: the request shares its launches
+    // with the other admitted ones (PSOLVE_SERVER_SLAB_SHARE unless asked)
+    problem_geometry(P, s->di.sms, 0, o.slab_share > 0 ? o.slab_share : PSOLVE_SERVER_SLAB_SHARE);
     P.desc.rtol = rtol;
     P.desc.maxit = maxit;
     P.desc.half_check = o.half_step_check ? 1 : 0;

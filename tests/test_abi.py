@@ -49,16 +49,18 @@ def test_struct_layout_matches_c(tmp_path):
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(psolve_opts), sizeof(psolve_result),"
         " offsetof(psolve_result, kernel_launches), offsetof(psolve_result, kclass_bytes),"
         " offsetof(psolve_opts, engine), offsetof(psolve_opts, autotune), offsetof(psolve_result, tuned));"
-        " printf(\"%zu %zu\\n\", offsetof(psolve_opts, record_history), offsetof(psolve_opts, inner_rtol));"
+        " printf(\"%zu %zu %zu %d\\n\", offsetof(psolve_opts, record_history), offsetof(psolve_opts, inner_rtol),"
+        " offsetof(psolve_opts, slab_share), PSOLVE_SERVER_SLAB_SHARE);"
         " return 0;}\n")
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
-    so, sr, okl, okb, orr, oat, otu, orh, oir = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
-                                                                        check=True).stdout.split())
+    so, sr, okl, okb, orr, oat, otu, orh, oir, oss, sss = map(
+        int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split())
     assert so == ctypes.sizeof(B.Opts) and sr == ctypes.sizeof(B.Result)
     assert okl == B.Result.kernel_launches.offset and okb == B.Result.kclass_bytes.offset
     assert orr == B.Opts.engine.offset and oat == B.Opts.autotune.offset and otu == B.Result.tuned.offset
     assert orh == B.Opts.record_history.offset and oir == B.Opts.inner_rtol.offset
+    assert oss == B.Opts.slab_share.offset and sss == B.SERVER_SLAB_SHARE
 
 
 def test_default_opts(L):
@@ -67,7 +69,7 @@ def test_default_opts(L):
     assert list(o.blocks) == [1, 1, 1]
     assert o.cheb_prec == B.FP64 and o.half_step_check == 1 and o.use_x0 == 0
     assert o.use_graph == 1 and o.true_residual == 1 and o.timing == 0
-    assert o.record_history == 0
+    assert o.record_history == 0 and o.slab_share == 0
 
 
 def _create(L, grid, h, bc=None, opts=None):

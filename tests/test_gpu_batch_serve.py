@@ -1,6 +1,8 @@
 """Batched and served solves: each problem's result is bitwise the result of
-solving it alone, whatever else shares the launches; the server admits work
-as memory frees up and rejects requests that cannot fit."""
+solving it alone (in a context with the same slab_share: 1 for batches,
+PSOLVE_SERVER_SLAB_SHARE for served requests by default), whatever else shares
+the launches; the server admits work as memory frees up and rejects requests
+that cannot fit."""
 import numpy as np
 import pytest
 import torch
@@ -28,19 +30,25 @@ def solo(shape, b, precond, degree, prec, rtol=1e-10, **kw):
     return x.cpu().numpy(), info
 
 
+@pytest.mark.parametrize("share", [0, 1])
 @pytest.mark.parametrize("prec", [B.FP64, B.FP32])
-def test_served_results_bitwise_equal_alone(prec):
+def test_served_results_bitwise_equal_alone(prec, share):
+    """share 0: the server's default slab share, against contexts created with
+    slab_share = SERVER_SLAB_SHARE; share 1: requests decomposed as a grid
+    alone, against default contexts."""
     shapes = [(24, 16, 40), (17, 9, 33), (32, 32, 32), (8, 40, 16), (20, 20, 21), (48, 24, 64)]
     bs = [torch.from_numpy(I.rhs_uniform(sh, seed=50 + q)).to(DEV) for q, sh in enumerate(shapes)]
     xs = [torch.zeros(sh, dtype=torch.float64, device=DEV) for sh in shapes]
     torch.cuda.synchronize()
     with B.Server(budget_bytes=2 << 30, max_slots=4) as srv:
-        tickets = [srv.submit(b, x, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=6, cheb_prec=prec)
+        tickets = [srv.submit(b, x, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=6, cheb_prec=prec,
+                              slab_share=share)
                    for b, x in zip(bs, xs)]
         infos = [srv.wait(t) for t in tickets]
     torch.cuda.synchronize()
     for q, sh in enumerate(shapes):
-        xa, ia = solo(sh, bs[q], B.PC_CHEB, 6, prec)
+        xa, ia = solo(sh, bs[q], B.PC_CHEB, 6, prec, slab_share=share or B.SERVER_SLAB_SHARE)
+        assert infos[q].slab_planes == ia.slab_planes
         assert infos[q].status == B.OK and infos[q].iterations == ia.iterations
         assert np.array_equal(xs[q].cpu().numpy(), xa)
         assert infos[q].rel_res_true <= 2e-10
@@ -91,7 +99,7 @@ def test_served_requests_join_while_others_run():
         ib = srv.wait(tb)
     assert ism.status == B.OK and ib.status == B.OK
     assert st_big == B.PENDING  # the small one completed while the big one was still running
-    xa, ia = solo(small_shape, bsm, B.PC_CHEB, 8, B.FP64)
+    xa, ia = solo(small_shape, bsm, B.PC_CHEB, 8, B.FP64, slab_share=B.SERVER_SLAB_SHARE)
     assert np.array_equal(xsm.cpu().numpy(), xa)
 
 
@@ -126,7 +134,7 @@ def test_served_mixed_preconditioners_bitwise_equal_alone():
     torch.cuda.synchronize()
     for q, (sh, pc, d, prec, blk) in enumerate(MIXED_REQUESTS):
         x = torch.zeros(sh, dtype=torch.float64, device=DEV)
-        with B.Solver(sh, cheb_prec=prec, blocks=blk) as s:
+        with B.Solver(sh, cheb_prec=prec, blocks=blk, slab_share=B.SERVER_SLAB_SHARE) as s:
             ia = s.solve(bs[q], x, rtol=1e-10, maxit=1000, precond=pc, degree=d)
         torch.cuda.synchronize()
         assert infos[q].status == B.OK and ia.status == B.OK
@@ -145,3 +153,23 @@ def test_batch_of_mixed_sizes_config_shapes():
         xa, ia = solo(sh, bs[q], B.PC_CHEB, 8, B.FP64)
         assert infos[q].status == B.OK and infos[q].iterations == ia.iterations
         assert np.array_equal(xs[q].cpu().numpy(), xa)
+
+
+def test_slab_share_picks_deeper_slabs_for_shared_launches():
+    """A 32^3 grid alone is cut into one-plane units (parallelism for one
+    grid); with slab_share = 16 the rule takes it to share every launch with
+    15 more and picks deeper slabs.  Both decompositions solve to the oracle's
+    solution, and a batch with slab_share = 16 is bitwise the solo solve with
+    the same setting."""
+    shape = (32, 32, 32)
+    b = torch.from_numpy(I.rhs_uniform(shape, seed=90)).to(DEV)
+    x1, i1 = solo(shape, b, B.PC_CHEB, 8, B.FP64)
+    x16, i16 = solo(shape, b, B.PC_CHEB, 8, B.FP64, slab_share=16)
+    assert i16.slab_planes > i1.slab_planes
+    xo, ro = O.bicgstab(b.cpu().numpy(), I.default_h(shape), rtol=1e-10, maxit=500, precond=O.PC_CHEB, degree=8)
+    for x, info in ((x1, i1), (x16, i16)):
+        assert info.status == B.OK and abs(info.iterations - ro.iterations) <= 2
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-8
+    xb = [torch.zeros(shape, dtype=torch.float64, device=DEV)]
+    ib = B.solve_batch([b], xb, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8, slab_share=16)
+    assert ib[0].slab_planes == i16.slab_planes and np.array_equal(xb[0].cpu().numpy(), x16)

@@ -387,7 +387,7 @@ def test_padded_rows_every_entry_point(shape):
     infos = B.solve_batch([b, dev(I.rhs_uniform((8, 8, 16), seed=34))], xb, rtol=1e-10, maxit=300,
                           precond=B.PC_CHEB, degree=4)
     assert infos[0].engine == 1 and np.array_equal(host(xb[0]), res[0]["x"])
-    with B.Solver(shape, h, cheb_prec=B.FP32) as s:
+    with B.Solver(shape, h, cheb_prec=B.FP32, slab_share=B.SERVER_SLAB_SHARE) as s:
         xs = torch.zeros_like(b)
         solo = s.solve(b, xs, rtol=1e-9, maxit=300, precond=B.PC_CHEB, degree=8)
     with B.Server(4e9, max_slots=4) as srv:
