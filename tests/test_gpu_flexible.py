@@ -97,6 +97,25 @@ def test_flexible_solve_matches_oracle(bc, precond, blocks, inner_rtol):
     assert info.rel_res_true <= 1.1e-10
 
 
+@pytest.mark.parametrize("precond,blocks", [(B.PC_G_BICGS, (1, 1, 1)), (B.PC_BJ_BICGS, (2, 2, 2))])
+def test_flexible_solve_on_padded_rows_equals_general_engine(precond, blocks):
+    """nx = 36: the context pads its rows to 40 for the tensor copies; the
+    G(BiCGS) inner problem shares that pitch, and BJ(BiCGS) gathers its blocks
+    from the padded rows.  The solve is bitwise the one of the general engine
+    on unpadded rows."""
+    shape = (16, 24, 36)
+    h = I.default_h(shape)
+    b = dev(I.rhs_uniform(shape, seed=906))
+    out = []
+    for engine in (0, 1):
+        x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+        with B.Solver(shape, h, blocks=blocks, engine=engine, inner_rtol=1e-6, inner_maxit=500) as s:
+            info = s.solve(b, x, rtol=1e-10, maxit=500, precond=precond)
+        assert info.status == B.OK and info.engine == (1 if engine == 0 else 0)
+        out.append((x, info.iterations, info.inner_iterations))
+    assert out[0][1:] == out[1][1:] and torch.equal(out[0][0], out[1][0])
+
+
 def test_bj_bicgs_with_one_block_equals_g_bicgs_bitwise():
     shape = (16, 24, 32)
     h = (0.05, 0.06, 0.07)
