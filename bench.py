@@ -615,8 +615,9 @@ def extra_small_latency(B, I, torch, stream, reps=200):
 def extra_batch(B, I, torch, stream, count=64):
     """64 independent grids, sides drawn (seed 2) from {32, 48, 64, 96, 128},
     G(CI) degree 8, FP64, rtol 1e-10: one batched solve (every launch covers
-    all unfinished grids, iterations replayed from one CUDA graph) against a
-    sequential loop of single solves of the same grids on the same GPU."""
+    all unfinished grids, iterations replayed from one CUDA graph; the batch's
+    default slab share) against a sequential loop of single solves of the same
+    grids on the same GPU (contexts created beforehand, slab share 1)."""
     shapes = I.batch_shapes(count=count, seed=2)
     bs = [torch.from_numpy(I.rhs_uniform(sh, seed=1 + q)).cuda() for q, sh in enumerate(shapes)]
     xs = [torch.zeros_like(b) for b in bs]
@@ -653,14 +654,16 @@ def extra_batch(B, I, torch, stream, count=64):
     ms_s, infos_s = _timed_cuda(seq, stream, torch, 1)
     for s_ in solvers:
         s_.close()
-    same = all(a.iterations == c.iterations for a, c in zip(infos, infos_s))
+    # the batch decomposes its grids with the shared slab share, the single
+    # solves as grids alone: other reduction orders, iteration counts may differ
+    diff = max(abs(a.iterations - c.iterations) for a, c in zip(infos, infos_s))
     return {"workload": f"batch of {count} grids, sides from {{32,48,64,96,128}} (seed 2), G(CI) d=8 FP64, rtol 1e-10",
             "points_total": npts, "batched_ms": ms_b, "batched_solves_per_s": count * 1e3 / ms_b,
             "persistent_ms": ms_p, "persistent_solves_per_s": count * 1e3 / ms_p,
             "persistent_launches": infos_p[0].kernel_launches, "persistent_bitwise_equal_to_graph": same_p,
             "autotuned": tuned,
             "sequential_ms": ms_s, "sequential_solves_per_s": count * 1e3 / ms_s, "speedup": ms_s / ms_b,
-            "all_ok": all(i.status == B.OK for i in infos), "iterations_equal_to_solo": same,
+            "all_ok": all(i.status == B.OK for i in infos), "max_iteration_difference_vs_solo": diff,
             "max_iterations": max(i.iterations for i in infos)}
 
 

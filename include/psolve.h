@@ -150,14 +150,14 @@ typedef struct {
                                 it picks, hence fewer units and less
                                 per-unit overhead when many grids fill the
                                 GPU together.  0 = the entry point's own: 1
-                                (a grid alone) for psolve_create and
-                                psolve_solve_batch, PSOLVE_SERVER_SLAB_SHARE
-                                for psolve_submit.  The decomposition fixes
-                                the order of every reduction, so a served
-                                request's result is bitwise that of a
-                                context created with the same slab_share (and
-                                otherwise the same options).  Ignored with
-                                autotune = 1.                                */
+                                (a grid alone) for psolve_create,
+                                PSOLVE_SHARED_SLAB_SHARE for
+                                psolve_solve_batch and psolve_submit.  The
+                                decomposition fixes the order of every
+                                reduction, so a batched or served problem's
+                                result is bitwise that of a context created
+                                with the same slab_share (and otherwise the
+                                same options).  Ignored with autotune = 1.   */
     double inner_rtol;       /* and inner relative tolerance; 0 = the
                                 experimental set-up's 1e-2 for G(BiCGS) and
                                 1e-6 for BJ(BiCGS)                           */
@@ -380,7 +380,9 @@ PSOLVE_API psolve_status psolve_measure_fp64_rate(int32_t kind, int64_t iters, u
  * psolve_solve).  All problems share rtol, maxit, precond, degree and opts;
  * precond is PSOLVE_PC_NONE or one of the Chebyshev forms.
  * results[q] receives problem q's result.  Each problem's iterates are
- * bitwise the same as when it is solved alone with the same opts. */
+ * bitwise the same as when it is solved alone in a context created with the
+ * same opts and the batch's slab share (opts.slab_share, by default
+ * PSOLVE_SHARED_SLAB_SHARE). */
 PSOLVE_API psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const double *h,
                                  const double *const *rhs_dev, double *const *x_dev, double rtol,
                                  int32_t maxit, int32_t precond, int32_t degree,
@@ -391,10 +393,11 @@ PSOLVE_API psolve_status psolve_solve_batch(int32_t count, const int64_t *grids,
 
 typedef struct psolve_server psolve_server;
 
-/* The slab-depth rule's default share for served requests (opts.slab_share =
- * 0 in psolve_submit): a served request shares its launches with the other
- * admitted ones. */
-#define PSOLVE_SERVER_SLAB_SHARE 16
+/* The slab-depth rule's default share for batched and served problems
+ * (opts.slab_share = 0 in psolve_solve_batch and psolve_submit): they share
+ * every launch with the other problems of the batch or the admitted
+ * requests. */
+#define PSOLVE_SHARED_SLAB_SHARE 16
 
 /* A server owns a device memory pool of hbm_budget_bytes, a request queue
  * and a host thread that advances all admitted problems together, a few

@@ -22,7 +22,7 @@ STATUS_NAMES = ["OK", "E_ARG", "E_OOM", "E_CUDA", "NOT_CONVERGED", "BREAKDOWN", 
                 "PENDING", "REJECTED"]
 PC_NONE, PC_CHEB, PC_BJ_CHEB, PC_GNOCOMM_CHEB, PC_G_BICGS, PC_BJ_BICGS = 0, 1, 2, 3, 4, 5
 FP64, FP32, BF16 = 0, 1, 2
-SERVER_SLAB_SHARE = 16  # PSOLVE_SERVER_SLAB_SHARE: psolve_submit's default opts.slab_share
+SHARED_SLAB_SHARE = 16  # PSOLVE_SHARED_SLAB_SHARE: the batch's and the server's default opts.slab_share
 K_INIT, K_CI_FIRST, K_CI_SWEEP3, K_CI_SWEEP4, K_STENCIL_DOT, K_STENCIL_2DOT, K_UPDATE, K_OTHER = range(8)
 K_NCLASS = 8
 K_NAMES = ["init", "ci_first", "ci_sweep3", "ci_sweep4", "stencil_dot", "stencil_2dot", "update", "other"]

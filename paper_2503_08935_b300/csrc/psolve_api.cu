@@ -1433,7 +1433,8 @@ psolve_status psolve_solve_batch(int32_t count, const int64_t *grids, const doub
         st = check_blocks(P, precond);
         if (st != PSOLVE_OK) return st;
         P.px = (o.engine != 1 && P.n[0] % 8 != 0) ? padded_pitch(P.n[0]) : 0; // as in psolve_create
-        problem_geometry(P, di.sms, 0, o.slab_share > 0 ? o.slab_share : 1);
+        // the grids of a batch share every launch: deeper slabs than alone
+        problem_geometry(P, di.sms, 0, o.slab_share > 0 ? o.slab_share : PSOLVE_SHARED_SLAB_SHARE);
         offs[q] = total_bytes;
         total_bytes += problem_bytes(P.n, P.prec, false, di.sms, P.px);
         total_units += P.desc.units;

@@ -568,8 +568,8 @@ psolve_status psolve_submit(psolve_server *s, const int64_t grid[3], const doubl
     // when the request retires)
     P.px = P.n[0] % 8 != 0 ? padded_pitch(P.n[0]) : 0;
     // deeper slabs than for a grid alone: the request shares its launches
-    // with the other admitted ones (PSOLVE_SERVER_SLAB_SHARE unless asked)
-    problem_geometry(P, s->di.sms, 0, o.slab_share > 0 ? o.slab_share : PSOLVE_SERVER_SLAB_SHARE);
+    // with the other admitted ones (PSOLVE_SHARED_SLAB_SHARE unless asked)
+    problem_geometry(P, s->di.sms, 0, o.slab_share > 0 ? o.slab_share : PSOLVE_SHARED_SLAB_SHARE);
     P.desc.rtol = rtol;
     P.desc.maxit = maxit;
     P.desc.half_check = o.half_step_check ? 1 : 0;

@@ -50,7 +50,7 @@ def test_struct_layout_matches_c(tmp_path):
         " offsetof(psolve_result, kernel_launches), offsetof(psolve_result, kclass_bytes),"
         " offsetof(psolve_opts, engine), offsetof(psolve_opts, autotune), offsetof(psolve_result, tuned));"
         " printf(\"%zu %zu %zu %d\\n\", offsetof(psolve_opts, record_history), offsetof(psolve_opts, inner_rtol),"
-        " offsetof(psolve_opts, slab_share), PSOLVE_SERVER_SLAB_SHARE);"
+        " offsetof(psolve_opts, slab_share), PSOLVE_SHARED_SLAB_SHARE);"
         " return 0;}\n")
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
@@ -60,7 +60,7 @@ def test_struct_layout_matches_c(tmp_path):
     assert okl == B.Result.kernel_launches.offset and okb == B.Result.kclass_bytes.offset
     assert orr == B.Opts.engine.offset and oat == B.Opts.autotune.offset and otu == B.Result.tuned.offset
     assert orh == B.Opts.record_history.offset and oir == B.Opts.inner_rtol.offset
-    assert oss == B.Opts.slab_share.offset and sss == B.SERVER_SLAB_SHARE
+    assert oss == B.Opts.slab_share.offset and sss == B.SHARED_SLAB_SHARE
 
 
 def test_default_opts(L):

@@ -1,6 +1,6 @@
 """Batched and served solves: each problem's result is bitwise the result of
-solving it alone (in a context with the same slab_share: 1 for batches,
-PSOLVE_SERVER_SLAB_SHARE for served requests by default), whatever else shares
+solving it alone (in a context with the same slab_share, by default
+PSOLVE_SHARED_SLAB_SHARE for batches and served requests), whatever else shares
 the launches; the server admits work as memory frees up and rejects requests
 that cannot fit."""
 import numpy as np
@@ -34,7 +34,7 @@ def solo(shape, b, precond, degree, prec, rtol=1e-10, **kw):
 @pytest.mark.parametrize("prec", [B.FP64, B.FP32])
 def test_served_results_bitwise_equal_alone(prec, share):
     """share 0: the server's default slab share, against contexts created with
-    slab_share = SERVER_SLAB_SHARE; share 1: requests decomposed as a grid
+    slab_share = SHARED_SLAB_SHARE; share 1: requests decomposed as a grid
     alone, against default contexts."""
     shapes = [(24, 16, 40), (17, 9, 33), (32, 32, 32), (8, 40, 16), (20, 20, 21), (48, 24, 64)]
     bs = [torch.from_numpy(I.rhs_uniform(sh, seed=50 + q)).to(DEV) for q, sh in enumerate(shapes)]
@@ -47,7 +47,7 @@ def test_served_results_bitwise_equal_alone(prec, share):
         infos = [srv.wait(t) for t in tickets]
     torch.cuda.synchronize()
     for q, sh in enumerate(shapes):
-        xa, ia = solo(sh, bs[q], B.PC_CHEB, 6, prec, slab_share=share or B.SERVER_SLAB_SHARE)
+        xa, ia = solo(sh, bs[q], B.PC_CHEB, 6, prec, slab_share=share or B.SHARED_SLAB_SHARE)
         assert infos[q].slab_planes == ia.slab_planes
         assert infos[q].status == B.OK and infos[q].iterations == ia.iterations
         assert np.array_equal(xs[q].cpu().numpy(), xa)
@@ -99,7 +99,7 @@ def test_served_requests_join_while_others_run():
         ib = srv.wait(tb)
     assert ism.status == B.OK and ib.status == B.OK
     assert st_big == B.PENDING  # the small one completed while the big one was still running
-    xa, ia = solo(small_shape, bsm, B.PC_CHEB, 8, B.FP64, slab_share=B.SERVER_SLAB_SHARE)
+    xa, ia = solo(small_shape, bsm, B.PC_CHEB, 8, B.FP64, slab_share=B.SHARED_SLAB_SHARE)
     assert np.array_equal(xsm.cpu().numpy(), xa)
 
 
@@ -134,7 +134,7 @@ def test_served_mixed_preconditioners_bitwise_equal_alone():
     torch.cuda.synchronize()
     for q, (sh, pc, d, prec, blk) in enumerate(MIXED_REQUESTS):
         x = torch.zeros(sh, dtype=torch.float64, device=DEV)
-        with B.Solver(sh, cheb_prec=prec, blocks=blk, slab_share=B.SERVER_SLAB_SHARE) as s:
+        with B.Solver(sh, cheb_prec=prec, blocks=blk, slab_share=B.SHARED_SLAB_SHARE) as s:
             ia = s.solve(bs[q], x, rtol=1e-10, maxit=1000, precond=pc, degree=d)
         torch.cuda.synchronize()
         assert infos[q].status == B.OK and ia.status == B.OK
@@ -150,7 +150,7 @@ def test_batch_of_mixed_sizes_config_shapes():
     xs = [torch.zeros(sh, dtype=torch.float64, device=DEV) for sh in shapes]
     infos = B.solve_batch(bs, xs, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=8)
     for q, sh in enumerate(shapes):
-        xa, ia = solo(sh, bs[q], B.PC_CHEB, 8, B.FP64)
+        xa, ia = solo(sh, bs[q], B.PC_CHEB, 8, B.FP64, slab_share=B.SHARED_SLAB_SHARE)
         assert infos[q].status == B.OK and infos[q].iterations == ia.iterations
         assert np.array_equal(xs[q].cpu().numpy(), xa)
 

@@ -385,9 +385,9 @@ def test_padded_rows_every_entry_point(shape):
     # a batch with the padded grid and an unpadded one, and a served request
     xb = [torch.zeros_like(b), torch.zeros((8, 8, 16), dtype=torch.float64, device=DEV)]
     infos = B.solve_batch([b, dev(I.rhs_uniform((8, 8, 16), seed=34))], xb, rtol=1e-10, maxit=300,
-                          precond=B.PC_CHEB, degree=4)
+                          precond=B.PC_CHEB, degree=4, slab_share=1)  # decomposed as a grid alone
     assert infos[0].engine == 1 and np.array_equal(host(xb[0]), res[0]["x"])
-    with B.Solver(shape, h, cheb_prec=B.FP32, slab_share=B.SERVER_SLAB_SHARE) as s:
+    with B.Solver(shape, h, cheb_prec=B.FP32, slab_share=B.SHARED_SLAB_SHARE) as s:
         xs = torch.zeros_like(b)
         solo = s.solve(b, xs, rtol=1e-9, maxit=300, precond=B.PC_CHEB, degree=8)
     with B.Server(4e9, max_slots=4) as srv:
@@ -560,7 +560,7 @@ def test_batch_bitwise_equals_alone_and_matches_oracle():
     infos = B.solve_batch([dev(b) for b in bs], xs, rtol=1e-10, maxit=300, precond=B.PC_CHEB, degree=4)
     for q, sh in enumerate(shapes):
         xa = torch.zeros(sh, dtype=torch.float64, device=DEV)
-        with B.Solver(sh) as s:
+        with B.Solver(sh, slab_share=B.SHARED_SLAB_SHARE) as s:  # the batch's default slab share
             ia = s.solve(dev(bs[q]), xa, rtol=1e-10, maxit=300, precond=B.PC_CHEB, degree=4)
         assert infos[q].status == B.OK and infos[q].iterations == ia.iterations
         assert np.array_equal(host(xs[q]), host(xa))

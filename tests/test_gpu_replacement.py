@@ -79,7 +79,7 @@ def test_replacement_in_a_batch_equals_alone():
     infos = B.solve_batch(bs, xs, rtol=1e-10, maxit=500, precond=B.PC_CHEB, degree=6, rr_every=2)
     torch.cuda.synchronize()
     for q, sh in enumerate(shapes):
-        xa, ia = run(sh, bs[q], B.PC_CHEB, 6, rr_every=2)
+        xa, ia = run(sh, bs[q], B.PC_CHEB, 6, rr_every=2, slab_share=B.SHARED_SLAB_SHARE)
         assert infos[q].status == B.OK and infos[q].iterations == ia.iterations
         assert np.array_equal(xs[q].cpu().numpy(), xa)
 
