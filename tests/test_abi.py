@@ -100,6 +100,19 @@ def test_create_rejects_bad_faces_and_bad_opts(L):
     assert st == B.E_ARG
     st, _ = _create(L, (4, 4, 4), (1, 1, 1), opts=B.default_opts(cheb_prec=7))
     assert st == B.E_ARG
+    for share in (-1, 4097):
+        st, _ = _create(L, (4, 4, 4), (1, 1, 1), opts=B.default_opts(slab_share=share))
+        assert st == B.E_ARG and "slab_share" in B.last_error()
+
+
+def test_batch_rejects_a_bad_slab_share_before_touching_the_device(L):
+    g = (ctypes.c_int64 * 3)(4, 4, 4)
+    hh = (ctypes.c_double * 3)(1, 1, 1)
+    ptrs = (ctypes.c_void_p * 1)(16)  # never dereferenced: the options are checked first
+    res = (B.Result * 1)()
+    o = B.default_opts(slab_share=-3)
+    st = L.psolve_solve_batch(1, g, hh, ptrs, ptrs, 1e-10, 10, B.PC_CHEB, 8, ctypes.byref(o), None, res)
+    assert st == B.E_ARG and "slab_share" in B.last_error()
 
 
 def test_null_arguments_are_rejected(L):
