@@ -397,6 +397,24 @@ def test_padded_rows_every_entry_point(shape):
     assert torch.equal(xv, xs)
 
 
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+@pytest.mark.parametrize("shape", [(40, 50, 99), (24, 33, 130)])
+def test_padded_rows_larger_grids_bitwise(prec, shape):
+    """Padded rows on grids of several x tiles (nx = 99: the straddling pair
+    in the fourth tile; nx = 130: pitch 136, a last tile of two columns):
+    solves on the TMA ring equal the general engine's bit for bit."""
+    h = I.default_h(shape)
+    b = dev(I.rhs_uniform(shape, seed=35))
+    out = []
+    for engine in (0, 1):
+        x = torch.zeros(shape, dtype=torch.float64, device=DEV)
+        with B.Solver(shape, h, engine=engine, cheb_prec=prec) as s:
+            info = s.solve(b, x, rtol=1e-10, maxit=400, precond=B.PC_CHEB, degree=8)
+        assert info.status == B.OK and info.engine == (1 if engine == 0 else 0)
+        out.append((x, info.iterations))
+    assert out[0][1] == out[1][1] and torch.equal(out[0][0], out[1][0])
+
+
 def test_solve_with_initial_guess():
     shape = (18, 21, 34)
     x0 = I.rhs_uniform(shape, seed=12)
