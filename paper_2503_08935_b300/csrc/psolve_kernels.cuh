@@ -1542,7 +1542,10 @@ struct OpCiFirstC {
 // accumulated product), so the iterates stay in range.
 // A sweep compiled without UNIT computes the same values (its b coefficient
 // is then c/c = 1).
-template <class T, class TB, bool BLK, bool WITH_Y = true, bool NEU = true, bool UNIT = false>
+// K2: the sweep k = 2 only, compiled without the y_{k-2} term (its coefficient
+// and operand are zero at k = 2, but with k known only at run time the term
+// costs an FMA on the FP64 pipe per point: 7 FP64 instructions instead of 6).
+template <class T, class TB, bool BLK, bool WITH_Y = true, bool NEU = true, bool UNIT = false, bool K2 = false>
 struct OpCiSweep {
     using E = Elem<T>;
     using EB = Elem<TB>;
@@ -1582,7 +1585,7 @@ struct OpCiSweep {
         k = a.k;
         nh = 1;
         hrole[0] = a.in;
-        np = a.k >= 3 ? 2 : 1;
+        np = (!K2 && a.k >= 3) ? 2 : 1;
         prole[0] = resolve_role(a.b, iter);
         prole[1] = a.z;
         // w = rho_k (2 sigma y + (2/delta)(b - A y) - rho_{k-1} z) with A y expanded:
@@ -1621,14 +1624,14 @@ struct OpCiSweep {
         PW p{C(0), C(0)};
         if (valid) {
             p.b = (C)EB::ld(bv, idx);
-            if (k >= 3) p.z = E::ld(zv, idx);
+            if (!K2 && k >= 3) p.z = E::ld(zv, idx);
         }
         return p;
     }
     __device__ __forceinline__ PW pw_s(const void *const *p, int x) const
     {
         PW v{(C)EB::lds(p[0], x), C(0)};
-        if (k >= 3) v.z = E::lds(p[1], x);
+        if (!K2 && k >= 3) v.z = E::lds(p[1], x);
         return v;
     }
     // the new iterate at one point from its centre value, neighbour-pair sums,
@@ -1640,7 +1643,8 @@ struct OpCiSweep {
         else if constexpr (UNIT) v = b;
         else if constexpr (WITH_Y) v = fma(c_b, b, c_y * yc);
         else v = c_b * b;
-        if (k >= 3) v = fma(c_z, z, v);
+        if constexpr (!K2)
+            if (k >= 3) v = fma(c_z, z, v);
         return fma(c_zz, sz, fma(c_yy, sy, fma(c_x, sx, v)));
     }
     template <int NA>

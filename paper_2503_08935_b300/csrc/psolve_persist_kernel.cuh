@@ -111,9 +111,9 @@ template <class Op>
 struct PersistAlias {
     using type = Op;
 };
-template <class T, class TB, bool BLK, bool WY, bool UNIT>
-struct PersistAlias<OpCiSweep<T, TB, BLK, WY, false, UNIT>> {
-    using type = OpCiSweep<T, TB, BLK, WY, true, UNIT>;
+template <class T, class TB, bool BLK, bool WY, bool UNIT, bool K2>
+struct PersistAlias<OpCiSweep<T, TB, BLK, WY, false, UNIT, K2>> {
+    using type = OpCiSweep<T, TB, BLK, WY, true, UNIT, K2>;
 };
 
 template <class L, class Op>
@@ -133,7 +133,8 @@ struct PersistOps { // Chebyshev-preconditioned iteration
     using Fused = typename Append<typename Append<Common, OpCiFirst<T, BLK, SIDE_P>>::type,
                                   OpCiFirst<T, BLK, SIDE_S>>::type;
     using Scaled = typename Append<
-        typename Append<typename Append<Fused, OpCiSweep<T, TB, BLK, WY, true, true>>::type,
+        typename Append<typename Append<typename Append<Fused, OpCiSweep<T, TB, BLK, WY, true, true>>::type,
+                                        OpCiSweep<T, TB, BLK, WY, true, true, true>>::type,
                         OpCiFirst<T, BLK, SIDE_P, true>>::type,
         OpCiFirst<T, BLK, SIDE_S, true>>::type;
     // mixed precision: the pointwise right-hand sides and sweep 1 on b_c

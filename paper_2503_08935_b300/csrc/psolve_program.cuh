@@ -61,6 +61,13 @@ __host__ __device__ void prog_sweep(V &v, int cls, int side, const KArgs &a, dou
             return;
         }
     }
+    if constexpr (U) {
+        if (unit && a.k == 2) { // FP64 pipe bound: the form without the y_{k-2} term
+            if (neu) v.template go<OpCiSweep<T, TB, BLK, WY, true, true, true>>(cls, side, a, bytes);
+            else v.template go<OpCiSweep<T, TB, BLK, WY, false, true, true>>(cls, side, a, bytes);
+            return;
+        }
+    }
     if (neu && unit) v.template go<OpCiSweep<T, TB, BLK, WY, true, U>>(cls, side, a, bytes);
     else if (neu) v.template go<OpCiSweep<T, TB, BLK, WY, true, false>>(cls, side, a, bytes);
     else if (unit) v.template go<OpCiSweep<T, TB, BLK, WY, false, U>>(cls, side, a, bytes);
