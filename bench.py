@@ -55,15 +55,19 @@ def sweep4_fp64_ops_per_point(degree):
 
 
 # FP64 instructions per grid point of each kernel class of the FP64 solve
-# (exact bounds, Chebyshev degree >= 2, TMA ring).  CI sweep 1 forms its
-# right-hand side u on every cell of its 36 x 10 halo box per 32 x 8 tile (the
-# direction update p = r + beta (p - omega w): 2 fused multiply-adds per cell;
-# the half step s = r - alpha w: 1), then 3 pair sums and 3 fused multiply-adds
-# per point, plus ||s||^2 on the s side; the two sides alternate, so the class
-# mean is their average.  The others: sweep k = 2: 3 adds + 3 fmas; k >= 3:
-# 3 adds + 4 fmas; stencil + dot: A u / cc (3 adds + 3 fmas) + 1; stencil + 2
-# dots: 6 + 2; update: x (2 fmas), r (1 fma), 2 dots.
-HALO_CELLS_PER_POINT_FP64 = (32 + 2 * 2) * (8 + 2) / (32 * 8)
+# (exact bounds, Chebyshev degree >= 2, TMA ring, 32-plane work units).  CI
+# sweep 1 forms its right-hand side u on every cell of its 36 x 10 halo box
+# per 32 x 8 tile and on the unit's two halo planes (the direction update
+# p = r + beta (p - omega w): 2 fused multiply-adds per cell; the half step
+# s = r - alpha w: 1), then 3 pair sums and 3 fused multiply-adds per point,
+# plus ||s||^2 on the s side; the two sides alternate, so the class mean is
+# their average.  The others: sweep k = 2: 3 adds + 3 fmas; k >= 3: 3 adds +
+# 4 fmas; stencil + dot: A u / cc (3 adds + 3 fmas) + 1; stencil + 2 dots:
+# 6 + 2; update: x (2 fmas), r (1 fma), 2 dots.  ncu's per-opcode counters
+# (DADD + DFMA executed per point) agree: 9.0 for the p side of sweep 1, 6.0
+# and 7.0 for the sweeps; the dot kernels execute 0.15-0.45 more in their
+# per-unit reductions, which the counts below leave out.
+HALO_CELLS_PER_POINT_FP64 = (32 + 2 * 2) * (8 + 2) / (32 * 8) * (32 + 2) / 32
 FP64_OPS_PER_POINT = {
     "ci_first": 0.5 * ((2 * HALO_CELLS_PER_POINT_FP64 + 6) + (HALO_CELLS_PER_POINT_FP64 + 6 + 1)),
     "ci_sweep3": 6.0, "ci_sweep4": 7.0, "stencil_dot": 7.0, "stencil_2dot": 8.0, "update": 5.0,
